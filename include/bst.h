@@ -1,0 +1,240 @@
+/*
+ * bst.h -- C ABI of libbst, a GB300 (sm_103a) block-sparse matrix multiply and
+ * block-sparse tensor contraction library following DBCSR (arXiv:1910.13555).
+ *
+ * The operations and where the paper defines them:
+ *   - blocked-CSR matrices of small dense blocks with per-row/column block sizes
+ *     (paper Sec. 2, first paragraph: "blocked compressed sparse row");
+ *   - the local multiply C = C + A x B as pairwise products of (m x k) blocks of A
+ *     with (k x n) blocks of B, grouped into batches ("stacks") that a small-GEMM
+ *     kernel processes (paper Sec. 2, the local-computation paragraph);
+ *   - the S_C << S_A,S_B rectangular product C~ = A^T B with the long K dimension
+ *     split into parts whose partial results are reduced into C (paper Sec. 3.1,
+ *     Eq. 2); here the parts are CTA groups of one GPU and the reduction is a fixed-
+ *     order sum;
+ *   - block-sparse tensors of rank 2..4 (up to 8 accepted) and their contraction
+ *     over 1..3 index pairs, computed by mapping each tensor onto a matrix whose
+ *     rows fold one set of modes and whose columns fold the other (paper Sec. 4).
+ *
+ * Additions that the paper does not define (each a reading of this library):
+ *   - the block-norm filter eps: a product A_ik B_kj is computed iff
+ *     ||A_ik||_F * ||B_kj||_F >= eps (alpha does not enter; eps = 0 keeps all);
+ *   - pattern(C_out) = pattern(C_in) U {(i,j): some kept product}; no post-filter;
+ *   - block elements are row-major (last index fastest);
+ *   - stacks: one entry (a_off, b_off, c_off) per kept product, int32 element
+ *     offsets of the stored blocks, bucketed by (m, n, k) sizes in lexicographic
+ *     order and ordered by (i, j, k) block indices inside a bucket;
+ *   - the adjoint of the computed function with the filter decisions held fixed;
+ *   - FP64 emulation on BF16 tensor cores (Ozaki-scheme slices) and a 3xTF32 path.
+ *
+ * Conventions for every entry point:
+ *   - Return value: BST_OK (0) or an error code below.  Nothing aborts and no C++
+ *     exception crosses this boundary.  bst_last_error() gives a message for the
+ *     calling thread's most recent failure.
+ *   - Host-detectable errors (bad arguments, duplicates, shape mismatches, offset
+ *     overflow) are reported synchronously before any device work is queued.
+ *   - Element data (double*) is caller-owned DEVICE memory on the context's GPU.
+ *     Index arrays passed in are HOST memory and are copied; the library keeps its
+ *     own device copies.  Everything the library allocates goes through the
+ *     context's allocator callbacks (or stream-ordered cudaMallocAsync when none
+ *     are given) and is released by the matching destroy call.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on it except where documented (plans synchronise once or twice
+ *     to learn output sizes).
+ *   - Handles are not thread-safe; use one handle per thread or lock around it.
+ *   - A matrix or tensor must outlive every plan built from it.
+ */
+#ifndef BST_H
+#define BST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t bst_status;
+
+enum {
+  BST_OK = 0,
+  BST_ERR_INVALID_ARG = 1,      /* null/negative/inconsistent argument          */
+  BST_ERR_OUT_OF_RANGE = 2,     /* block index outside the declared grid          */
+  BST_ERR_DUPLICATE_BLOCK = 3,  /* the same block listed twice                    */
+  BST_ERR_SHAPE_MISMATCH = 4,   /* block sizes of the operands do not line up     */
+  BST_ERR_OVERFLOW = 5,         /* > 2^31-1 elements in a matrix, or stack entries */
+  BST_ERR_ALLOC = 6,            /* an allocation failed                           */
+  BST_ERR_CUDA = 7,             /* a CUDA runtime call failed                     */
+  BST_ERR_TIMEOUT = 8,          /* a bounded device wait gave up                  */
+  BST_ERR_UNSUPPORTED = 9,      /* valid but outside this build's limits          */
+  BST_ERR_STATE = 10            /* wrong call order (e.g. C data not bound)       */
+};
+
+/* Message for the calling thread's last failing call (static storage). */
+const char *bst_last_error(void);
+/* Name of a status code, e.g. "BST_ERR_SHAPE_MISMATCH". */
+const char *bst_status_name(bst_status s);
+/* Library version string. */
+const char *bst_version(void);
+/* Number of CUDA kernels this library has launched in this process so far (all
+ * contexts, all threads); lets a caller count the kernels of a timed region. */
+int64_t bst_kernel_launches(void);
+
+typedef struct bst_ctx bst_ctx;
+typedef struct bst_matrix bst_matrix;
+typedef struct bst_tensor bst_tensor;
+typedef struct bst_plan bst_plan;
+typedef struct bst_batch bst_batch;
+
+/* Device allocator callbacks: return a device pointer of at least `bytes` bytes
+ * usable on `stream` (NULL on failure); free it.  `user` is passed through. */
+typedef void *(*bst_alloc_fn)(size_t bytes, void *user, void *stream);
+typedef void (*bst_free_fn)(void *ptr, void *user, void *stream);
+
+/* Create a context on CUDA device `device`.  alloc/free may both be NULL, in which
+ * case the library uses cudaMallocAsync/cudaFreeAsync on the call's stream. */
+bst_status bst_context_create(bst_ctx **out, int32_t device, bst_alloc_fn alloc,
+                              bst_free_fn free_fn, void *user);
+bst_status bst_context_destroy(bst_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Matrices (paper Sec. 2: blocked CSR of small dense blocks).
+ *
+ * nbr/nbc block rows/columns with sizes row_blk_sizes[nbr], col_blk_sizes[nbc]
+ * (host, each >= 1).  The nblocks present blocks (blk_row[b], blk_col[b]) are host
+ * arrays in any order; the library sorts them into canonical CSR order (row, then
+ * column).  `data` (device, may be NULL until bound) holds the blocks packed in
+ * that canonical order, each block row-major; its length is the sum of the block
+ * areas (bst_matrix_info).  Errors: INVALID_ARG, OUT_OF_RANGE, DUPLICATE_BLOCK,
+ * OVERFLOW (more than 2^31-1 elements or blocks).
+ * ------------------------------------------------------------------------- */
+bst_status bst_matrix_create(bst_ctx *ctx, bst_matrix **out, int32_t nbr,
+                             const int32_t *row_blk_sizes, int32_t nbc,
+                             const int32_t *col_blk_sizes, int64_t nblocks,
+                             const int32_t *blk_row, const int32_t *blk_col, double *data,
+                             void *stream);
+/* Any pointer may be NULL.  nelem = number of doubles the data buffer holds. */
+bst_status bst_matrix_info(const bst_matrix *m, int32_t *nbr, int32_t *nbc, int64_t *nblocks,
+                           int64_t *nelem);
+/* Host copies of the canonical block index and block element offsets
+ * (arrays of nblocks; any may be NULL).  Synchronises the matrix's stream. */
+bst_status bst_matrix_get_index(const bst_matrix *m, int32_t *blk_row, int32_t *blk_col,
+                                int64_t *blk_off);
+bst_status bst_matrix_bind_data(bst_matrix *m, double *data);
+bst_status bst_matrix_destroy(bst_matrix *m);
+
+/* ---------------------------------------------------------------------------
+ * Multiply (paper Sec. 2 local multiply; Sec. 3.1 for transa = 'T').
+ *
+ * C_out = alpha * op(A) * op(B) + beta * C_in, op(X) = X ('N') or X^T ('T'), with
+ * the block-norm filter eps >= 0 (see top).  C_in may be NULL.  Planning runs the
+ * GPU symbolic phase on `stream`: block norms, pair matching + filter, pattern of
+ * C_out, and the stacks.  It synchronises `stream` to learn the output sizes.
+ * The plan keeps pointers to A, B, C_in; their data are read at execute time.
+ * Errors: INVALID_ARG, SHAPE_MISMATCH (inner block sizes differ, or C_in's grid
+ * differs from op(A) rows x op(B) columns), OVERFLOW, UNSUPPORTED (more than 2^20
+ * (m,n,k) size buckets, or a C row of more than 2^21 block columns).
+ * ------------------------------------------------------------------------- */
+bst_status bst_multiply_plan(bst_ctx *ctx, char transa, char transb, const bst_matrix *A,
+                             const bst_matrix *B, const bst_matrix *C_in, double eps,
+                             void *stream, bst_plan **out);
+
+/* The result's pattern as a matrix owned by the plan (valid until the plan is
+ * destroyed).  Bind a device buffer of its nelem doubles before executing. */
+bst_status bst_plan_result(bst_plan *plan, bst_matrix **C_out);
+
+typedef struct {
+  int64_t n_candidates;   /* (i,k,j) pairs with both blocks present              */
+  int64_t n_filtered;     /* of those, dropped by the norm filter                */
+  int64_t n_stack;        /* kept products = stack entries                       */
+  int64_t n_c_blocks;     /* blocks of C_out                                     */
+  int64_t n_c_elements;   /* doubles of C_out                                    */
+  int32_t n_buckets;      /* non-empty (m,n,k) buckets                           */
+  int32_t split_k;        /* K parts used by the last execute (1 = unsplit)      */
+  double flops;           /* sum over kept products of 2 m n k                   */
+  double bytes;           /* algorithmic bytes of execute (see bst_plan_bytes)   */
+} bst_stats;
+
+bst_status bst_plan_stats(const bst_plan *plan, bst_stats *out);
+
+/* Host copies of the stacks: mnk[n_buckets*3], bucket_ptr[n_buckets+1] (int64),
+ * a_off/b_off/c_off[n_stack].  Offsets index the STORED A, B data and C_out data.
+ * Any pointer may be NULL.  Synchronises. */
+bst_status bst_plan_get_stacks(const bst_plan *plan, int32_t *mnk, int64_t *bucket_ptr,
+                               int32_t *a_off, int32_t *b_off, int32_t *c_off);
+
+/* Arithmetic used by execute. */
+enum {
+  BST_FP64 = 0,          /* native FP64 FMA                                        */
+  BST_FP64_EMU_BF16 = 1, /* Ozaki slices on BF16 tensor cores, FP64 recombination  */
+  BST_TF32X3 = 2         /* 3xTF32 compensated products, FP32 accumulate per block */
+};
+
+/* Numeric phase into C_out's bound data.  split_k: 1 = each C block summed by one
+ * warp; S > 1 = the K block range is cut into S equal parts whose partial sums go
+ * to a workspace and are added in the fixed order 0..S-1 (paper Sec. 3.1);
+ * 0 = choose S from the plan's shape.  With beta == 0 C_in is not read.
+ * Errors: STATE (C_out, A or B data not bound), INVALID_ARG, UNSUPPORTED. */
+bst_status bst_multiply_execute(bst_plan *plan, double alpha, double beta, int32_t precision,
+                                int32_t split_k, void *stream);
+
+/* Adjoint of execute's function with the filter decisions held fixed:
+ *   dop(A)_ik = alpha sum_{j kept} dC_ij op(B)_kj^T on pattern(A),
+ *   dop(B)_kj = alpha sum_{i kept} op(A)_ik^T dC_ij on pattern(B),
+ *   dC_in = beta dC on pattern(C_in)  (dC_in may be NULL),
+ * written (overwritten) in the stored layout of A, B, C_in.  dC is packed like
+ * C_out.  For a contraction plan the buffers are the tensors' packings.  FP64. */
+bst_status bst_plan_adjoint(bst_plan *plan, const double *dC, double *dA, double *dB,
+                            double *dC_in, double alpha, double beta, void *stream);
+
+bst_status bst_plan_destroy(bst_plan *plan);
+
+/* ---------------------------------------------------------------------------
+ * Tensors (paper Sec. 4).
+ *
+ * rank in 1..8; nblk[rank] blocks per mode; blk_sizes holds the block sizes of
+ * mode 0, then mode 1, ... (host).  blk_idx[nblocks*rank] (host) lists the present
+ * block tuples in any order; canonical order is lexicographic.  `data` (device)
+ * packs the blocks in canonical order, each row-major (last mode fastest).
+ * ------------------------------------------------------------------------- */
+bst_status bst_tensor_create(bst_ctx *ctx, bst_tensor **out, int32_t rank, const int32_t *nblk,
+                             const int32_t *blk_sizes, int64_t nblocks, const int32_t *blk_idx,
+                             double *data, void *stream);
+bst_status bst_tensor_info(const bst_tensor *t, int32_t *rank, int64_t *nblocks, int64_t *nelem);
+/* host copies: blk_idx[nblocks*rank] canonical, blk_off[nblocks] */
+bst_status bst_tensor_get_index(const bst_tensor *t, int32_t *blk_idx, int64_t *blk_off);
+bst_status bst_tensor_bind_data(bst_tensor *t, double *data);
+bst_status bst_tensor_destroy(bst_tensor *t);
+
+/* Contraction R = alpha * sum over contracted indices of T1 * T2 + beta * R_in.
+ * Mode c1[s] of T1 is summed against mode c2[s] of T2 (s < ncontract, 1..3); their
+ * block sizes must agree (else SHAPE_MISMATCH).  f1 (f2) lists the free modes of
+ * T1 (T2); every mode appears exactly once in c + f.  The result's modes are the
+ * free modes in the order (f1..., f2...) permuted by result_order (NULL =
+ * identity): result mode r is free slot result_order[r].  Computed on the GPU by
+ * remapping T1 to a matrix with rows = f1 fold, cols = c1 fold (or its transpose,
+ * or a permuted copy when neither is a pure fold of the stored layout), T2 to rows
+ * = c2, cols = f2, then the multiply above.  The filter applies per tensor-block
+ * pair (Frobenius norms do not change under reshaping).  R_in may be NULL. */
+bst_status bst_contract_plan(bst_ctx *ctx, const bst_tensor *T1, const bst_tensor *T2,
+                             int32_t ncontract, const int32_t *c1, const int32_t *c2,
+                             int32_t nfree1, const int32_t *f1, int32_t nfree2,
+                             const int32_t *f2, const int32_t *result_order,
+                             const bst_tensor *R_in, double eps, void *stream, bst_plan **out);
+/* The result tensor of a contraction plan (owned by the plan; bind its data). */
+bst_status bst_plan_result_tensor(bst_plan *plan, bst_tensor **R);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many independent plans executed by one persistent kernel launch,
+ * capturable into a CUDA graph.  Tile choices per (m,n) class come from the
+ * library's tune table (bst_tune_*).  alpha/beta are host arrays of n values.
+ * ------------------------------------------------------------------------- */
+bst_status bst_batch_create(bst_ctx *ctx, int32_t n, bst_plan *const *plans, bst_batch **out);
+bst_status bst_batch_execute(bst_batch *batch, const double *alpha, const double *beta,
+                             int32_t precision, void *stream);
+bst_status bst_batch_destroy(bst_batch *batch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BST_H */

@@ -1,0 +1,410 @@
+// C ABI of libbst: contexts, matrices, multiply plans (see include/bst.h).
+//
+// Host work here is limited to argument validation, canonicalising the caller's
+// block index (sort + duplicate check) at creation time, and orchestration; every
+// step of the multiply itself runs in the CUDA kernels of symbolic.cu and
+// numeric_*.cu.
+#include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "bst_internal.h"
+
+namespace bst {
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+void *Arena::alloc(size_t bytes) {
+  void *p = nullptr;
+  if (bytes == 0) bytes = 8;
+  if (ctx && ctx->alloc) {
+    p = ctx->alloc(bytes, ctx->user, stream);
+    if (!p) throw Error{BST_ERR_ALLOC, "allocator callback returned NULL"};
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      throw Error{BST_ERR_ALLOC, std::string("cudaMallocAsync: ") + cudaGetErrorString(e)};
+    }
+  }
+  bufs.push_back({p, bytes});
+  return p;
+}
+
+void Arena::release_all() {
+  for (auto &b : bufs) {
+    if (ctx && ctx->free_fn)
+      ctx->free_fn(b.p, ctx->user, stream);
+    else
+      (void)cudaFreeAsync(b.p, stream);
+  }
+  bufs.clear();
+}
+
+}  // namespace bst
+
+using bst::Error;
+
+#define API_BEGIN try {
+#define API_END                                                   \
+  }                                                               \
+  catch (const bst::Error &e) {                                   \
+    bst::set_error(e.msg);                                        \
+    return e.code;                                                \
+  }                                                               \
+  catch (const std::bad_alloc &) {                                \
+    bst::set_error("host allocation failed");                     \
+    return BST_ERR_ALLOC;                                         \
+  }                                                               \
+  catch (...) {                                                   \
+    bst::set_error("unexpected internal error");                  \
+    return BST_ERR_INVALID_ARG;                                   \
+  }                                                               \
+  return BST_OK;
+
+namespace {
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+void use_device(const bst_ctx *ctx) {
+  int cur = -1;
+  BST_CUDA(cudaGetDevice(&cur));
+  if (cur != ctx->device) BST_CUDA(cudaSetDevice(ctx->device));
+}
+
+template <class T>
+T *upload(bst::Arena &ar, const std::vector<T> &v, cudaStream_t s) {
+  T *d = ar.alloc_n<T>(v.size());
+  if (!v.empty())
+    BST_CUDA(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bst_last_error(void) { return bst::g_last_error.c_str(); }
+
+const char *bst_status_name(bst_status s) {
+  switch (s) {
+    case BST_OK: return "BST_OK";
+    case BST_ERR_INVALID_ARG: return "BST_ERR_INVALID_ARG";
+    case BST_ERR_OUT_OF_RANGE: return "BST_ERR_OUT_OF_RANGE";
+    case BST_ERR_DUPLICATE_BLOCK: return "BST_ERR_DUPLICATE_BLOCK";
+    case BST_ERR_SHAPE_MISMATCH: return "BST_ERR_SHAPE_MISMATCH";
+    case BST_ERR_OVERFLOW: return "BST_ERR_OVERFLOW";
+    case BST_ERR_ALLOC: return "BST_ERR_ALLOC";
+    case BST_ERR_CUDA: return "BST_ERR_CUDA";
+    case BST_ERR_TIMEOUT: return "BST_ERR_TIMEOUT";
+    case BST_ERR_UNSUPPORTED: return "BST_ERR_UNSUPPORTED";
+    case BST_ERR_STATE: return "BST_ERR_STATE";
+    default: return "BST_ERR_UNKNOWN";
+  }
+}
+
+const char *bst_version(void) { return "bst 0.1 (sm_103a)"; }
+
+int64_t bst_kernel_launches(void) { return bst::g_launches.load(std::memory_order_relaxed); }
+
+bst_status bst_context_create(bst_ctx **out, int32_t device, bst_alloc_fn alloc,
+                              bst_free_fn free_fn, void *user) {
+  API_BEGIN
+  BST_REQUIRE(out != nullptr, BST_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  BST_REQUIRE((alloc == nullptr) == (free_fn == nullptr), BST_ERR_INVALID_ARG,
+              "alloc and free callbacks must be given together");
+  int ndev = 0;
+  BST_CUDA(cudaGetDeviceCount(&ndev));
+  BST_REQUIRE(device >= 0 && device < ndev, BST_ERR_INVALID_ARG, "no such CUDA device");
+  auto *c = new bst::Ctx();
+  c->device = device;
+  c->alloc = alloc;
+  c->free_fn = free_fn;
+  c->user = user;
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+  c->num_sms = v;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  c->max_smem_optin = (size_t)v;
+  *out = c;
+  API_END
+}
+
+bst_status bst_context_destroy(bst_ctx *ctx) {
+  API_BEGIN
+  delete static_cast<bst::Ctx *>(ctx);
+  API_END
+}
+
+bst_status bst_matrix_create(bst_ctx *ctx, bst_matrix **out, int32_t nbr,
+                             const int32_t *row_blk_sizes, int32_t nbc,
+                             const int32_t *col_blk_sizes, int64_t nblocks,
+                             const int32_t *blk_row, const int32_t *blk_col, double *data,
+                             void *stream) {
+  API_BEGIN
+  BST_REQUIRE(ctx && out, BST_ERR_INVALID_ARG, "ctx or out is NULL");
+  *out = nullptr;
+  BST_REQUIRE(nbr >= 0 && nbc >= 0 && nblocks >= 0, BST_ERR_INVALID_ARG, "negative size");
+  BST_REQUIRE((nbr == 0 || row_blk_sizes) && (nbc == 0 || col_blk_sizes), BST_ERR_INVALID_ARG,
+              "block size array is NULL");
+  BST_REQUIRE(nblocks == 0 || (blk_row && blk_col), BST_ERR_INVALID_ARG, "block index is NULL");
+  BST_REQUIRE(nblocks < INT32_MAX, BST_ERR_OVERFLOW, "more than 2^31-1 blocks");
+  for (int32_t i = 0; i < nbr; ++i)
+    BST_REQUIRE(row_blk_sizes[i] >= 1, BST_ERR_INVALID_ARG, "block row size < 1");
+  for (int32_t j = 0; j < nbc; ++j)
+    BST_REQUIRE(col_blk_sizes[j] >= 1, BST_ERR_INVALID_ARG, "block column size < 1");
+  use_device(ctx);
+  cudaStream_t s = as_stream(stream);
+  std::vector<int64_t> key((size_t)nblocks);
+  for (int64_t b = 0; b < nblocks; ++b) {
+    BST_REQUIRE(blk_row[b] >= 0 && blk_row[b] < nbr && blk_col[b] >= 0 && blk_col[b] < nbc,
+                BST_ERR_OUT_OF_RANGE, "block index outside the block grid");
+    key[b] = (int64_t)blk_row[b] * nbc + blk_col[b];
+  }
+  std::vector<int32_t> ord((size_t)nblocks);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return key[x] < key[y]; });
+  std::vector<int32_t> row((size_t)nblocks), col((size_t)nblocks), rowptr((size_t)nbr + 1, 0);
+  std::vector<int64_t> off((size_t)nblocks);
+  int64_t acc = 0;
+  for (int64_t b = 0; b < nblocks; ++b) {
+    const int32_t o = ord[b];
+    BST_REQUIRE(b == 0 || key[o] != key[ord[b - 1]], BST_ERR_DUPLICATE_BLOCK,
+                "a block is listed twice");
+    row[b] = blk_row[o];
+    col[b] = blk_col[o];
+    off[b] = acc;
+    acc += (int64_t)row_blk_sizes[row[b]] * col_blk_sizes[col[b]];
+    rowptr[row[b] + 1]++;
+  }
+  BST_REQUIRE(acc <= INT32_MAX, BST_ERR_OVERFLOW, "more than 2^31-1 elements");
+  for (int32_t i = 0; i < nbr; ++i) rowptr[i + 1] += rowptr[i];
+  auto *m = new bst_matrix();
+  try {
+    m->ctx = ctx;
+    m->arena.ctx = static_cast<bst::Ctx *>(ctx);
+    m->arena.stream = s;
+    m->nbr = nbr;
+    m->nbc = nbc;
+    m->h_rsz.assign(row_blk_sizes, row_blk_sizes + nbr);
+    m->h_csz.assign(col_blk_sizes, col_blk_sizes + nbc);
+    m->nblocks = nblocks;
+    m->nelem = acc;
+    m->rsz = upload(m->arena, m->h_rsz, s);
+    m->csz = upload(m->arena, m->h_csz, s);
+    m->rowptr = upload(m->arena, rowptr, s);
+    m->row = upload(m->arena, row, s);
+    m->col = upload(m->arena, col, s);
+    m->off = upload(m->arena, off, s);
+    m->data = data;
+    BST_CUDA(cudaStreamSynchronize(s));  // the host staging vectors end here
+  } catch (...) {
+    delete m;
+    throw;
+  }
+  *out = m;
+  API_END
+}
+
+bst_status bst_matrix_info(const bst_matrix *m, int32_t *nbr, int32_t *nbc, int64_t *nblocks,
+                           int64_t *nelem) {
+  API_BEGIN
+  BST_REQUIRE(m, BST_ERR_INVALID_ARG, "matrix is NULL");
+  if (nbr) *nbr = m->nbr;
+  if (nbc) *nbc = m->nbc;
+  if (nblocks) *nblocks = m->nblocks;
+  if (nelem) *nelem = m->nelem;
+  API_END
+}
+
+bst_status bst_matrix_get_index(const bst_matrix *m, int32_t *blk_row, int32_t *blk_col,
+                                int64_t *blk_off) {
+  API_BEGIN
+  BST_REQUIRE(m, BST_ERR_INVALID_ARG, "matrix is NULL");
+  use_device(m->ctx);
+  const size_t n = (size_t)m->nblocks;
+  if (n) {
+    if (blk_row) BST_CUDA(cudaMemcpy(blk_row, m->row, 4 * n, cudaMemcpyDeviceToHost));
+    if (blk_col) BST_CUDA(cudaMemcpy(blk_col, m->col, 4 * n, cudaMemcpyDeviceToHost));
+    if (blk_off) BST_CUDA(cudaMemcpy(blk_off, m->off, 8 * n, cudaMemcpyDeviceToHost));
+  }
+  API_END
+}
+
+bst_status bst_matrix_bind_data(bst_matrix *m, double *data) {
+  API_BEGIN
+  BST_REQUIRE(m, BST_ERR_INVALID_ARG, "matrix is NULL");
+  m->data = data;
+  API_END
+}
+
+bst_status bst_matrix_destroy(bst_matrix *m) {
+  API_BEGIN
+  if (!m) return BST_OK;
+  BST_REQUIRE(!m->owned_by_plan, BST_ERR_STATE, "this matrix belongs to a plan");
+  delete m;
+  API_END
+}
+
+bst_status bst_multiply_plan(bst_ctx *ctx, char transa, char transb, const bst_matrix *A,
+                             const bst_matrix *B, const bst_matrix *C_in, double eps,
+                             void *stream, bst_plan **out) {
+  API_BEGIN
+  BST_REQUIRE(ctx && A && B && out, BST_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  const bool ta = transa == 'T' || transa == 't', tb = transb == 'T' || transb == 't';
+  BST_REQUIRE(ta || transa == 'N' || transa == 'n', BST_ERR_INVALID_ARG, "transa must be N or T");
+  BST_REQUIRE(tb || transb == 'N' || transb == 'n', BST_ERR_INVALID_ARG, "transb must be N or T");
+  BST_REQUIRE(eps >= 0.0, BST_ERR_INVALID_ARG, "eps must be >= 0");
+  BST_REQUIRE(A->nblocks == 0 || A->data, BST_ERR_STATE, "A data not bound");
+  BST_REQUIRE(B->nblocks == 0 || B->data, BST_ERR_STATE, "B data not bound");
+  // shapes: block columns of op(A) == block rows of op(B), with equal sizes
+  const std::vector<int32_t> &a_rs = ta ? A->h_csz : A->h_rsz, &a_cs = ta ? A->h_rsz : A->h_csz;
+  const std::vector<int32_t> &b_rs = tb ? B->h_csz : B->h_rsz, &b_cs = tb ? B->h_rsz : B->h_csz;
+  BST_REQUIRE(a_cs == b_rs, BST_ERR_SHAPE_MISMATCH,
+              "inner block sizes of op(A) and op(B) differ");
+  if (C_in) {
+    BST_REQUIRE(C_in->h_rsz == a_rs && C_in->h_csz == b_cs, BST_ERR_SHAPE_MISMATCH,
+                "C_in block grid differs from op(A) rows x op(B) columns");
+  }
+  use_device(ctx);
+  cudaStream_t s = as_stream(stream);
+  auto *p = new bst_plan();
+  try {
+    p->ctx = ctx;
+    p->arena.ctx = static_cast<bst::Ctx *>(ctx);
+    p->arena.stream = s;
+    p->work.ctx = static_cast<bst::Ctx *>(ctx);
+    p->work.stream = s;
+    p->A = A;
+    p->B = B;
+    p->Cin = C_in;
+    p->ta = ta;
+    p->tb = tb;
+    p->eps = eps;
+    p->oa = bst::make_opview(A, ta, p->arena, s);
+    p->ob = bst::make_opview(B, tb, p->arena, s);
+    p->M = p->oa.nr;
+    p->N = p->ob.nc;
+    p->K = p->oa.nc;
+    p->C = new bst_matrix();
+    p->C->ctx = ctx;
+    p->C->owned_by_plan = true;
+    bst::symbolic_phase(p, s);
+  } catch (...) {
+    if (p->C) {
+      p->C->owned_by_plan = false;
+      delete p->C;
+    }
+    delete p;
+    throw;
+  }
+  *out = p;
+  API_END
+}
+
+bst_status bst_plan_result(bst_plan *plan, bst_matrix **C_out) {
+  API_BEGIN
+  BST_REQUIRE(plan && C_out, BST_ERR_INVALID_ARG, "NULL argument");
+  *C_out = plan->C;
+  API_END
+}
+
+bst_status bst_plan_stats(const bst_plan *plan, bst_stats *out) {
+  API_BEGIN
+  BST_REQUIRE(plan && out, BST_ERR_INVALID_ARG, "NULL argument");
+  *out = plan->stats;
+  API_END
+}
+
+bst_status bst_plan_get_stacks(const bst_plan *plan, int32_t *mnk, int64_t *bucket_ptr,
+                               int32_t *a_off, int32_t *b_off, int32_t *c_off) {
+  API_BEGIN
+  BST_REQUIRE(plan, BST_ERR_INVALID_ARG, "plan is NULL");
+  use_device(plan->ctx);
+  int32_t q = 0;
+  const auto &hb = plan->h_bucket_ptr;
+  for (int32_t b = 0; b < plan->nb_all; ++b) {
+    if (hb[b + 1] == hb[b]) continue;
+    const int32_t kc = b % plan->Dk, nc = (b / plan->Dk) % plan->Dn, mc = b / (plan->Dk * plan->Dn);
+    if (mnk) {
+      mnk[3 * q + 0] = plan->m_vals[mc];
+      mnk[3 * q + 1] = plan->n_vals[nc];
+      mnk[3 * q + 2] = plan->k_vals[kc];
+    }
+    if (bucket_ptr) bucket_ptr[q] = hb[b];
+    ++q;
+  }
+  if (bucket_ptr) bucket_ptr[q] = plan->T;
+  const size_t n = (size_t)plan->T;
+  if (n) {
+    if (a_off) BST_CUDA(cudaMemcpy(a_off, plan->s_a, 4 * n, cudaMemcpyDeviceToHost));
+    if (b_off) BST_CUDA(cudaMemcpy(b_off, plan->s_b, 4 * n, cudaMemcpyDeviceToHost));
+    if (c_off) BST_CUDA(cudaMemcpy(c_off, plan->s_c, 4 * n, cudaMemcpyDeviceToHost));
+  }
+  API_END
+}
+
+bst_status bst_multiply_execute(bst_plan *plan, double alpha, double beta, int32_t precision,
+                                int32_t split_k, void *stream) {
+  API_BEGIN
+  BST_REQUIRE(plan, BST_ERR_INVALID_ARG, "plan is NULL");
+  BST_REQUIRE(split_k >= 0 && split_k <= 64, BST_ERR_INVALID_ARG, "split_k must be in 0..64");
+  BST_REQUIRE(std::isfinite(alpha) && std::isfinite(beta), BST_ERR_INVALID_ARG,
+              "alpha and beta must be finite");
+  const bst_matrix *C = plan->C;
+  BST_REQUIRE(C->nelem == 0 || C->data, BST_ERR_STATE, "C_out data not bound");
+  BST_REQUIRE(plan->A->nblocks == 0 || plan->A->data, BST_ERR_STATE, "A data not bound");
+  BST_REQUIRE(plan->B->nblocks == 0 || plan->B->data, BST_ERR_STATE, "B data not bound");
+  const bool read_cin = beta != 0.0 && plan->Cin && plan->Cin->nblocks > 0;
+  BST_REQUIRE(!read_cin || plan->Cin->data, BST_ERR_STATE, "C_in data not bound");
+  use_device(plan->ctx);
+  cudaStream_t s = as_stream(stream);
+  bst::NumArgs a;
+  a.A = plan->A->data;
+  a.B = plan->B->data;
+  a.Cin = read_cin ? plan->Cin->data : nullptr;
+  a.C = C->data;
+  a.alpha = alpha;
+  a.beta = read_cin ? beta : 0.0;
+  int split = 1;
+  switch (precision) {
+    case BST_FP64:
+      split = split_k == 0 ? bst::choose_split(plan, plan->ctx->num_sms) : split_k;
+      bst::execute_fp64(plan, a, split, s);
+      break;
+    case BST_FP64_EMU_BF16:
+      bst::execute_emu_bf16(plan, a, s);
+      break;
+    case BST_TF32X3:
+      bst::execute_tf32x3(plan, a, s);
+      break;
+    default:
+      throw Error{BST_ERR_INVALID_ARG, "unknown precision"};
+  }
+  plan->stats.split_k = split;
+  API_END
+}
+
+bst_status bst_plan_destroy(bst_plan *plan) {
+  API_BEGIN
+  if (!plan) return BST_OK;
+  if (plan->C) {
+    plan->C->owned_by_plan = false;
+    delete plan->C;
+  }
+  delete plan;
+  API_END
+}
+
+}  // extern "C"

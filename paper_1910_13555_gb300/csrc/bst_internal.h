@@ -1,0 +1,236 @@
+// Internal declarations of libbst: handle structs, device views, helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bst.h"
+
+namespace bst {
+
+// ---------------------------------------------------------------------------
+// errors
+
+void set_error(const std::string &msg);
+
+struct Error {
+  bst_status code;
+  std::string msg;
+};
+
+#define BST_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t _e = (call);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      throw ::bst::Error{BST_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)}; \
+  } while (0)
+
+// every kernel launch site ends with BST_CHECK_LAUNCH(): it checks the launch and
+// counts it (bst_kernel_launches)
+void count_launch();
+#define BST_CHECK_LAUNCH()          \
+  do {                              \
+    ::bst::count_launch();          \
+    BST_CUDA(cudaGetLastError());   \
+  } while (0)
+
+#define BST_REQUIRE(cond, code, msg)                                      \
+  do {                                                                    \
+    if (!(cond)) throw ::bst::Error{(code), std::string(msg)};            \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device memory through the context's allocator
+
+struct Ctx;
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+// A set of device allocations released together (by a plan, a matrix, ...).
+struct Arena {
+  Ctx *ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<DevBuf> bufs;
+  void *alloc(size_t bytes);
+  template <class T>
+  T *alloc_n(size_t n) {
+    return static_cast<T *>(alloc(sizeof(T) * (n ? n : 1)));
+  }
+  void release_all();
+  ~Arena() { release_all(); }
+};
+
+}  // namespace bst
+
+struct bst_ctx {
+  int device = 0;
+  bst_alloc_fn alloc = nullptr;
+  bst_free_fn free_fn = nullptr;
+  void *user = nullptr;
+  int num_sms = 0;
+  size_t max_smem_optin = 0;
+};
+
+namespace bst {
+struct Ctx : bst_ctx {};
+}  // namespace bst
+
+// Device view of a block-sparse matrix in canonical CSR order.  Blocks need not be
+// packed in CSR order (a tensor view keeps the tensor's packing): off[] gives each
+// block's element offset into data.  Element (p, q) of block b sits at
+// data[off[b] + p * ld + q] with ld = column size of the block (row-major).
+struct bst_matrix {
+  bst_ctx *ctx = nullptr;
+  int32_t nbr = 0, nbc = 0;
+  std::vector<int32_t> h_rsz, h_csz;  // host copies of block sizes
+  int64_t nblocks = 0;
+  int64_t nelem = 0;
+  // device arrays (owned by `arena` unless borrowed)
+  int32_t *rsz = nullptr, *csz = nullptr;
+  int32_t *rowptr = nullptr;  // nbr + 1
+  int32_t *row = nullptr, *col = nullptr;
+  int64_t *off = nullptr;
+  double *data = nullptr;
+  bst::Arena arena;
+  bool owned_by_plan = false;
+};
+
+struct bst_tensor {
+  bst_ctx *ctx = nullptr;
+  int32_t rank = 0;
+  std::vector<int32_t> h_nblk;
+  std::vector<std::vector<int32_t>> h_sz;
+  int64_t nblocks = 0, nelem = 0;
+  std::vector<int32_t> h_idx;  // canonical, nblocks * rank (host copy)
+  std::vector<int64_t> h_off;
+  int32_t *idx = nullptr;      // device, canonical
+  int64_t *off = nullptr;      // device
+  int32_t *sz = nullptr;       // device, concatenated per-mode sizes
+  double *data = nullptr;
+  bst::Arena arena;
+  bool owned_by_plan = false;
+};
+
+namespace bst {
+
+// ---------------------------------------------------------------------------
+// primitives (prims.cu)
+
+// exclusive scan of n int32 counts into int64 (out has n + 1 entries, out[n] = total)
+void exscan_i32_i64(const int32_t *in, int64_t *out, int64_t n, Arena &ar, cudaStream_t s);
+// exclusive scan int64 -> int64 (n + 1 outputs)
+void exscan_i64(const int64_t *in, int64_t *out, int64_t n, Arena &ar, cudaStream_t s);
+// exclusive scan int32 -> int32 (n + 1 outputs); caller guarantees no overflow
+void exscan_i32(const int32_t *in, int32_t *out, int64_t n, Arena &ar, cudaStream_t s);
+
+// Stable counting sort of n items by a key in [0, nkeys): perm[out_pos] = in_pos and
+// key_ptr[k] = first output position of key k (nkeys + 1 entries).
+void stable_partition(const int32_t *keys, int64_t n, int32_t nkeys, int32_t *perm,
+                      int32_t *key_ptr, Arena &ar, cudaStream_t s);
+
+// Stable LSD radix sort of n (key, index) pairs on `bits` low bits of key;
+// returns the permutation (out_pos -> in_pos).
+void radix_sort_perm(const uint64_t *keys, int64_t n, int bits, int32_t *perm, Arena &ar,
+                     cudaStream_t s);
+
+void iota_i32(int32_t *p, int64_t n, cudaStream_t s);
+void fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s);
+void gather_i32(const int32_t *src, const int32_t *idx, int32_t *dst, int64_t n, cudaStream_t s);
+
+template <class T>
+T read_scalar(const T *dptr, cudaStream_t s) {
+  T v;
+  BST_CUDA(cudaMemcpyAsync(&v, dptr, sizeof(T), cudaMemcpyDeviceToHost, s));
+  BST_CUDA(cudaStreamSynchronize(s));
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// block norms (symbolic.cu): Frobenius norm of each block of m, in its canonical order
+void block_norms(const bst_matrix *m, double *norms, cudaStream_t s);
+
+// A view of op(X) as CSR over its block rows (symbolic.cu)
+struct OpView {
+  int32_t nr = 0, nc = 0;
+  const int32_t *rs = nullptr, *cs = nullptr;  // device block sizes of op(X)
+  const int32_t *rowptr = nullptr;             // nr + 1
+  const int32_t *col = nullptr;                // block column of op(X) per entry
+  const int32_t *blk = nullptr;                // stored block id per entry (null = identity)
+  std::vector<int32_t> h_rs, h_cs;
+  bool trans = false;
+};
+OpView make_opview(const bst_matrix *m, bool trans, Arena &ar, cudaStream_t s);
+
+}  // namespace bst
+
+// ---------------------------------------------------------------------------
+// plans
+
+struct bst_plan {
+  bst_ctx *ctx = nullptr;
+  const bst_matrix *A = nullptr, *B = nullptr, *Cin = nullptr;
+  bool ta = false, tb = false;
+  double eps = 0.0;
+  bst::OpView oa, ob;
+  // C_out (pattern owned by the plan)
+  bst_matrix *C = nullptr;
+  int32_t M = 0, N = 0, K = 0;
+  // size classes
+  std::vector<int32_t> m_vals, n_vals, k_vals;  // distinct sizes, ascending
+  int32_t Dm = 0, Dn = 0, Dk = 0;
+  int32_t *m_cls = nullptr, *n_cls = nullptr, *k_cls = nullptr;  // per block row/col/inner
+  int32_t *cls_m = nullptr, *cls_n = nullptr;  // (m,n) class id -> m, n
+  int32_t *kval = nullptr;                     // k class -> k
+  // symbolic results (device)
+  int32_t *c_cin = nullptr;    // per C block: C_in block id or -1
+  int32_t *c_cls = nullptr;    // per C block: (m,n) class
+  int64_t T = 0;               // kept products
+  int32_t *t_start = nullptr;  // per C block: first triple in (i,j,k) order (nnzC + 1)
+  // bucketed stacks
+  int32_t nb_all = 0;                 // Dm*Dn*Dk buckets (incl. empty)
+  std::vector<int64_t> h_bucket_ptr;  // nb_all + 1
+  int32_t *s_a = nullptr, *s_b = nullptr, *s_c = nullptr;  // element offsets (int32)
+  int32_t *s_cb = nullptr;            // C block of each entry
+  int32_t *s_k = nullptr;             // k block index of each entry
+  int32_t *run_start = nullptr;       // nnzC * Dk: first entry of (C block, k class) run
+  int32_t *run_len = nullptr;         // nnzC * Dk
+  // numeric task list: C blocks sorted by (m,n) class
+  int32_t *task_c = nullptr;
+  std::vector<int32_t> h_class_ptr;   // Dm*Dn + 1
+  int32_t *class_ptr = nullptr;
+  // stats
+  bst_stats stats{};
+  // contraction glue (remap.cu)
+  struct Contract *contract = nullptr;
+  bst::Arena arena;
+  bst::Arena work;  // execute-time workspaces (split-k partials, emulation slices)
+  size_t work_bytes = 0;
+};
+
+namespace bst {
+
+// symbolic phase (symbolic.cu): fills everything in the plan from oa/ob/Cin
+void symbolic_phase(bst_plan *p, cudaStream_t s);
+
+// numeric phase (numeric_fp64.cu / numeric_emu.cu)
+struct NumArgs {
+  const double *A, *B, *Cin;
+  double *C;
+  double alpha, beta;
+};
+void execute_fp64(bst_plan *p, const NumArgs &a, int split, cudaStream_t s);
+void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s);
+void execute_tf32x3(bst_plan *p, const NumArgs &a, cudaStream_t s);
+void adjoint_fp64(bst_plan *p, const double *A, const double *B, const double *dC, double *dA,
+                  double *dB, double alpha, cudaStream_t s);
+void scale_cin_grad(bst_plan *p, const double *dC, double *dCin, double beta, cudaStream_t s);
+
+int choose_split(const bst_plan *p, int num_sms);
+
+}  // namespace bst

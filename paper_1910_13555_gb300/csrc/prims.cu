@@ -1,0 +1,267 @@
+// Device primitives of the symbolic phase: exclusive scans, a stable counting sort
+// (partition by a small integer key) and an LSD radix sort built on it.
+//
+// All of them are deterministic: the counting sort is stable because every warp
+// owns one contiguous segment of the input and emits it in order, with the ranks of
+// equal keys inside a 32-element batch taken from __match_any_sync.
+#include "bst_internal.h"
+
+namespace bst {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T o = __shfl_up_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) >= d) v += o;
+  }
+  return v;
+}
+
+// block-wide exclusive scan of one value per thread; returns the exclusive prefix,
+// *total gets the block sum.
+template <class T>
+__device__ __forceinline__ T block_excl_scan(T v, T *total) {
+  constexpr int NW = kScanThreads / 32;
+  __shared__ T warp_sums[NW];
+  __shared__ T tot;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T inc = warp_incl_scan(v);
+  if (lane == 31) warp_sums[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    T w = lane < NW ? warp_sums[lane] : T(0);
+    T wi = warp_incl_scan(w);
+    if (lane < NW) warp_sums[lane] = wi - w;
+    if (lane == NW - 1) tot = wi;
+  }
+  __syncthreads();
+  T excl = inc - v + warp_sums[wid];
+  *total = tot;
+  __syncthreads();  // the shared slots are reused by the next call
+  return excl;
+}
+
+template <class TI, class TO>
+__global__ void k_tile_sums(const TI *__restrict__ in, int64_t n, TO *__restrict__ sums) {
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  TO acc = 0;
+#pragma unroll
+  for (int r = 0; r < kScanItems; ++r) {
+    int64_t i = base + (int64_t)r * kScanThreads + threadIdx.x;
+    if (i < n) acc += (TO)in[i];
+  }
+  TO total;
+  block_excl_scan<TO>(acc, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// single-CTA exclusive scan of the tile sums (in place), carry across chunks
+template <class TO>
+__global__ void k_scan_sums(TO *sums, int64_t nt) {
+  TO carry = 0;
+  for (int64_t c0 = 0; c0 < nt; c0 += kScanThreads) {
+    int64_t i = c0 + threadIdx.x;
+    TO v = i < nt ? sums[i] : TO(0);
+    TO total;
+    TO ex = block_excl_scan<TO>(v, &total);
+    if (i < nt) sums[i] = ex + carry;
+    carry += total;
+  }
+}
+
+template <class TI, class TO>
+__global__ void k_tile_scan(const TI *__restrict__ in, int64_t n, const TO *__restrict__ sums,
+                            TO *__restrict__ out) {
+  // each thread takes kScanItems consecutive elements
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  TO v[kScanItems];
+  TO acc = 0;
+#pragma unroll
+  for (int r = 0; r < kScanItems; ++r) {
+    int64_t i = base + r;
+    v[r] = i < n ? (TO)in[i] : TO(0);
+    acc += v[r];
+  }
+  TO total;
+  TO ex = block_excl_scan<TO>(acc, &total) + sums[blockIdx.x];
+#pragma unroll
+  for (int r = 0; r < kScanItems; ++r) {
+    int64_t i = base + r;
+    if (i < n) out[i] = ex;
+    ex += v[r];
+  }
+  // the grand total goes to out[n]
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) out[n] = ex;
+}
+
+template <class TI, class TO>
+void exscan_impl(const TI *in, TO *out, int64_t n, Arena &ar, cudaStream_t s) {
+  if (n == 0) {
+    BST_CUDA(cudaMemsetAsync(out, 0, sizeof(TO), s));
+    return;
+  }
+  int64_t nt = (n + kScanTile - 1) / kScanTile;
+  TO *sums = ar.alloc_n<TO>((size_t)nt);
+  k_tile_sums<TI, TO><<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, sums);
+  BST_CHECK_LAUNCH();
+  k_scan_sums<TO><<<1, kScanThreads, 0, s>>>(sums, nt);
+  BST_CHECK_LAUNCH();
+  k_tile_scan<TI, TO><<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, sums, out);
+  BST_CHECK_LAUNCH();
+}
+
+// ---- stable counting sort ------------------------------------------------------
+
+__global__ void k_part_hist(const int32_t *__restrict__ keys, int64_t n, int64_t L, int64_t G,
+                            int32_t *__restrict__ hist) {
+  const int lane = threadIdx.x & 31;
+  int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (g >= G) return;
+  int64_t p0 = g * L, p1 = min(n, p0 + L);
+  for (int64_t b = p0; b < p1; b += 32) {
+    int64_t p = b + lane;
+    unsigned act = __ballot_sync(0xffffffffu, p < p1);
+    if (p < p1) {
+      int32_t key = keys[p];
+      unsigned peers = __match_any_sync(act, key);
+      if ((int)(__ffs(peers) - 1) == lane) atomicAdd(&hist[(int64_t)key * G + g], __popc(peers));
+    }
+  }
+}
+
+__global__ void k_part_keyptr(const int32_t *__restrict__ base, int32_t nkeys, int64_t G,
+                              int32_t *__restrict__ key_ptr) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k <= nkeys) key_ptr[k] = base[k * G];
+}
+
+__global__ void k_part_scatter(const int32_t *__restrict__ keys, int64_t n, int64_t L, int64_t G,
+                               int32_t *__restrict__ base, int32_t *__restrict__ perm) {
+  const int lane = threadIdx.x & 31;
+  int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (g >= G) return;
+  int64_t p0 = g * L, p1 = min(n, p0 + L);
+  for (int64_t b = p0; b < p1; b += 32) {
+    int64_t p = b + lane;
+    unsigned act = __ballot_sync(0xffffffffu, p < p1);
+    int32_t key = 0;
+    unsigned peers = 0;
+    int32_t pos = 0;
+    if (p < p1) {
+      key = keys[p];
+      peers = __match_any_sync(act, key);
+      unsigned lt = peers & ((1u << lane) - 1u);
+      pos = base[(int64_t)key * G + g] + __popc(lt);
+      perm[pos] = (int32_t)p;
+    }
+    __syncwarp();
+    if (p < p1 && (int)(__ffs(peers) - 1) == lane) base[(int64_t)key * G + g] += __popc(peers);
+    __syncwarp();
+  }
+}
+
+__global__ void k_iota(int32_t *p, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = (int32_t)i;
+}
+
+__global__ void k_fill(int32_t *p, int32_t v, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+__global__ void k_gather(const int32_t *__restrict__ src, const int32_t *__restrict__ idx,
+                         int32_t *__restrict__ dst, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
+__global__ void k_digits(const uint64_t *__restrict__ keys, const int32_t *__restrict__ perm,
+                         int64_t n, int shift, int32_t *__restrict__ dig) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dig[i] = (int32_t)((keys[perm[i]] >> shift) & 0xffu);
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void exscan_i32_i64(const int32_t *in, int64_t *out, int64_t n, Arena &ar, cudaStream_t s) {
+  exscan_impl<int32_t, int64_t>(in, out, n, ar, s);
+}
+void exscan_i64(const int64_t *in, int64_t *out, int64_t n, Arena &ar, cudaStream_t s) {
+  exscan_impl<int64_t, int64_t>(in, out, n, ar, s);
+}
+void exscan_i32(const int32_t *in, int32_t *out, int64_t n, Arena &ar, cudaStream_t s) {
+  exscan_impl<int32_t, int32_t>(in, out, n, ar, s);
+}
+
+void iota_i32(int32_t *p, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_iota<<<nblk(n, 256), 256, 0, s>>>(p, n);
+  BST_CHECK_LAUNCH();
+}
+void fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_fill<<<nblk(n, 256), 256, 0, s>>>(p, v, n);
+  BST_CHECK_LAUNCH();
+}
+void gather_i32(const int32_t *src, const int32_t *idx, int32_t *dst, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_gather<<<nblk(n, 256), 256, 0, s>>>(src, idx, dst, n);
+  BST_CHECK_LAUNCH();
+}
+
+void stable_partition(const int32_t *keys, int64_t n, int32_t nkeys, int32_t *perm,
+                      int32_t *key_ptr, Arena &ar, cudaStream_t s) {
+  BST_REQUIRE(nkeys >= 1, BST_ERR_INVALID_ARG, "stable_partition: nkeys < 1");
+  if (n == 0) {
+    BST_CUDA(cudaMemsetAsync(key_ptr, 0, sizeof(int32_t) * ((size_t)nkeys + 1), s));
+    return;
+  }
+  // segment length: at least 256 items per warp, and at most 2^24 histogram cells
+  int64_t L = 256;
+  const int64_t max_cells = int64_t(1) << 24;
+  while ((int64_t)nkeys * ((n + L - 1) / L) > max_cells) L *= 2;
+  int64_t G = (n + L - 1) / L;
+  int64_t cells = (int64_t)nkeys * G;
+  int32_t *hist = ar.alloc_n<int32_t>((size_t)cells);
+  int32_t *base = ar.alloc_n<int32_t>((size_t)cells + 1);
+  BST_CUDA(cudaMemsetAsync(hist, 0, sizeof(int32_t) * (size_t)cells, s));
+  const int wpb = 8;
+  k_part_hist<<<nblk(G, wpb), 32 * wpb, 0, s>>>(keys, n, L, G, hist);
+  BST_CHECK_LAUNCH();
+  exscan_i32(hist, base, cells, ar, s);
+  // key_ptr[k] = base[k * G]; the entry for k = nkeys reads base[cells] = n
+  k_part_keyptr<<<nblk((int64_t)nkeys + 1, 256), 256, 0, s>>>(base, nkeys, G, key_ptr);
+  BST_CHECK_LAUNCH();
+  k_part_scatter<<<nblk(G, wpb), 32 * wpb, 0, s>>>(keys, n, L, G, base, perm);
+  BST_CHECK_LAUNCH();
+}
+
+void radix_sort_perm(const uint64_t *keys, int64_t n, int bits, int32_t *perm, Arena &ar,
+                     cudaStream_t s) {
+  iota_i32(perm, n, s);
+  if (n <= 1 || bits <= 0) return;
+  int32_t *dig = ar.alloc_n<int32_t>((size_t)n);
+  int32_t *p2 = ar.alloc_n<int32_t>((size_t)n);
+  int32_t *cur = ar.alloc_n<int32_t>((size_t)n);
+  int32_t *kp = ar.alloc_n<int32_t>(257);
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_digits<<<nblk(n, 256), 256, 0, s>>>(keys, perm, n, shift, dig);
+    BST_CHECK_LAUNCH();
+    stable_partition(dig, n, 256, p2, kp, ar, s);
+    // new perm[i] = perm[p2[i]]
+    gather_i32(perm, p2, cur, n, s);
+    BST_CUDA(cudaMemcpyAsync(perm, cur, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+  }
+}
+
+}  // namespace bst
