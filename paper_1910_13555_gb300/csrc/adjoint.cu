@@ -1,0 +1,227 @@
+// Adjoint of the block-sparse multiply (sampled block-sparse products), native FP64.
+//
+// For C_out = alpha op(A) op(B) + beta C_in with the filter decisions held fixed (a
+// kept product stays kept; its derivative through the filter threshold is zero):
+//     dop(A)_ik = alpha sum_{j: (i,k,j) kept} dC_ij op(B)_kj^T   on pattern(A)
+//     dop(B)_kj = alpha sum_{i: (i,k,j) kept} op(A)_ik^T dC_ij   on pattern(B)
+//     dC_in     = beta dC                                        on pattern(C_in)
+// The paper defines only the forward product; this is its exact adjoint.
+//
+// Each output block has one owner warp (no atomics): the plan's stack entries are
+// grouped by stored A block and by stored B block once (stable counting sort, cached
+// in the plan), and warp `a` sums over the entries of A block `a`.  Lanes own output
+// elements (m x k of dop(A), k x n of dop(B)) in passes of 256; every block product
+// reads its dC block and the other operand's block from L1/L2.
+#include <algorithm>
+
+#include "bst_internal.h"
+
+namespace bst {
+
+struct AdjState {
+  Arena ar;
+  int32_t *by_a = nullptr, *a_ptr = nullptr;  // entries grouped by stored A block
+  int32_t *by_b = nullptr, *b_ptr = nullptr;  // entries grouped by stored B block
+};
+
+namespace {
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+constexpr int RA = 8;  // outputs per lane per pass
+
+struct AdjArgs {
+  const double *A, *B, *dC;
+  double *dA, *dB;
+  double alpha;
+  int ta, tb;
+  const int32_t *grp, *ptr;        // entries of each output block
+  const int32_t *s_a, *s_b, *s_c, *s_cb;
+  const int32_t *c_row, *c_col, *c_rsz, *c_csz;  // C block index and sizes
+  // stored blocks of the output side
+  int64_t nblocks;
+  const int32_t *row, *col, *rsz, *csz;
+  const int64_t *off;
+};
+
+// dop(A) for stored A block b: lanes own (p, l) of the m x k op block
+__global__ void k_adj_a(AdjArgs P) {
+  const int lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (b >= P.nblocks) return;
+  const int R = P.rsz[P.row[b]], Cc = P.csz[P.col[b]];
+  const int m = P.ta ? Cc : R, k = P.ta ? R : Cc;
+  const int e0 = P.ptr[b], e1 = P.ptr[b + 1];
+  double *out = P.dA + P.off[b];
+  for (int o0 = 0; o0 < m * k; o0 += 32 * RA) {
+    double acc[RA];
+#pragma unroll
+    for (int r = 0; r < RA; ++r) acc[r] = 0.0;
+    for (int q0 = e0; q0 < e1; ++q0) {
+      const int e = P.grp[q0];
+      const int c = P.s_cb[e];
+      const int n = P.c_csz[P.c_col[c]];
+      const double *g = P.dC + P.s_c[e];   // m x n
+      const double *bb = P.B + P.s_b[e];   // op(B): k x n
+      const int b_sl = P.tb ? 1 : n, b_sq = P.tb ? k : 1;
+#pragma unroll
+      for (int r = 0; r < RA; ++r) {
+        const int o = o0 + lane + 32 * r;
+        if (o < m * k) {
+          const int p = o / k, l = o % k;
+          double s = acc[r];
+          for (int q = 0; q < n; ++q) s = fma(__ldg(g + p * n + q), __ldg(bb + l * b_sl + q * b_sq), s);
+          acc[r] = s;
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RA; ++r) {
+      const int o = o0 + lane + 32 * r;
+      if (o < m * k) {
+        const int p = o / k, l = o % k;
+        out[P.ta ? l * m + p : p * k + l] = P.alpha * acc[r];
+      }
+    }
+  }
+}
+
+// dop(B) for stored B block b: lanes own (l, q) of the k x n op block
+__global__ void k_adj_b(AdjArgs P) {
+  const int lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (b >= P.nblocks) return;
+  const int R = P.rsz[P.row[b]], Cc = P.csz[P.col[b]];
+  const int k = P.tb ? Cc : R, n = P.tb ? R : Cc;
+  const int e0 = P.ptr[b], e1 = P.ptr[b + 1];
+  double *out = P.dB + P.off[b];
+  for (int o0 = 0; o0 < k * n; o0 += 32 * RA) {
+    double acc[RA];
+#pragma unroll
+    for (int r = 0; r < RA; ++r) acc[r] = 0.0;
+    for (int q0 = e0; q0 < e1; ++q0) {
+      const int e = P.grp[q0];
+      const int c = P.s_cb[e];
+      const int m = P.c_rsz[P.c_row[c]];
+      const double *g = P.dC + P.s_c[e];  // m x n
+      const double *aa = P.A + P.s_a[e];  // op(A): m x k
+      const int a_sp = P.ta ? 1 : k, a_sl = P.ta ? m : 1;
+#pragma unroll
+      for (int r = 0; r < RA; ++r) {
+        const int o = o0 + lane + 32 * r;
+        if (o < k * n) {
+          const int l = o / n, q = o % n;
+          double s = acc[r];
+          for (int p = 0; p < m; ++p) s = fma(__ldg(aa + p * a_sp + l * a_sl), __ldg(g + p * n + q), s);
+          acc[r] = s;
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RA; ++r) {
+      const int o = o0 + lane + 32 * r;
+      if (o < k * n) {
+        const int l = o / n, q = o % n;
+        out[P.tb ? q * k + l : l * n + q] = P.alpha * acc[r];
+      }
+    }
+  }
+}
+
+// dC_in = beta dC on the C_in blocks (one warp per C block that carries a C_in block)
+__global__ void k_adj_cin(int64_t nc, const int32_t *c_cin, const int64_t *c_off,
+                          const int64_t *cin_off, const int32_t *c_row, const int32_t *c_col,
+                          const int32_t *rsz, const int32_t *csz, const double *dC, double *dCin,
+                          double beta) {
+  const int lane = threadIdx.x & 31;
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= nc) return;
+  const int ci = c_cin[c];
+  if (ci < 0) return;
+  const int len = rsz[c_row[c]] * csz[c_col[c]];
+  for (int e = lane; e < len; e += 32) dCin[cin_off[ci] + e] = beta * dC[c_off[c] + e];
+}
+
+}  // namespace
+
+void adj_state_free(bst_plan *p) {
+  delete p->adj;
+  p->adj = nullptr;
+}
+
+void adjoint_fp64(bst_plan *p, const double *A, const double *B, const double *dC, double *dA,
+                  double *dB, double alpha, cudaStream_t s) {
+  const bst_matrix *Am = p->A, *Bm = p->B;
+  if (!p->adj) {
+    p->adj = new AdjState();
+    AdjState &S = *p->adj;
+    S.ar.ctx = static_cast<Ctx *>(p->ctx);
+    S.ar.stream = s;
+    Arena scratch;
+    scratch.ctx = S.ar.ctx;
+    scratch.stream = s;
+    S.by_a = S.ar.alloc_n<int32_t>((size_t)p->T);
+    S.a_ptr = S.ar.alloc_n<int32_t>((size_t)Am->nblocks + 1);
+    S.by_b = S.ar.alloc_n<int32_t>((size_t)p->T);
+    S.b_ptr = S.ar.alloc_n<int32_t>((size_t)Bm->nblocks + 1);
+    stable_partition(p->s_ab, p->T, (int32_t)std::max<int64_t>(Am->nblocks, 1), S.by_a, S.a_ptr,
+                     scratch, s);
+    stable_partition(p->s_bb, p->T, (int32_t)std::max<int64_t>(Bm->nblocks, 1), S.by_b, S.b_ptr,
+                     scratch, s);
+    BST_CUDA(cudaStreamSynchronize(s));
+  }
+  AdjState &S = *p->adj;
+  AdjArgs P{};
+  P.A = A;
+  P.B = B;
+  P.dC = dC;
+  P.dA = dA;
+  P.dB = dB;
+  P.alpha = alpha;
+  P.ta = p->ta;
+  P.tb = p->tb;
+  P.s_a = p->s_a;
+  P.s_b = p->s_b;
+  P.s_c = p->s_c;
+  P.s_cb = p->s_cb;
+  P.c_row = p->C->row;
+  P.c_col = p->C->col;
+  P.c_rsz = p->C->rsz;
+  P.c_csz = p->C->csz;
+  const int wpb = 8;
+  if (Am->nblocks > 0 && dA) {
+    P.grp = S.by_a;
+    P.ptr = S.a_ptr;
+    P.nblocks = Am->nblocks;
+    P.row = Am->row;
+    P.col = Am->col;
+    P.rsz = Am->rsz;
+    P.csz = Am->csz;
+    P.off = Am->off;
+    k_adj_a<<<nblk(Am->nblocks, wpb), 32 * wpb, 0, s>>>(P);
+    BST_CHECK_LAUNCH();
+  }
+  if (Bm->nblocks > 0 && dB) {
+    P.grp = S.by_b;
+    P.ptr = S.b_ptr;
+    P.nblocks = Bm->nblocks;
+    P.row = Bm->row;
+    P.col = Bm->col;
+    P.rsz = Bm->rsz;
+    P.csz = Bm->csz;
+    P.off = Bm->off;
+    k_adj_b<<<nblk(Bm->nblocks, wpb), 32 * wpb, 0, s>>>(P);
+    BST_CHECK_LAUNCH();
+  }
+}
+
+void scale_cin_grad(bst_plan *p, const double *dC, double *dCin, double beta, cudaStream_t s) {
+  const int64_t nc = p->C->nblocks;
+  if (!p->Cin || !dCin || nc == 0) return;
+  const int wpb = 8;
+  k_adj_cin<<<nblk(nc, wpb), 32 * wpb, 0, s>>>(nc, p->c_cin, p->C->off, p->Cin->off, p->C->row,
+                                               p->C->col, p->C->rsz, p->C->csz, dC, dCin, beta);
+  BST_CHECK_LAUNCH();
+}
+
+}  // namespace bst

@@ -362,6 +362,10 @@ bst_status bst_multiply_execute(bst_plan *plan, double alpha, double beta, int32
   BST_REQUIRE(split_k >= 0 && split_k <= 64, BST_ERR_INVALID_ARG, "split_k must be in 0..64");
   BST_REQUIRE(std::isfinite(alpha) && std::isfinite(beta), BST_ERR_INVALID_ARG,
               "alpha and beta must be finite");
+  use_device(plan->ctx);
+  if (plan->contract)
+    bst::contract_prepare(plan, beta != 0.0 && plan->Cin && plan->Cin->nblocks > 0,
+                          as_stream(stream));
   const bst_matrix *C = plan->C;
   BST_REQUIRE(C->nelem == 0 || C->data, BST_ERR_STATE, "C_out data not bound");
   BST_REQUIRE(plan->A->nblocks == 0 || plan->A->data, BST_ERR_STATE, "A data not bound");
@@ -392,17 +396,44 @@ bst_status bst_multiply_execute(bst_plan *plan, double alpha, double beta, int32
     default:
       throw Error{BST_ERR_INVALID_ARG, "unknown precision"};
   }
+  if (plan->contract) bst::contract_finish(plan, s);
   plan->stats.split_k = split;
+  API_END
+}
+
+bst_status bst_plan_adjoint(bst_plan *plan, const double *dC, double *dA, double *dB,
+                            double *dC_in, double alpha, double beta, void *stream) {
+  API_BEGIN
+  BST_REQUIRE(plan, BST_ERR_INVALID_ARG, "plan is NULL");
+  BST_REQUIRE(std::isfinite(alpha) && std::isfinite(beta), BST_ERR_INVALID_ARG,
+              "alpha and beta must be finite");
+  BST_REQUIRE(plan->C->nelem == 0 || dC, BST_ERR_INVALID_ARG, "dC is NULL");
+  BST_REQUIRE(plan->contract || plan->A->nblocks == 0 || plan->A->data, BST_ERR_STATE,
+              "A data not bound");
+  BST_REQUIRE(plan->contract || plan->B->nblocks == 0 || plan->B->data, BST_ERR_STATE,
+              "B data not bound");
+  use_device(plan->ctx);
+  cudaStream_t s = as_stream(stream);
+  if (plan->contract) {
+    bst::contract_adjoint(plan, dC, dA, dB, dC_in, alpha, beta, s);
+    return BST_OK;
+  }
+  bst::adjoint_fp64(plan, plan->A->data, plan->B->data, dC, dA, dB, alpha, s);
+  bst::scale_cin_grad(plan, dC, dC_in, beta, s);
   API_END
 }
 
 bst_status bst_plan_destroy(bst_plan *plan) {
   API_BEGIN
   if (!plan) return BST_OK;
+  bst::emu_state_free(plan);
+  bst::adj_state_free(plan);
   if (plan->C) {
     plan->C->owned_by_plan = false;
     delete plan->C;
   }
+  plan->C = nullptr;
+  bst::contract_free(plan);
   delete plan;
   API_END
 }

@@ -172,6 +172,12 @@ OpView make_opview(const bst_matrix *m, bool trans, Arena &ar, cudaStream_t s);
 // ---------------------------------------------------------------------------
 // plans
 
+namespace bst {
+struct EmuState;
+struct AdjState;
+struct Contract;
+}  // namespace bst
+
 struct bst_plan {
   bst_ctx *ctx = nullptr;
   const bst_matrix *A = nullptr, *B = nullptr, *Cin = nullptr;
@@ -198,6 +204,7 @@ struct bst_plan {
   int32_t *s_a = nullptr, *s_b = nullptr, *s_c = nullptr;  // element offsets (int32)
   int32_t *s_cb = nullptr;            // C block of each entry
   int32_t *s_k = nullptr;             // k block index of each entry
+  int32_t *s_ab = nullptr, *s_bb = nullptr;  // stored A / B block of each entry
   int32_t *run_start = nullptr;       // nnzC * Dk: first entry of (C block, k class) run
   int32_t *run_len = nullptr;         // nnzC * Dk
   // numeric task list: C blocks sorted by (m,n) class
@@ -206,8 +213,11 @@ struct bst_plan {
   int32_t *class_ptr = nullptr;
   // stats
   bst_stats stats{};
+  // emulated-precision state (numeric_emu.cu), built on first use
+  bst::EmuState *emu = nullptr;
+  bst::AdjState *adj = nullptr;  // adjoint grouping of the stacks (adjoint.cu)
   // contraction glue (remap.cu)
-  struct Contract *contract = nullptr;
+  bst::Contract *contract = nullptr;
   bst::Arena arena;
   bst::Arena work;  // execute-time workspaces (split-k partials, emulation slices)
   size_t work_bytes = 0;
@@ -227,6 +237,14 @@ struct NumArgs {
 void execute_fp64(bst_plan *p, const NumArgs &a, int split, cudaStream_t s);
 void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s);
 void execute_tf32x3(bst_plan *p, const NumArgs &a, cudaStream_t s);
+void emu_state_free(bst_plan *p);
+void adj_state_free(bst_plan *p);
+// contractions (contract.cu)
+void contract_prepare(bst_plan *p, bool read_cin, cudaStream_t s);
+void contract_finish(bst_plan *p, cudaStream_t s);
+void contract_adjoint(bst_plan *p, const double *dR, double *dT1, double *dT2, double *dRin,
+                      double alpha, double beta, cudaStream_t s);
+void contract_free(bst_plan *p);
 void adjoint_fp64(bst_plan *p, const double *A, const double *B, const double *dC, double *dA,
                   double *dB, double alpha, cudaStream_t s);
 void scale_cin_grad(bst_plan *p, const double *dC, double *dCin, double beta, cudaStream_t s);

@@ -1,0 +1,761 @@
+// Numeric phase on the tensor cores: FP64 emulated with BF16 slices (Ozaki scheme),
+// and a 3xTF32 compensated path.
+//
+// Emulated FP64 (BST_FP64_EMU_BF16).  The error-free splitting of Ozaki, Ogita, Oishi
+// and Rump (Numer. Algorithms 59, 2012) cuts every operand into slices whose pairwise
+// products a low-precision unit computes exactly.  Here, for each block row p of every
+// op(A) block (block column q of every op(B) block), the largest exponent E of the row
+// fixes the scale; the row is written as fixed point with 42 fraction bits,
+//     a = 2^E * sum_{s=0..5} d_s 2^{-7(s+1)},   d_s integers, |d_0| <= 128, |d_s| <= 127,
+// so every digit is exact in BF16.  A digit product d_s e_t is exact in FP32, and any
+// sum of at most 6 * 160 of them stays below 2^24, so the tensor core's FP32
+// accumulation is exact for up to 160 inner elements.  Products are grouped by level
+// w = s + t; levels w <= 5 are kept (21 of the 36 slice products; the dropped ones
+// weigh at most about 2^-42 of the scale).  After each block product (or 160-element
+// segment of it) the level sums become one exact integer
+//     I = sum_w D_w 2^{7 (5 - w)}          (|I| < 2^60)
+// in units of 2^{ea + eb - 49} (ea, eb: the row / column scales of this block pair),
+// which is shifted (with rounding) to the C element's common scale 2^{ref - 49 + G}
+// (ref: the largest ea + eb over the element's products; G guard bits against int64
+// overflow) and added into an int64 accumulator.  The result is exact up to the digit truncation and one rounding per
+// shift; it is turned into FP64 by an integer-only, round-to-nearest-even conversion
+// (IEEE 754 binary64 encoding), so C is formed in FP64 without FP64 multiply-adds --
+// on GB300 the FP64 pipe runs at 1/64 of the FP32 rate.
+//
+// 3xTF32 (BST_TF32X3), after Ootomo and Yokota (IJHPCA 2022): x = hi + lo with hi, lo
+// TF32; C += hi*hi + hi*lo + lo*hi on the TF32 tensor cores, FP32 accumulation over
+// the whole C block, then converted to FP64 and combined with alpha, beta.
+//
+// Both use warp-level mma.sync tiles (m16n8k16 BF16, m16n8k8 TF32): one warp owns a
+// 16-row x 16-column tile of one C block (so no two warps write the same element),
+// and the operand slices are staged once per execute in a padded, permuted layout that
+// makes every fragment a single 8-byte load (inner dimension padded with zeros to the
+// MMA K and permuted inside each chunk so a thread's four values are adjacent).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "bst_internal.h"
+
+namespace bst {
+
+constexpr int kSlices = 6;     // BF16 digits per operand
+constexpr int kBeta = 7;       // bits per digit
+constexpr int kSegChunks = 10; // 16-wide K chunks per exact FP32 segment (160 elements)
+constexpr int kExpNone = -4000;
+
+struct EmuState {
+  Arena ar;
+  bool index_ready = false;
+  // per stored block: offsets of its digit block, its exponents
+  int64_t *a_doff = nullptr, *b_doff = nullptr, *a_toff = nullptr, *b_toff = nullptr;
+  int64_t *a_eoff = nullptr, *b_eoff = nullptr;
+  int64_t a_dsize = 0, b_dsize = 0, a_tsize = 0, b_tsize = 0, a_esize = 0, b_esize = 0;
+  int32_t guard = 0;
+  int64_t nwarps = 0;
+  int64_t *wstart = nullptr;  // per (m,n) class: first warp
+  int32_t ncls = 0;
+  // data-dependent buffers (rebuilt per execute)
+  __nv_bfloat16 *a_dig = nullptr, *b_dig = nullptr;
+  float *a_tf = nullptr, *b_tf = nullptr;
+  int32_t *a_exp = nullptr, *b_exp = nullptr;
+  bool dig_alloc = false, tf_alloc = false;
+};
+
+namespace {
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ---- exponents and slices ------------------------------------------------------------
+
+// E(x): the smallest E with |x| < 2^E, for normal x; kExpNone for zero and subnormals
+__device__ __forceinline__ int exp_of(double x) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  return ex == 0 ? kExpNone : ex - 1022;
+}
+
+// position of inner index l inside its 16-chunk after the fragment permutation
+// (thread t of an m16n8k16 fragment holds k = 2t, 2t+1, 2t+8, 2t+9 -> positions 4t..4t+3)
+__device__ __forceinline__ int perm16(int l) {
+  const int j = l & 15;
+  return (l & ~15) + 4 * ((j & 7) >> 1) + 2 * (j >> 3) + (j & 1);
+}
+// same for m16n8k8 TF32 (thread t holds k = t, t+4 -> positions 2t, 2t+1)
+__device__ __forceinline__ int perm8(int l) {
+  const int j = l & 7;
+  return (l & ~7) + 2 * (j & 3) + (j >> 2);
+}
+
+struct SideArgs {
+  int64_t nblocks;
+  const int32_t *row, *col, *rsz, *csz;  // stored block index and sizes
+  const int64_t *off;                    // element offset of stored block
+  const double *data;
+  int trans;       // op(X) = X^T
+  int is_b;        // 0: exponents per op row (A side), 1: per op column (B side)
+  const int64_t *eoff;   // per block exponent offset
+  const int64_t *doff;   // per block digit / tf32 offset
+  int32_t *bexp;         // per block exponents
+  __nv_bfloat16 *dig;
+  float *tf;
+};
+
+// decompose stored element e of block b into op coordinates: (r, l) for the A side
+// (op row r, inner l), (l, q) for the B side (inner l, op column q); `outer` is r or q
+__device__ __forceinline__ void op_coords(const SideArgs &S, int rs, int cs, int &outer,
+                                          int &inner) {
+  // stored element (rs, cs); op(X) element = (rs, cs) or (cs, rs)
+  const int opr = S.trans ? cs : rs, opc = S.trans ? rs : cs;
+  if (S.is_b) {
+    inner = opr;
+    outer = opc;
+  } else {
+    outer = opr;
+    inner = opc;
+  }
+}
+
+__global__ void k_emu_exponents(SideArgs S) {
+  const int lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (b >= S.nblocks) return;
+  const int R = S.rsz[S.row[b]], Cc = S.csz[S.col[b]];
+  const double *x = S.data + S.off[b];
+  for (int e = lane; e < R * Cc; e += 32) {
+    int outer, inner;
+    op_coords(S, e / Cc, e % Cc, outer, inner);
+    const int E = exp_of(x[e]);
+    if (E != kExpNone) atomicMax(&S.bexp[S.eoff[b] + outer], E);
+  }
+}
+
+__global__ void k_emu_digits(SideArgs S) {
+  const int lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (b >= S.nblocks) return;
+  const int R = S.rsz[S.row[b]], Cc = S.csz[S.col[b]];
+  const int nouter = S.is_b ? (S.trans ? R : Cc) : (S.trans ? Cc : R);
+  const int ninner = S.is_b ? (S.trans ? Cc : R) : (S.trans ? R : Cc);
+  const int kp = (ninner + 15) & ~15;
+  const int64_t plane = (int64_t)nouter * kp;
+  const double *x = S.data + S.off[b];
+  __nv_bfloat16 *d = S.dig + S.doff[b];
+  for (int e = lane; e < R * Cc; e += 32) {
+    int outer, inner;
+    op_coords(S, e / Cc, e % Cc, outer, inner);
+    const double v = x[e];
+    const int E = S.bexp[S.eoff[b] + outer];
+    const long long bits = __double_as_longlong(v);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    unsigned long long N = 0;
+    if (ex != 0 && E != kExpNone) {
+      const unsigned long long M = (unsigned long long)(bits & 0xfffffffffffffLL) | (1ull << 52);
+      // N = round(|v| 2^(42 - E)) = round(M 2^(ex - 1075 + 42 - E)); the shift is >= 11
+      const int rsh = 1075 - kSlices * kBeta - ex + E;
+      if (rsh < 64) N = (M + (1ull << (rsh - 1))) >> rsh;
+    }
+    const bool neg = bits < 0;
+    const int64_t pos = (int64_t)outer * kp + perm16(inner);
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) {
+      int dg = (int)((N >> (kBeta * (kSlices - 1 - s))) & (s == 0 ? 0xffu : 0x7fu));
+      if (neg) dg = -dg;
+      d[s * plane + pos] = __float2bfloat16_rn((float)dg);
+    }
+  }
+}
+
+// round a double to TF32 (10 explicit mantissa bits), nearest with ties away
+__device__ __forceinline__ float to_tf32(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__global__ void k_tf32_split(SideArgs S) {
+  const int lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (b >= S.nblocks) return;
+  const int R = S.rsz[S.row[b]], Cc = S.csz[S.col[b]];
+  const int nouter = S.is_b ? (S.trans ? R : Cc) : (S.trans ? Cc : R);
+  const int ninner = S.is_b ? (S.trans ? Cc : R) : (S.trans ? R : Cc);
+  const int kp = (ninner + 7) & ~7;
+  const int64_t plane = (int64_t)nouter * kp;
+  const double *x = S.data + S.off[b];
+  float *t = S.tf + S.doff[b];
+  for (int e = lane; e < R * Cc; e += 32) {
+    int outer, inner;
+    op_coords(S, e / Cc, e % Cc, outer, inner);
+    const double v = x[e];
+    const float hi = to_tf32((float)v);
+    const float lo = to_tf32((float)(v - (double)hi));
+    const int64_t pos = (int64_t)outer * kp + perm8(inner);
+    t[pos] = hi;
+    t[plane + pos] = lo;
+  }
+}
+
+// per stored block: digit / tf32 / exponent sizes
+__global__ void k_side_sizes(SideArgs S, int64_t *dsz, int64_t *tsz, int64_t *esz) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= S.nblocks) return;
+  const int R = S.rsz[S.row[b]], Cc = S.csz[S.col[b]];
+  const int nouter = S.is_b ? (S.trans ? R : Cc) : (S.trans ? Cc : R);
+  const int ninner = S.is_b ? (S.trans ? Cc : R) : (S.trans ? R : Cc);
+  dsz[b] = (int64_t)kSlices * nouter * ((ninner + 15) & ~15);
+  tsz[b] = (int64_t)2 * nouter * ((ninner + 7) & ~7);
+  esz[b] = nouter;
+}
+
+// largest sum of inner sizes over the products of one C block
+__global__ void k_max_ktot(int64_t nc, int32_t Dk, const int32_t *run_len, const int32_t *kval,
+                           unsigned long long *out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  unsigned long long s = 0;
+  for (int kc = 0; kc < Dk; ++kc) s += (unsigned long long)run_len[c * Dk + kc] * kval[kc];
+  atomicMax(out, s);
+}
+
+// ---- integer -> FP64 ---------------------------------------------------------------
+
+// v * 2^e2 rounded to nearest-even binary64, from the IEEE 754 encoding (sign, biased
+// exponent, 52-bit fraction); integer operations only.  Results outside the normal
+// range take the library conversion.
+__device__ __forceinline__ double i64_ldexp(long long v, int e2) {
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
+  unsigned long long u = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int nb = 64 - __clzll(u);  // significant bits
+  int e = e2;
+  if (nb > 53) {
+    const int r = nb - 53;
+    const unsigned long long rem = u & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+    u >>= r;
+    e += r;
+    if (rem > half || (rem == half && (u & 1ull))) {
+      ++u;
+      if (u == (1ull << 53)) {
+        u >>= 1;
+        ++e;
+      }
+    }
+  } else {
+    u <<= (53 - nb);
+    e -= (53 - nb);
+  }
+  const int be = e + 52 + 1023;  // value = u 2^e with u in [2^52, 2^53)
+  if (be <= 0 || be >= 2047) return ldexp((double)v, e2);
+  return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) |
+                                          (u & ((1ull << 52) - 1ull))));
+}
+
+// FP32 -> FP64 from the binary32 / binary64 encodings (normal numbers and zero; FP32
+// subnormals flush to zero), integer operations only
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned ex = (b >> 23) & 0xffu;
+  if (ex == 0) return 0.0;
+  if (ex == 0xffu) return (double)f;
+  const unsigned long long bits = ((unsigned long long)(b >> 31) << 63) |
+                                  ((unsigned long long)(ex - 127 + 1023) << 52) |
+                                  ((unsigned long long)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ long long round_shift(long long v, int sh) {
+  if (sh <= 0) return v;
+  if (sh >= 62) return 0;
+  return (v + (1ll << (sh - 1))) >> sh;
+}
+
+// ---- the numeric kernels -----------------------------------------------------------
+
+struct EmuParams {
+  const double *Cin;
+  double *C;
+  double alpha, beta;
+  int32_t Dk, ncls, guard;
+  const int64_t *wstart;
+  const int32_t *class_ptr, *task_c, *cls_m, *cls_n, *kval;
+  const int32_t *c_row, *c_col, *c_cin;
+  const int64_t *c_off, *cin_off;
+  const int32_t *run_start, *run_len, *s_ab, *s_bb;
+  const int64_t *a_doff, *b_doff, *a_eoff, *b_eoff;
+  const __nv_bfloat16 *a_dig, *b_dig;
+  const float *a_tf, *b_tf;
+  const int32_t *a_exp, *b_exp;
+};
+
+struct WarpTask {
+  int c, m, n, mt, ng, ntn;
+};
+
+__device__ __forceinline__ WarpTask find_task(const EmuParams &P, int64_t gw) {
+  // class of this warp: last class whose start <= gw (classes with no warps are skipped)
+  int lo = 0, hi = P.ncls;  // wstart has ncls + 1 entries, wstart[ncls] = total
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (P.wstart[mid] <= gw)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  WarpTask w;
+  const int cls = lo;
+  w.m = P.cls_m[cls];
+  w.n = P.cls_n[cls];
+  const int MT = (w.m + 15) >> 4, NT = (w.n + 7) >> 3, NG = (NT + 1) >> 1;
+  const int64_t local = gw - P.wstart[cls];
+  const int64_t task = P.class_ptr[cls] + local / (MT * NG);
+  const int sub = (int)(local % (MT * NG));
+  w.mt = sub / NG;
+  w.ng = sub % NG;
+  w.ntn = min(2, NT - 2 * w.ng);
+  w.c = P.task_c[task];
+  return w;
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint2 ld8(const void *p) {
+  return __ldg(reinterpret_cast<const uint2 *>(p));
+}
+
+// element (row, col) of this warp's tile owned by accumulator slot h of N-tile nt
+__device__ __forceinline__ void slot_rc(const WarpTask &w, int nt, int h, int &r, int &c) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  r = w.mt * 16 + g + (h >= 2 ? 8 : 0);
+  c = (2 * w.ng + nt) * 8 + 2 * t + (h & 1);
+}
+
+__global__ void __launch_bounds__(256) k_num_emu_bf16(EmuParams P, int64_t nwarps) {
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (gw >= nwarps) return;
+  const WarpTask w = find_task(P, gw);
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = w.mt * 16 + g, r1 = r0 + 8;
+  const bool v0 = r0 < w.m, v1 = r1 < w.m;
+  int colB[2];
+  bool vB[2];
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt) {
+    colB[nt] = (2 * w.ng + nt) * 8 + g;
+    vB[nt] = nt < w.ntn && colB[nt] < w.n;
+  }
+  // exponents of the products of one entry for this thread's rows and columns
+  auto entry_exps = [&](int e, int (&ea)[2], int (&eb)[2][2]) {
+    const int ab = P.s_ab[e], bb = P.s_bb[e];
+    ea[0] = v0 ? P.a_exp[P.a_eoff[ab] + r0] : kExpNone;
+    ea[1] = v1 ? P.a_exp[P.a_eoff[ab] + r1] : kExpNone;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int cc = (2 * w.ng + nt) * 8 + 2 * t + h;
+        eb[nt][h] = (nt < w.ntn && cc < w.n) ? P.b_exp[P.b_eoff[bb] + cc] : kExpNone;
+      }
+  };
+  // common scale of every C element: the largest exponent sum over its products, so
+  // the int64 sum keeps 49 - G fraction bits relative to the largest contribution
+  int ref[2][4];
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+    for (int h = 0; h < 4; ++h) ref[nt][h] = 2 * kExpNone;
+  for (int kc = 0; kc < P.Dk; ++kc) {
+    const int64_t rr = (int64_t)w.c * P.Dk + kc;
+    const int len = P.run_len[rr];
+    const int e0 = len ? P.run_start[rr] : 0;
+    for (int e = e0; e < e0 + len; ++e) {
+      int ea[2], eb[2][2];
+      entry_exps(e, ea, eb);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int h = 0; h < 4; ++h) ref[nt][h] = max(ref[nt][h], ea[h >> 1] + eb[nt][h & 1]);
+    }
+  }
+  long long acc[2][4];
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+    for (int h = 0; h < 4; ++h) acc[nt][h] = 0;
+
+  for (int kc = 0; kc < P.Dk; ++kc) {
+    const int64_t rr = (int64_t)w.c * P.Dk + kc;
+    const int len = P.run_len[rr];
+    if (len == 0) continue;
+    const int e0 = P.run_start[rr];
+    const int k = P.kval[kc], kp = (k + 15) & ~15, nch = kp >> 4;
+    for (int e = e0; e < e0 + len; ++e) {
+      const int ab = P.s_ab[e], bb = P.s_bb[e];
+      const __nv_bfloat16 *Ad = P.a_dig + P.a_doff[ab];
+      const __nv_bfloat16 *Bd = P.b_dig + P.b_doff[bb];
+      const int64_t pa = (int64_t)w.m * kp, pb = (int64_t)w.n * kp;
+      int ea[2], eb[2][2];
+      entry_exps(e, ea, eb);
+      for (int cs = 0; cs < nch; cs += kSegChunks) {
+        float accw[kSlices][2][4];
+#pragma unroll
+        for (int s = 0; s < kSlices; ++s)
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) accw[s][nt][h] = 0.f;
+        const int ce = min(nch, cs + kSegChunks);
+        for (int ch = cs; ch < ce; ++ch) {
+          uint32_t af[kSlices][4];
+#pragma unroll
+          for (int s = 0; s < kSlices; ++s) {
+            const uint2 x0 = v0 ? ld8(Ad + s * pa + (int64_t)r0 * kp + ch * 16 + 4 * t) : make_uint2(0, 0);
+            const uint2 x1 = v1 ? ld8(Ad + s * pa + (int64_t)r1 * kp + ch * 16 + 4 * t) : make_uint2(0, 0);
+            af[s][0] = x0.x;
+            af[s][2] = x0.y;
+            af[s][1] = x1.x;
+            af[s][3] = x1.y;
+          }
+#pragma unroll
+          for (int tt = 0; tt < kSlices; ++tt) {
+            uint2 bf[2];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+              bf[nt] = vB[nt] ? ld8(Bd + tt * pb + (int64_t)colB[nt] * kp + ch * 16 + 4 * t)
+                              : make_uint2(0, 0);
+#pragma unroll
+            for (int s = 0; s + tt < kSlices; ++s) {
+              mma_bf16(accw[s + tt][0], af[s], bf[0].x, bf[0].y);
+              if (w.ntn > 1) mma_bf16(accw[s + tt][1], af[s], bf[1].x, bf[1].y);
+            }
+          }
+        }
+        // fold the exact level sums into the int64 accumulators
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            long long I = 0;
+#pragma unroll
+            for (int s = 0; s < kSlices; ++s)
+              I += (long long)__float2int_rn(accw[s][nt][h]) << (kBeta * (kSlices - 1 - s));
+            const int sh = ref[nt][h] - (ea[h >> 1] + eb[nt][h & 1]) + P.guard;
+            acc[nt][h] += round_shift(I, sh);
+          }
+      }
+    }
+  }
+  const int64_t off = P.c_off[w.c];
+  const int cin = P.c_cin[w.c];
+  const double *ci = (P.beta != 0.0 && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      int r, c;
+      slot_rc(w, nt, h, r, c);
+      if (nt < w.ntn && r < w.m && c < w.n) {
+        const int e2 = ref[nt][h] - (kSlices + 1) * kBeta + P.guard;
+        double v = i64_ldexp(acc[nt][h], e2);
+        if (P.alpha != 1.0) v *= P.alpha;
+        if (ci) v = fma(P.beta, ci[r * w.n + c], v);
+        P.C[off + r * w.n + c] = v;
+      }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_num_tf32x3(EmuParams P, int64_t nwarps) {
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (gw >= nwarps) return;
+  const WarpTask w = find_task(P, gw);
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = w.mt * 16 + g, r1 = r0 + 8;
+  const bool v0 = r0 < w.m, v1 = r1 < w.m;
+  int colB[2];
+  bool vB[2];
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt) {
+    colB[nt] = (2 * w.ng + nt) * 8 + g;
+    vB[nt] = nt < w.ntn && colB[nt] < w.n;
+  }
+  // running sum over the block products as an unevaluated FP32 pair (hi + lo), each
+  // product added with an error-free TwoSum, so the sum over many products keeps about
+  // twice FP32's precision
+  float hi[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  float lo[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  for (int kc = 0; kc < P.Dk; ++kc) {
+    const int64_t rr = (int64_t)w.c * P.Dk + kc;
+    const int len = P.run_len[rr];
+    if (len == 0) continue;
+    const int e0 = P.run_start[rr];
+    const int k = P.kval[kc], kp = (k + 7) & ~7, nch = kp >> 3;
+    for (int e = e0; e < e0 + len; ++e) {
+      const float *At = P.a_tf + P.a_doff[P.s_ab[e]];
+      const float *Bt = P.b_tf + P.b_doff[P.s_bb[e]];
+      const int64_t pa = (int64_t)w.m * kp, pb = (int64_t)w.n * kp;
+      float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+      for (int ch = 0; ch < nch; ++ch) {
+        const uint2 ah0 = v0 ? ld8(At + (int64_t)r0 * kp + ch * 8 + 2 * t) : make_uint2(0, 0);
+        const uint2 ah1 = v1 ? ld8(At + (int64_t)r1 * kp + ch * 8 + 2 * t) : make_uint2(0, 0);
+        const uint2 al0 = v0 ? ld8(At + pa + (int64_t)r0 * kp + ch * 8 + 2 * t) : make_uint2(0, 0);
+        const uint2 al1 = v1 ? ld8(At + pa + (int64_t)r1 * kp + ch * 8 + 2 * t) : make_uint2(0, 0);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          if (nt >= w.ntn) break;
+          const uint2 bh = vB[nt] ? ld8(Bt + (int64_t)colB[nt] * kp + ch * 8 + 2 * t) : make_uint2(0, 0);
+          const uint2 bl = vB[nt] ? ld8(Bt + pb + (int64_t)colB[nt] * kp + ch * 8 + 2 * t) : make_uint2(0, 0);
+          mma_tf32(acc[nt], al0.x, al1.x, al0.y, al1.y, bh.x, bh.y);
+          mma_tf32(acc[nt], ah0.x, ah1.x, ah0.y, ah1.y, bl.x, bl.y);
+          mma_tf32(acc[nt], ah0.x, ah1.x, ah0.y, ah1.y, bh.x, bh.y);
+        }
+      }
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const float a = hi[nt][h], b = acc[nt][h];
+          const float s = __fadd_rn(a, b);
+          const float bb = __fsub_rn(s, a);
+          const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+          hi[nt][h] = s;
+          lo[nt][h] = __fadd_rn(lo[nt][h], err);
+        }
+    }
+  }
+  const int64_t off = P.c_off[w.c];
+  const int cin = P.c_cin[w.c];
+  const double *ci = (P.beta != 0.0 && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      int r, c;
+      slot_rc(w, nt, h, r, c);
+      if (nt < w.ntn && r < w.m && c < w.n) {
+        double v = f32_to_f64(hi[nt][h]) + f32_to_f64(lo[nt][h]);
+        if (P.alpha != 1.0) v *= P.alpha;
+        if (ci) v = fma(P.beta, ci[r * w.n + c], v);
+        P.C[off + r * w.n + c] = v;
+      }
+    }
+}
+
+SideArgs side_args(const bst_matrix *X, bool trans, bool is_b) {
+  SideArgs S{};
+  S.nblocks = X->nblocks;
+  S.row = X->row;
+  S.col = X->col;
+  S.rsz = X->rsz;
+  S.csz = X->csz;
+  S.off = X->off;
+  S.data = X->data;
+  S.trans = trans;
+  S.is_b = is_b;
+  return S;
+}
+
+// plan-shape dependent index data (built once per plan)
+void emu_index(bst_plan *p, EmuState &E, cudaStream_t s) {
+  if (E.index_ready) return;
+  Arena &ar = E.ar;
+  Arena scratch;
+  scratch.ctx = static_cast<Ctx *>(p->ctx);
+  scratch.stream = s;
+  auto side = [&](const bst_matrix *X, bool trans, bool is_b, int64_t *&doff, int64_t *&toff,
+                  int64_t *&eoff, int64_t &dsize, int64_t &tsize, int64_t &esize) {
+    SideArgs S = side_args(X, trans, is_b);
+    const int64_t n = X->nblocks;
+    int64_t *dsz = scratch.alloc_n<int64_t>((size_t)n), *tsz = scratch.alloc_n<int64_t>((size_t)n),
+            *esz = scratch.alloc_n<int64_t>((size_t)n);
+    doff = ar.alloc_n<int64_t>((size_t)n + 1);
+    toff = ar.alloc_n<int64_t>((size_t)n + 1);
+    eoff = ar.alloc_n<int64_t>((size_t)n + 1);
+    if (n > 0) {
+      k_side_sizes<<<nblk(n, 256), 256, 0, s>>>(S, dsz, tsz, esz);
+      BST_CHECK_LAUNCH();
+    }
+    exscan_i64(dsz, doff, n, scratch, s);
+    exscan_i64(tsz, toff, n, scratch, s);
+    exscan_i64(esz, eoff, n, scratch, s);
+    int64_t tot[3];
+    BST_CUDA(cudaMemcpyAsync(&tot[0], doff + n, 8, cudaMemcpyDeviceToHost, s));
+    BST_CUDA(cudaMemcpyAsync(&tot[1], toff + n, 8, cudaMemcpyDeviceToHost, s));
+    BST_CUDA(cudaMemcpyAsync(&tot[2], eoff + n, 8, cudaMemcpyDeviceToHost, s));
+    BST_CUDA(cudaStreamSynchronize(s));
+    dsize = tot[0];
+    tsize = tot[1];
+    esize = tot[2];
+  };
+  side(p->A, p->ta, false, E.a_doff, E.a_toff, E.a_eoff, E.a_dsize, E.a_tsize, E.a_esize);
+  side(p->B, p->tb, true, E.b_doff, E.b_toff, E.b_eoff, E.b_dsize, E.b_tsize, E.b_esize);
+  // warps per (m,n) class: one per 16-row x 16-column tile of each C block
+  const int32_t ncls = p->Dm * p->Dn;
+  std::vector<int64_t> ws((size_t)ncls + 1, 0);
+  for (int32_t c = 0; c < ncls; ++c) {
+    const int64_t cnt = (int64_t)p->h_class_ptr[c + 1] - p->h_class_ptr[c];
+    const int m = p->m_vals.empty() ? 0 : p->m_vals[c / p->Dn];
+    const int n = p->n_vals.empty() ? 0 : p->n_vals[c % p->Dn];
+    const int64_t per = (int64_t)((m + 15) / 16) * (((n + 7) / 8 + 1) / 2);
+    ws[c + 1] = ws[c] + cnt * per;
+  }
+  E.ncls = ncls;
+  E.nwarps = ws.back();
+  E.wstart = ar.alloc_n<int64_t>(ws.size());
+  BST_CUDA(cudaMemcpyAsync(E.wstart, ws.data(), 8 * ws.size(), cudaMemcpyHostToDevice, s));
+  // guard bits: the int64 accumulator of a C element holds up to K_tot * 2^(49 - G)
+  unsigned long long *mk = scratch.alloc_n<unsigned long long>(1);
+  BST_CUDA(cudaMemsetAsync(mk, 0, 8, s));
+  const int64_t nc = p->C->nblocks;
+  if (nc > 0) {
+    k_max_ktot<<<nblk(nc, 256), 256, 0, s>>>(nc, p->Dk, p->run_len, p->kval, mk);
+    BST_CHECK_LAUNCH();
+  }
+  unsigned long long hk = 0;
+  BST_CUDA(cudaMemcpyAsync(&hk, mk, 8, cudaMemcpyDeviceToHost, s));
+  BST_CUDA(cudaStreamSynchronize(s));
+  int lg = 0;
+  while ((1ull << lg) <= hk) ++lg;
+  E.guard = std::max(0, lg - 12);
+  scratch.release_all();
+  E.index_ready = true;
+}
+
+EmuState &emu_state(bst_plan *p, cudaStream_t s) {
+  if (!p->emu) {
+    p->emu = new EmuState();
+    p->emu->ar.ctx = static_cast<Ctx *>(p->ctx);
+    p->emu->ar.stream = s;
+  }
+  emu_index(p, *p->emu, s);
+  return *p->emu;
+}
+
+EmuParams emu_params(bst_plan *p, const EmuState &E, const NumArgs &a) {
+  EmuParams P{};
+  P.Cin = a.Cin;
+  P.C = a.C;
+  P.alpha = a.alpha;
+  P.beta = a.beta;
+  P.Dk = p->Dk;
+  P.ncls = E.ncls;
+  P.guard = E.guard;
+  P.wstart = E.wstart;
+  P.class_ptr = p->class_ptr;
+  P.task_c = p->task_c;
+  P.cls_m = p->cls_m;
+  P.cls_n = p->cls_n;
+  P.kval = p->kval;
+  P.c_row = p->C->row;
+  P.c_col = p->C->col;
+  P.c_cin = p->c_cin;
+  P.c_off = p->C->off;
+  P.cin_off = p->Cin ? p->Cin->off : nullptr;
+  P.run_start = p->run_start;
+  P.run_len = p->run_len;
+  P.s_ab = p->s_ab;
+  P.s_bb = p->s_bb;
+  P.a_eoff = E.a_eoff;
+  P.b_eoff = E.b_eoff;
+  P.a_dig = E.a_dig;
+  P.b_dig = E.b_dig;
+  P.a_tf = E.a_tf;
+  P.b_tf = E.b_tf;
+  P.a_exp = E.a_exp;
+  P.b_exp = E.b_exp;
+  return P;
+}
+
+}  // namespace
+
+void emu_state_free(bst_plan *p) {
+  delete p->emu;
+  p->emu = nullptr;
+}
+
+void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
+  if (p->C->nblocks == 0) return;
+  EmuState &E = emu_state(p, s);
+  if (!E.dig_alloc) {
+    E.a_dig = E.ar.alloc_n<__nv_bfloat16>((size_t)E.a_dsize);
+    E.b_dig = E.ar.alloc_n<__nv_bfloat16>((size_t)E.b_dsize);
+    E.a_exp = E.ar.alloc_n<int32_t>((size_t)E.a_esize);
+    E.b_exp = E.ar.alloc_n<int32_t>((size_t)E.b_esize);
+    E.dig_alloc = true;
+  }
+  // slices of the current operand data (padding must read as zero)
+  BST_CUDA(cudaMemsetAsync(E.a_dig, 0, 2 * (size_t)std::max<int64_t>(E.a_dsize, 1), s));
+  BST_CUDA(cudaMemsetAsync(E.b_dig, 0, 2 * (size_t)std::max<int64_t>(E.b_dsize, 1), s));
+  fill_i32(E.a_exp, kExpNone, E.a_esize, s);
+  fill_i32(E.b_exp, kExpNone, E.b_esize, s);
+  const int wpb = 8;
+  for (int side = 0; side < 2; ++side) {
+    const bst_matrix *X = side ? p->B : p->A;
+    if (X->nblocks == 0) continue;
+    SideArgs S = side_args(X, side ? p->tb : p->ta, side == 1);
+    S.data = side ? a.B : a.A;
+    S.eoff = side ? E.b_eoff : E.a_eoff;
+    S.doff = side ? E.b_doff : E.a_doff;
+    S.bexp = side ? E.b_exp : E.a_exp;
+    S.dig = side ? E.b_dig : E.a_dig;
+    k_emu_exponents<<<nblk(X->nblocks, wpb), 32 * wpb, 0, s>>>(S);
+    BST_CHECK_LAUNCH();
+    k_emu_digits<<<nblk(X->nblocks, wpb), 32 * wpb, 0, s>>>(S);
+    BST_CHECK_LAUNCH();
+  }
+  EmuParams P = emu_params(p, E, a);
+  P.a_doff = E.a_doff;
+  P.b_doff = E.b_doff;
+  if (E.nwarps > 0) {
+    k_num_emu_bf16<<<nblk(E.nwarps, wpb), 32 * wpb, 0, s>>>(P, E.nwarps);
+    BST_CHECK_LAUNCH();
+  }
+}
+
+void execute_tf32x3(bst_plan *p, const NumArgs &a, cudaStream_t s) {
+  if (p->C->nblocks == 0) return;
+  EmuState &E = emu_state(p, s);
+  if (!E.tf_alloc) {
+    E.a_tf = E.ar.alloc_n<float>((size_t)E.a_tsize);
+    E.b_tf = E.ar.alloc_n<float>((size_t)E.b_tsize);
+    E.tf_alloc = true;
+  }
+  BST_CUDA(cudaMemsetAsync(E.a_tf, 0, 4 * (size_t)std::max<int64_t>(E.a_tsize, 1), s));
+  BST_CUDA(cudaMemsetAsync(E.b_tf, 0, 4 * (size_t)std::max<int64_t>(E.b_tsize, 1), s));
+  const int wpb = 8;
+  for (int side = 0; side < 2; ++side) {
+    const bst_matrix *X = side ? p->B : p->A;
+    if (X->nblocks == 0) continue;
+    SideArgs S = side_args(X, side ? p->tb : p->ta, side == 1);
+    S.data = side ? a.B : a.A;
+    S.doff = side ? E.b_toff : E.a_toff;
+    S.tf = side ? E.b_tf : E.a_tf;
+    k_tf32_split<<<nblk(X->nblocks, wpb), 32 * wpb, 0, s>>>(S);
+    BST_CHECK_LAUNCH();
+  }
+  EmuParams P = emu_params(p, E, a);
+  P.a_doff = E.a_toff;
+  P.b_doff = E.b_toff;
+  if (E.nwarps > 0) {
+    k_num_tf32x3<<<nblk(E.nwarps, wpb), 32 * wpb, 0, s>>>(P, E.nwarps);
+    BST_CHECK_LAUNCH();
+  }
+}
+
+}  // namespace bst

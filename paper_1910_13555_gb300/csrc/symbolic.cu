@@ -311,7 +311,7 @@ struct EmitArgs {
   const int64_t *a_off, *b_off, *c_off;
   const int32_t *k_cls;
   int32_t Dk;
-  int32_t *s_a, *s_b, *s_c, *s_cb, *s_k;
+  int32_t *s_a, *s_b, *s_c, *s_cb, *s_k, *s_ab, *s_bb;
   int32_t *run_start, *run_len;
   int32_t *refA, *refB;
 };
@@ -326,6 +326,8 @@ __global__ void k_emit_stacks(EmitArgs E) {
   E.s_c[q] = (int32_t)E.c_off[c];
   E.s_cb[q] = c;
   E.s_k[q] = k;
+  E.s_ab[q] = a;
+  E.s_bb[q] = b;
   const int64_t r = (int64_t)c * E.Dk + E.k_cls[k];
   atomicMin(&E.run_start[r], (int32_t)q);
   atomicAdd(&E.run_len[r], 1);
@@ -585,6 +587,8 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
   p->s_c = ar.alloc_n<int32_t>((size_t)T);
   p->s_cb = ar.alloc_n<int32_t>((size_t)T);
   p->s_k = ar.alloc_n<int32_t>((size_t)T);
+  p->s_ab = ar.alloc_n<int32_t>((size_t)T);
+  p->s_bb = ar.alloc_n<int32_t>((size_t)T);
   const int64_t nruns = nnzC * (int64_t)p->Dk;
   BST_REQUIRE(nruns < INT32_MAX, BST_ERR_UNSUPPORTED, "run table too large");
   p->run_start = ar.alloc_n<int32_t>((size_t)nruns);
@@ -613,6 +617,8 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
     E.s_c = p->s_c;
     E.s_cb = p->s_cb;
     E.s_k = p->s_k;
+    E.s_ab = p->s_ab;
+    E.s_bb = p->s_bb;
     E.run_start = p->run_start;
     E.run_len = p->run_len;
     E.refA = refA;
