@@ -388,6 +388,66 @@ class Plan:
             self.handle = None
 
 
+class Tensor:
+    """A library tensor handle with the torch tensor that owns its data."""
+
+    def __init__(self, handle, data, owned=True):
+        self.handle = handle
+        self.data = data
+        self.owned = owned
+
+    @classmethod
+    def from_host(cls, block_sizes, index, data, device=0, stream=None):
+        import torch
+        d = torch.as_tensor(np.ascontiguousarray(data, np.float64)).to(f"cuda:{device}")
+        h = bst_tensor_create(context(device), block_sizes, index, d, stream)
+        return cls(h, d)
+
+    @property
+    def info(self):
+        return bst_tensor_info(self.handle)
+
+    def index(self):
+        return bst_tensor_get_index(self.handle)
+
+    def __del__(self):
+        if getattr(self, "owned", False) and self.handle:
+            try:
+                bst_tensor_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+class ContractPlan(Plan):
+    """A contraction plan; ``result`` is the result tensor (pattern + data)."""
+
+    def alloc_result(self, device=0):
+        import torch
+        h = bst_plan_result_tensor(self.handle)
+        _, _, ne = bst_tensor_info(h)
+        d = torch.empty(max(ne, 1), dtype=torch.float64, device=f"cuda:{device}")
+        bst_tensor_bind_data(h, d)
+        self.result = Tensor(h, d, owned=False)
+        return self.result
+
+
+def contract_plan(T1: Tensor, T2: Tensor, c1, c2, f1, f2, result_order=None,
+                  R_in: Tensor | None = None, eps=0.0, device=0, stream=None) -> ContractPlan:
+    h = bst_contract_plan(context(device), T1.handle, T2.handle, c1, c2, f1, f2, result_order,
+                          R_in.handle if R_in is not None else None, eps, stream)
+    return ContractPlan(h, keep=(T1, T2, R_in))
+
+
+def contract(T1: Tensor, T2: Tensor, c1, c2, f1, f2, result_order=None, R_in=None, alpha=1.0,
+             beta=0.0, eps=0.0, precision=BST_FP64, split_k=1, device=0, stream=None):
+    """Plan + allocate the result tensor + execute; returns the plan (``plan.result``)."""
+    p = contract_plan(T1, T2, c1, c2, f1, f2, result_order, R_in, eps, device, stream)
+    p.alloc_result(device)
+    p.execute(alpha, beta, precision, split_k, stream)
+    return p
+
+
 def multiply_plan(A: Matrix, B: Matrix, C_in: Matrix | None = None, eps=0.0, transa="N",
                   transb="N", device=0, stream=None) -> Plan:
     h = bst_multiply_plan(context(device), transa, transb, A.handle, B.handle,

@@ -16,8 +16,9 @@
 //     I = sum_w D_w 2^{7 (5 - w)}          (|I| < 2^60)
 // in units of 2^{ea + eb - 49} (ea, eb: the row / column scales of this block pair),
 // which is shifted (with rounding) to the C element's common scale 2^{ref - 49 + G}
-// (ref: the largest ea + eb over the element's products; G guard bits against int64
-// overflow) and added into an int64 accumulator.  The result is exact up to the digit truncation and one rounding per
+// (ref: the largest exponent of the whole op(A) row plus that of the whole op(B)
+// column, so ref >= ea + eb for every product; G guard bits against int64 overflow)
+// and added into an int64 accumulator.  The result is exact up to the digit truncation and one rounding per
 // shift; it is turned into FP64 by an integer-only, round-to-nearest-even conversion
 // (IEEE 754 binary64 encoding), so C is formed in FP64 without FP64 multiply-adds --
 // on GB300 the FP64 pipe runs at 1/64 of the FP32 rate.
@@ -27,7 +28,8 @@
 // the whole C block, then converted to FP64 and combined with alpha, beta.
 //
 // Both use warp-level mma.sync tiles (m16n8k16 BF16, m16n8k8 TF32): one warp owns a
-// 16-row x 16-column tile of one C block (so no two warps write the same element),
+// 16 x 8 (BF16) or 16 x 16 (TF32) tile of one C block (no two warps write the same
+// element),
 // and the operand slices are staged once per execute in a padded, permuted layout that
 // makes every fragment a single 8-byte load (inner dimension padded with zeros to the
 // MMA K and permuted inside each chunk so a thread's four values are adjacent).
@@ -53,9 +55,15 @@ struct EmuState {
   int64_t *a_eoff = nullptr, *b_eoff = nullptr;
   int64_t a_dsize = 0, b_dsize = 0, a_tsize = 0, b_tsize = 0, a_esize = 0, b_esize = 0;
   int32_t guard = 0;
-  int64_t nwarps = 0;
-  int64_t *wstart = nullptr;  // per (m,n) class: first warp
+  int64_t nwarps = 0, nwarps_b = 0;
+  int64_t *wstart = nullptr;    // per (m,n) class: first warp, 16 x 16 tiles (3xTF32)
+  int64_t *wstart_b = nullptr;  // per (m,n) class: first warp, 16 x 8 tiles (BF16 slices)
   int32_t ncls = 0;
+  // global start of every op(A) row block / op(B) column block, and the largest
+  // exponent of every op(A) row / op(B) column over all blocks
+  int64_t *a_rowstart = nullptr, *b_colstart = nullptr;
+  int64_t nrows = 0, ncols = 0;
+  int32_t *row_exp = nullptr, *col_exp = nullptr;
   // data-dependent buffers (rebuilt per execute)
   __nv_bfloat16 *a_dig = nullptr, *b_dig = nullptr;
   float *a_tf = nullptr, *b_tf = nullptr;
@@ -98,6 +106,8 @@ struct SideArgs {
   const int64_t *eoff;   // per block exponent offset
   const int64_t *doff;   // per block digit / tf32 offset
   int32_t *bexp;         // per block exponents
+  const int64_t *start;  // global start of each op row block (A) / op column block (B)
+  int32_t *gexp;         // largest exponent of each whole op row (A) / op column (B)
   __nv_bfloat16 *dig;
   float *tf;
 };
@@ -123,11 +133,17 @@ __global__ void k_emu_exponents(SideArgs S) {
   if (b >= S.nblocks) return;
   const int R = S.rsz[S.row[b]], Cc = S.csz[S.col[b]];
   const double *x = S.data + S.off[b];
+  // op block index along the exponent dimension (rows of op(A), columns of op(B))
+  const int obr = S.trans ? S.col[b] : S.row[b], obc = S.trans ? S.row[b] : S.col[b];
+  const int64_t gbase = S.start[S.is_b ? obc : obr];
   for (int e = lane; e < R * Cc; e += 32) {
     int outer, inner;
     op_coords(S, e / Cc, e % Cc, outer, inner);
     const int E = exp_of(x[e]);
-    if (E != kExpNone) atomicMax(&S.bexp[S.eoff[b] + outer], E);
+    if (E != kExpNone) {
+      atomicMax(&S.bexp[S.eoff[b] + outer], E);
+      atomicMax(&S.gexp[gbase + outer], E);
+    }
   }
 }
 
@@ -279,6 +295,9 @@ struct EmuParams {
   double alpha, beta;
   int32_t Dk, ncls, guard;
   const int64_t *wstart;
+  int32_t tiles_n;  // N-tiles of 8 columns per warp (1 or 2)
+  const int64_t *a_rowstart, *b_colstart;
+  const int32_t *row_exp, *col_exp;
   const int32_t *class_ptr, *task_c, *cls_m, *cls_n, *kval;
   const int32_t *c_row, *c_col, *c_cin;
   const int64_t *c_off, *cin_off;
@@ -307,13 +326,13 @@ __device__ __forceinline__ WarpTask find_task(const EmuParams &P, int64_t gw) {
   const int cls = lo;
   w.m = P.cls_m[cls];
   w.n = P.cls_n[cls];
-  const int MT = (w.m + 15) >> 4, NT = (w.n + 7) >> 3, NG = (NT + 1) >> 1;
+  const int MT = (w.m + 15) >> 4, NT = (w.n + 7) >> 3, NG = (NT + P.tiles_n - 1) / P.tiles_n;
   const int64_t local = gw - P.wstart[cls];
   const int64_t task = P.class_ptr[cls] + local / (MT * NG);
   const int sub = (int)(local % (MT * NG));
   w.mt = sub / NG;
   w.ng = sub % NG;
-  w.ntn = min(2, NT - 2 * w.ng);
+  w.ntn = min(P.tiles_n, NT - P.tiles_n * w.ng);
   w.c = P.task_c[task];
   return w;
 }
@@ -347,80 +366,56 @@ __device__ __forceinline__ void slot_rc(const WarpTask &w, int nt, int h, int &r
   c = (2 * w.ng + nt) * 8 + 2 * t + (h & 1);
 }
 
-__global__ void __launch_bounds__(256) k_num_emu_bf16(EmuParams P, int64_t nwarps) {
+// One warp per 16 x 8 tile (w.mt, w.ng) of one C block.  Per stack entry: the six A
+// digit fragments are loaded once (two 8-byte loads each), each B digit fragment once,
+// and the 21 kept slice products go to six FP32 level accumulators; the levels are then
+// folded into the int64 accumulators at the element's common scale.
+__global__ void __launch_bounds__(256, 2) k_num_emu_bf16(EmuParams P, int64_t nwarps) {
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (gw >= nwarps) return;
   const WarpTask w = find_task(P, gw);
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int r0 = w.mt * 16 + g, r1 = r0 + 8;
   const bool v0 = r0 < w.m, v1 = r1 < w.m;
-  int colB[2];
-  bool vB[2];
-#pragma unroll
-  for (int nt = 0; nt < 2; ++nt) {
-    colB[nt] = (2 * w.ng + nt) * 8 + g;
-    vB[nt] = nt < w.ntn && colB[nt] < w.n;
+  const int colB = w.ng * 8 + g;
+  const bool vB = colB < w.n;
+  const int cc0 = w.ng * 8 + 2 * t, cc1 = cc0 + 1;
+  const bool vc0 = cc0 < w.n, vc1 = cc1 < w.n;
+  const int i = P.c_row[w.c], j = P.c_col[w.c];
+  // common scale of the four elements: largest exponent of the whole op(A) row plus
+  // that of the whole op(B) column, never below any product's ea + eb
+  int ref[4];
+  {
+    const int E0 = v0 ? P.row_exp[P.a_rowstart[i] + r0] : kExpNone;
+    const int E1 = v1 ? P.row_exp[P.a_rowstart[i] + r1] : kExpNone;
+    const int F0 = vc0 ? P.col_exp[P.b_colstart[j] + cc0] : kExpNone;
+    const int F1 = vc1 ? P.col_exp[P.b_colstart[j] + cc1] : kExpNone;
+    ref[0] = E0 + F0;
+    ref[1] = E0 + F1;
+    ref[2] = E1 + F0;
+    ref[3] = E1 + F1;
   }
-  // exponents of the products of one entry for this thread's rows and columns
-  auto entry_exps = [&](int e, int (&ea)[2], int (&eb)[2][2]) {
-    const int ab = P.s_ab[e], bb = P.s_bb[e];
-    ea[0] = v0 ? P.a_exp[P.a_eoff[ab] + r0] : kExpNone;
-    ea[1] = v1 ? P.a_exp[P.a_eoff[ab] + r1] : kExpNone;
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int cc = (2 * w.ng + nt) * 8 + 2 * t + h;
-        eb[nt][h] = (nt < w.ntn && cc < w.n) ? P.b_exp[P.b_eoff[bb] + cc] : kExpNone;
-      }
-  };
-  // common scale of every C element: the largest exponent sum over its products, so
-  // the int64 sum keeps 49 - G fraction bits relative to the largest contribution
-  int ref[2][4];
-#pragma unroll
-  for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-    for (int h = 0; h < 4; ++h) ref[nt][h] = 2 * kExpNone;
-  for (int kc = 0; kc < P.Dk; ++kc) {
-    const int64_t rr = (int64_t)w.c * P.Dk + kc;
-    const int len = P.run_len[rr];
-    const int e0 = len ? P.run_start[rr] : 0;
-    for (int e = e0; e < e0 + len; ++e) {
-      int ea[2], eb[2][2];
-      entry_exps(e, ea, eb);
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-        for (int h = 0; h < 4; ++h) ref[nt][h] = max(ref[nt][h], ea[h >> 1] + eb[nt][h & 1]);
-    }
-  }
-  long long acc[2][4];
-#pragma unroll
-  for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-    for (int h = 0; h < 4; ++h) acc[nt][h] = 0;
-
+  long long acc[4] = {0, 0, 0, 0};
   for (int kc = 0; kc < P.Dk; ++kc) {
     const int64_t rr = (int64_t)w.c * P.Dk + kc;
     const int len = P.run_len[rr];
     if (len == 0) continue;
     const int e0 = P.run_start[rr];
     const int k = P.kval[kc], kp = (k + 15) & ~15, nch = kp >> 4;
+    const int64_t pa = (int64_t)w.m * kp, pb = (int64_t)w.n * kp;
     for (int e = e0; e < e0 + len; ++e) {
       const int ab = P.s_ab[e], bb = P.s_bb[e];
       const __nv_bfloat16 *Ad = P.a_dig + P.a_doff[ab];
       const __nv_bfloat16 *Bd = P.b_dig + P.b_doff[bb];
-      const int64_t pa = (int64_t)w.m * kp, pb = (int64_t)w.n * kp;
-      int ea[2], eb[2][2];
-      entry_exps(e, ea, eb);
+      const int64_t aeo = P.a_eoff[ab], beo = P.b_eoff[bb];
+      const int ea0 = v0 ? P.a_exp[aeo + r0] : kExpNone, ea1 = v1 ? P.a_exp[aeo + r1] : kExpNone;
+      const int eb0 = vc0 ? P.b_exp[beo + cc0] : kExpNone, eb1 = vc1 ? P.b_exp[beo + cc1] : kExpNone;
       for (int cs = 0; cs < nch; cs += kSegChunks) {
-        float accw[kSlices][2][4];
+        float accw[kSlices][4];
 #pragma unroll
         for (int s = 0; s < kSlices; ++s)
 #pragma unroll
-          for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-            for (int h = 0; h < 4; ++h) accw[s][nt][h] = 0.f;
+          for (int h = 0; h < 4; ++h) accw[s][h] = 0.f;
         const int ce = min(nch, cs + kSegChunks);
         for (int ch = cs; ch < ce; ++ch) {
           uint32_t af[kSlices][4];
@@ -435,30 +430,21 @@ __global__ void __launch_bounds__(256) k_num_emu_bf16(EmuParams P, int64_t nwarp
           }
 #pragma unroll
           for (int tt = 0; tt < kSlices; ++tt) {
-            uint2 bf[2];
+            const uint2 bf = vB ? ld8(Bd + tt * pb + (int64_t)colB * kp + ch * 16 + 4 * t) : make_uint2(0, 0);
 #pragma unroll
-            for (int nt = 0; nt < 2; ++nt)
-              bf[nt] = vB[nt] ? ld8(Bd + tt * pb + (int64_t)colB[nt] * kp + ch * 16 + 4 * t)
-                              : make_uint2(0, 0);
-#pragma unroll
-            for (int s = 0; s + tt < kSlices; ++s) {
-              mma_bf16(accw[s + tt][0], af[s], bf[0].x, bf[0].y);
-              if (w.ntn > 1) mma_bf16(accw[s + tt][1], af[s], bf[1].x, bf[1].y);
-            }
+            for (int s = 0; s + tt < kSlices; ++s) mma_bf16(accw[s + tt], af[s], bf.x, bf.y);
           }
         }
         // fold the exact level sums into the int64 accumulators
+        const int eas[4] = {ea0 + eb0, ea0 + eb1, ea1 + eb0, ea1 + eb1};
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
+        for (int h = 0; h < 4; ++h) {
+          long long I = 0;
 #pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            long long I = 0;
-#pragma unroll
-            for (int s = 0; s < kSlices; ++s)
-              I += (long long)__float2int_rn(accw[s][nt][h]) << (kBeta * (kSlices - 1 - s));
-            const int sh = ref[nt][h] - (ea[h >> 1] + eb[nt][h & 1]) + P.guard;
-            acc[nt][h] += round_shift(I, sh);
-          }
+          for (int s = 0; s < kSlices; ++s)
+            I += (long long)__float2int_rn(accw[s][h]) << (kBeta * (kSlices - 1 - s));
+          acc[h] += round_shift(I, ref[h] - eas[h] + P.guard);
+        }
       }
     }
   }
@@ -466,19 +452,15 @@ __global__ void __launch_bounds__(256) k_num_emu_bf16(EmuParams P, int64_t nwarp
   const int cin = P.c_cin[w.c];
   const double *ci = (P.beta != 0.0 && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
 #pragma unroll
-  for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      int r, c;
-      slot_rc(w, nt, h, r, c);
-      if (nt < w.ntn && r < w.m && c < w.n) {
-        const int e2 = ref[nt][h] - (kSlices + 1) * kBeta + P.guard;
-        double v = i64_ldexp(acc[nt][h], e2);
-        if (P.alpha != 1.0) v *= P.alpha;
-        if (ci) v = fma(P.beta, ci[r * w.n + c], v);
-        P.C[off + r * w.n + c] = v;
-      }
+  for (int h = 0; h < 4; ++h) {
+    const int r = h < 2 ? r0 : r1, c = (h & 1) ? cc1 : cc0;
+    if (r < w.m && c < w.n) {
+      double v = i64_ldexp(acc[h], ref[h] - (kSlices + 1) * kBeta + P.guard);
+      if (P.alpha != 1.0) v *= P.alpha;
+      if (ci) v = fma(P.beta, ci[r * w.n + c], v);
+      P.C[off + r * w.n + c] = v;
     }
+  }
 }
 
 __global__ void __launch_bounds__(256) k_num_tf32x3(EmuParams P, int64_t nwarps) {
@@ -605,20 +587,36 @@ void emu_index(bst_plan *p, EmuState &E, cudaStream_t s) {
   };
   side(p->A, p->ta, false, E.a_doff, E.a_toff, E.a_eoff, E.a_dsize, E.a_tsize, E.a_esize);
   side(p->B, p->tb, true, E.b_doff, E.b_toff, E.b_eoff, E.b_dsize, E.b_tsize, E.b_esize);
-  // warps per (m,n) class: one per 16-row x 16-column tile of each C block
+  // warps per (m,n) class: one per 16-row x 16-column tile of each C block (3xTF32),
+  // one per 16-row x 8-column tile (BF16 slices)
   const int32_t ncls = p->Dm * p->Dn;
-  std::vector<int64_t> ws((size_t)ncls + 1, 0);
+  std::vector<int64_t> ws((size_t)ncls + 1, 0), wb((size_t)ncls + 1, 0);
   for (int32_t c = 0; c < ncls; ++c) {
     const int64_t cnt = (int64_t)p->h_class_ptr[c + 1] - p->h_class_ptr[c];
     const int m = p->m_vals.empty() ? 0 : p->m_vals[c / p->Dn];
     const int n = p->n_vals.empty() ? 0 : p->n_vals[c % p->Dn];
-    const int64_t per = (int64_t)((m + 15) / 16) * (((n + 7) / 8 + 1) / 2);
-    ws[c + 1] = ws[c] + cnt * per;
+    const int64_t mt = (m + 15) / 16, nt = (n + 7) / 8;
+    ws[c + 1] = ws[c] + cnt * mt * ((nt + 1) / 2);
+    wb[c + 1] = wb[c] + cnt * mt * nt;
   }
   E.ncls = ncls;
   E.nwarps = ws.back();
+  E.nwarps_b = wb.back();
   E.wstart = ar.alloc_n<int64_t>(ws.size());
+  E.wstart_b = ar.alloc_n<int64_t>(wb.size());
   BST_CUDA(cudaMemcpyAsync(E.wstart, ws.data(), 8 * ws.size(), cudaMemcpyHostToDevice, s));
+  BST_CUDA(cudaMemcpyAsync(E.wstart_b, wb.data(), 8 * wb.size(), cudaMemcpyHostToDevice, s));
+  // global element starts of op(A) row blocks and op(B) column blocks
+  auto starts = [&](const std::vector<int32_t> &sz, int64_t *&out, int64_t &total) {
+    std::vector<int64_t> h(sz.size() + 1, 0);
+    for (size_t q = 0; q < sz.size(); ++q) h[q + 1] = h[q] + sz[q];
+    total = h.back();
+    out = ar.alloc_n<int64_t>(h.size());
+    BST_CUDA(cudaMemcpyAsync(out, h.data(), 8 * h.size(), cudaMemcpyHostToDevice, s));
+    BST_CUDA(cudaStreamSynchronize(s));
+  };
+  starts(p->oa.h_rs, E.a_rowstart, E.nrows);
+  starts(p->ob.h_cs, E.b_colstart, E.ncols);
   // guard bits: the int64 accumulator of a C element holds up to K_tot * 2^(49 - G)
   unsigned long long *mk = scratch.alloc_n<unsigned long long>(1);
   BST_CUDA(cudaMemsetAsync(mk, 0, 8, s));
@@ -657,6 +655,11 @@ EmuParams emu_params(bst_plan *p, const EmuState &E, const NumArgs &a) {
   P.ncls = E.ncls;
   P.guard = E.guard;
   P.wstart = E.wstart;
+  P.tiles_n = 2;
+  P.a_rowstart = E.a_rowstart;
+  P.b_colstart = E.b_colstart;
+  P.row_exp = E.row_exp;
+  P.col_exp = E.col_exp;
   P.class_ptr = p->class_ptr;
   P.task_c = p->task_c;
   P.cls_m = p->cls_m;
@@ -697,6 +700,8 @@ void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
     E.b_dig = E.ar.alloc_n<__nv_bfloat16>((size_t)E.b_dsize);
     E.a_exp = E.ar.alloc_n<int32_t>((size_t)E.a_esize);
     E.b_exp = E.ar.alloc_n<int32_t>((size_t)E.b_esize);
+    E.row_exp = E.ar.alloc_n<int32_t>((size_t)E.nrows);
+    E.col_exp = E.ar.alloc_n<int32_t>((size_t)E.ncols);
     E.dig_alloc = true;
   }
   // slices of the current operand data (padding must read as zero)
@@ -704,6 +709,8 @@ void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
   BST_CUDA(cudaMemsetAsync(E.b_dig, 0, 2 * (size_t)std::max<int64_t>(E.b_dsize, 1), s));
   fill_i32(E.a_exp, kExpNone, E.a_esize, s);
   fill_i32(E.b_exp, kExpNone, E.b_esize, s);
+  fill_i32(E.row_exp, kExpNone, E.nrows, s);
+  fill_i32(E.col_exp, kExpNone, E.ncols, s);
   const int wpb = 8;
   for (int side = 0; side < 2; ++side) {
     const bst_matrix *X = side ? p->B : p->A;
@@ -713,6 +720,8 @@ void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
     S.eoff = side ? E.b_eoff : E.a_eoff;
     S.doff = side ? E.b_doff : E.a_doff;
     S.bexp = side ? E.b_exp : E.a_exp;
+    S.start = side ? E.b_colstart : E.a_rowstart;
+    S.gexp = side ? E.col_exp : E.row_exp;
     S.dig = side ? E.b_dig : E.a_dig;
     k_emu_exponents<<<nblk(X->nblocks, wpb), 32 * wpb, 0, s>>>(S);
     BST_CHECK_LAUNCH();
@@ -722,8 +731,10 @@ void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
   EmuParams P = emu_params(p, E, a);
   P.a_doff = E.a_doff;
   P.b_doff = E.b_doff;
-  if (E.nwarps > 0) {
-    k_num_emu_bf16<<<nblk(E.nwarps, wpb), 32 * wpb, 0, s>>>(P, E.nwarps);
+  P.wstart = E.wstart_b;
+  P.tiles_n = 1;
+  if (E.nwarps_b > 0) {
+    k_num_emu_bf16<<<nblk(E.nwarps_b, wpb), 32 * wpb, 0, s>>>(P, E.nwarps_b);
     BST_CHECK_LAUNCH();
   }
 }
