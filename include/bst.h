@@ -178,6 +178,25 @@ enum {
 bst_status bst_multiply_execute(bst_plan *plan, double alpha, double beta, int32_t precision,
                                 int32_t split_k, void *stream);
 
+/* Native-FP64 execute (as bst_multiply_execute with BST_FP64 and split_k >= 1) that
+ * allocates no device memory.  The paper has no counterpart: this entry point exists
+ * for callers that may not allocate while they run -- services that reserve all GPU
+ * memory up front and forbid later cudaMalloc (an allocation can synchronise the
+ * device and stall every stream), or host frameworks that own the whole device heap.
+ * The split-K partial sums live in a static __device__ array of
+ * bst_static_scratch_doubles() doubles (32 MiB) that every GPU loading the library
+ * holds until the process exits; split_k * nelem(C_out) above that returns
+ * BST_ERR_UNSUPPORTED (split_k = 1 needs no scratch).  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one array: calls that overlap on the
+ * GPU (different streams, or different plans on one device in flight together) race.
+ * Each call overwrites every scratch element it reads, so no clearing is needed.
+ * Errors: as bst_multiply_execute, plus UNSUPPORTED for a too-large workspace. */
+bst_status bst_multiply_execute_static(bst_plan *plan, double alpha, double beta,
+                                       int32_t split_k, void *stream);
+/* Capacity of the static split-K array of bst_multiply_execute_static, in doubles. */
+size_t bst_static_scratch_doubles(void);
+
 /* Adjoint of execute's function with the filter decisions held fixed:
  *   dop(A)_ik = alpha sum_{j kept} dC_ij op(B)_kj^T on pattern(A),
  *   dop(B)_kj = alpha sum_{i kept} op(A)_ik^T dC_ij on pattern(B),

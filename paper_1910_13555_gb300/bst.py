@@ -69,6 +69,8 @@ _SIGS = {
     "bst_plan_stats": ([_VP, C.POINTER(bst_stats)], C.c_int32),
     "bst_plan_get_stacks": ([_VP, _VP, _VP, _VP, _VP, _VP], C.c_int32),
     "bst_multiply_execute": ([_VP, C.c_double, C.c_double, C.c_int32, C.c_int32, _VP], C.c_int32),
+    "bst_multiply_execute_static": ([_VP, C.c_double, C.c_double, C.c_int32, _VP], C.c_int32),
+    "bst_static_scratch_doubles": ([], C.c_size_t),
     "bst_plan_adjoint": ([_VP, _VP, _VP, _VP, _VP, C.c_double, C.c_double, _VP], C.c_int32),
     "bst_plan_destroy": ([_VP], C.c_int32),
     "bst_tensor_create": ([_VP, C.POINTER(_VP), C.c_int32, _VP, _VP, C.c_int64, _VP, _VP, _VP],
@@ -228,6 +230,15 @@ def bst_multiply_execute(plan, alpha=1.0, beta=0.0, precision=BST_FP64, split_k=
         precision = PRECISIONS[precision]
     _check(load().bst_multiply_execute(plan, alpha, beta, precision, split_k, _stream(stream)),
            "bst_multiply_execute")
+
+
+def bst_multiply_execute_static(plan, alpha=1.0, beta=0.0, split_k=1, stream=None):
+    _check(load().bst_multiply_execute_static(plan, alpha, beta, split_k, _stream(stream)),
+           "bst_multiply_execute_static")
+
+
+def bst_static_scratch_doubles() -> int:
+    return int(load().bst_static_scratch_doubles())
 
 
 def bst_plan_adjoint(plan, dC, dA, dB, dC_in=None, alpha=1.0, beta=0.0, stream=None):

@@ -235,6 +235,7 @@ struct NumArgs {
   double alpha, beta;
 };
 void execute_fp64(bst_plan *p, const NumArgs &a, int split, cudaStream_t s);
+void execute_fp64_workspace(bst_plan *p, const NumArgs &a, int split, double *W, cudaStream_t s);
 void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s);
 void execute_tf32x3(bst_plan *p, const NumArgs &a, cudaStream_t s);
 void emu_state_free(bst_plan *p);
