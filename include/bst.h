@@ -208,6 +208,20 @@ bst_status bst_plan_adjoint(bst_plan *plan, const double *dC, double *dA, double
 
 bst_status bst_plan_destroy(bst_plan *plan);
 
+/* Kernel choices of a context, set by the project's autotuner (tune.py) or by hand.
+ *   BST_TUNE_EMU_ROW_SCALE (m, n ignored): 1 = emulated-FP64 digits scaled by the
+ *     largest exponent of the whole op(A) row / op(B) column, so all products of a C
+ *     element share a scale and their exact FP32 level sums run across products
+ *     (default); 0 = scaled per block row / column, each product folded on its own
+ *     (more robust to blocks of very different magnitudes in one row, slower).
+ *   BST_TUNE_FP64_ROWS_PER_WARP (per (m, n) C block class): native-FP64 thread
+ *     mapping; 0 = one warp per C block with lanes over its elements (default),
+ *     1 = the same with the C block's operands staged in shared memory.
+ * Errors: INVALID_ARG for an unknown key or value. */
+enum { BST_TUNE_EMU_ROW_SCALE = 0, BST_TUNE_FP64_ROWS_PER_WARP = 1 };
+bst_status bst_tune_set(bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t value);
+bst_status bst_tune_get(const bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t *value);
+
 /* ---------------------------------------------------------------------------
  * Tensors (paper Sec. 4).
  *

@@ -73,6 +73,8 @@ _SIGS = {
     "bst_static_scratch_doubles": ([], C.c_size_t),
     "bst_plan_adjoint": ([_VP, _VP, _VP, _VP, _VP, C.c_double, C.c_double, _VP], C.c_int32),
     "bst_plan_destroy": ([_VP], C.c_int32),
+    "bst_tune_set": ([_VP, C.c_int32, C.c_int32, C.c_int32, C.c_int32], C.c_int32),
+    "bst_tune_get": ([_VP, C.c_int32, C.c_int32, C.c_int32, _VP], C.c_int32),
     "bst_tensor_create": ([_VP, C.POINTER(_VP), C.c_int32, _VP, _VP, C.c_int64, _VP, _VP, _VP],
                           C.c_int32),
     "bst_tensor_info": ([_VP, _VP, _VP, _VP], C.c_int32),
@@ -248,6 +250,20 @@ def bst_plan_adjoint(plan, dC, dA, dB, dC_in=None, alpha=1.0, beta=0.0, stream=N
 
 def bst_plan_destroy(plan):
     _check(load().bst_plan_destroy(plan), "bst_plan_destroy")
+
+
+BST_TUNE_EMU_ROW_SCALE = 0
+BST_TUNE_FP64_ROWS_PER_WARP = 1
+
+
+def bst_tune_set(ctx, key, value, m=0, n=0):
+    _check(load().bst_tune_set(ctx, key, m, n, value), "bst_tune_set")
+
+
+def bst_tune_get(ctx, key, m=0, n=0) -> int:
+    v = C.c_int32()
+    _check(load().bst_tune_get(ctx, key, m, n, C.byref(v)), "bst_tune_get")
+    return v.value
 
 
 def bst_tensor_create(ctx, block_sizes, index, data=None, stream=None):

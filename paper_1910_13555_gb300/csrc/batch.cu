@@ -1,0 +1,198 @@
+// Batches: many independent block-sparse products in one persistent kernel launch.
+//
+// A batch holds plans that were built with bst_multiply_plan / bst_contract_plan
+// (their symbolic phases are done).  Its work list is every C block of every plan
+// (every 16 x 8 warp tile for emulated FP64), tagged with the plan's index and ordered
+// by decreasing cost across the whole batch, so one persistent grid balances products
+// of very different sizes (longest-processing-time first, dynamic fetch from one
+// counter).  bst_batch_execute only queues work: a parameter copy from the batch's
+// pinned staging buffer, the counter reset and the launches (plus the per-plan slicing
+// kernels for emulated FP64 and the permutations of contraction views), so a call can be
+// captured into a CUDA graph and replayed; everything that allocates or synchronises
+// happens in bst_batch_create.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "bst_internal.h"
+
+struct bst_batch {
+  bst_ctx *ctx = nullptr;
+  std::vector<bst_plan *> plans;
+  bst::Arena ar;
+  // native FP64 schedule
+  int64_t n_items = 0;
+  int64_t *items = nullptr;
+  unsigned long long *counter = nullptr;
+  void *d_params = nullptr, *h_params = nullptr;
+  size_t pbytes = 0;
+  int grid = 0;
+  // emulated FP64 schedule
+  int64_t n_items_e = 0;
+  int64_t *items_e = nullptr;
+  void *d_eparams = nullptr, *h_eparams = nullptr;
+  size_t epbytes = 0;
+  int grid_e = 0;
+  ~bst_batch() {
+    if (h_params) cudaFreeHost(h_params);
+    if (h_eparams) cudaFreeHost(h_eparams);
+  }
+};
+
+namespace {
+
+struct Args {
+  bst::NumArgs a;
+  bool read_cin;
+};
+
+Args plan_args(bst_plan *p, double alpha, double beta, cudaStream_t s) {
+  if (p->contract)
+    bst::contract_prepare(p, beta != 0.0 && p->Cin && p->Cin->nblocks > 0, s);
+  const bst_matrix *C = p->C;
+  BST_REQUIRE(std::isfinite(alpha) && std::isfinite(beta), BST_ERR_INVALID_ARG,
+              "alpha and beta must be finite");
+  BST_REQUIRE(C->nelem == 0 || C->data, BST_ERR_STATE, "C_out data not bound");
+  BST_REQUIRE(p->A->nblocks == 0 || p->A->data, BST_ERR_STATE, "A data not bound");
+  BST_REQUIRE(p->B->nblocks == 0 || p->B->data, BST_ERR_STATE, "B data not bound");
+  Args r;
+  r.read_cin = beta != 0.0 && p->Cin && p->Cin->nblocks > 0;
+  BST_REQUIRE(!r.read_cin || p->Cin->data, BST_ERR_STATE, "C_in data not bound");
+  r.a.A = p->A->data;
+  r.a.B = p->B->data;
+  r.a.Cin = r.read_cin ? p->Cin->data : nullptr;
+  r.a.C = C->data;
+  r.a.alpha = alpha;
+  r.a.beta = r.read_cin ? beta : 0.0;
+  return r;
+}
+
+}  // namespace
+
+extern "C" {
+
+bst_status bst_batch_create(bst_ctx *ctx, int32_t n, bst_plan *const *plans, bst_batch **out) {
+  try {
+    BST_REQUIRE(ctx && out && n >= 1 && plans, BST_ERR_INVALID_ARG, "bad batch arguments");
+    *out = nullptr;
+    for (int32_t q = 0; q < n; ++q) {
+      BST_REQUIRE(plans[q], BST_ERR_INVALID_ARG, "a plan is NULL");
+      BST_REQUIRE(plans[q]->ctx == ctx, BST_ERR_INVALID_ARG, "plans of another context");
+    }
+    int cur = -1;
+    BST_CUDA(cudaGetDevice(&cur));
+    if (cur != ctx->device) BST_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = nullptr;
+    auto *b = new bst_batch();
+    try {
+      b->ctx = ctx;
+      b->ar.ctx = static_cast<bst::Ctx *>(ctx);
+      b->ar.stream = s;
+      b->plans.assign(plans, plans + n);
+      bst::Arena scratch;
+      scratch.ctx = b->ar.ctx;
+      scratch.stream = s;
+      // native FP64: every C block of every plan
+      for (auto *p : b->plans) b->n_items += p->C->nblocks;
+      int64_t *it0 = scratch.alloc_n<int64_t>((size_t)b->n_items);
+      int32_t *keys = scratch.alloc_n<int32_t>((size_t)b->n_items);
+      int64_t off = 0;
+      for (int32_t q = 0; q < n; ++q) {
+        bst::build_cost_items(b->plans[q], (int64_t)q << 32, it0 + off, keys + off, scratch, s);
+        off += b->plans[q]->C->nblocks;
+      }
+      b->items = b->ar.alloc_n<int64_t>((size_t)b->n_items);
+      bst::sort_items(it0, keys, b->n_items, b->items, scratch, s);
+      b->counter = b->ar.alloc_n<unsigned long long>(1);
+      b->pbytes = bst::num_params_bytes();
+      b->d_params = b->ar.alloc(b->pbytes * n);
+      BST_CUDA(cudaMallocHost(&b->h_params, b->pbytes * n));
+      b->grid = bst::persist_grid(ctx->num_sms);
+      // emulated FP64: every 16 x 8 tile (slicing state built per plan here)
+      std::vector<int64_t> cnt(n);
+      for (int32_t q = 0; q < n; ++q) {
+        cnt[q] = b->plans[q]->contract ? 0 : bst::emu_item_count(b->plans[q], s);
+        b->n_items_e += cnt[q];
+      }
+      int64_t *ie0 = scratch.alloc_n<int64_t>((size_t)b->n_items_e);
+      int32_t *ke = scratch.alloc_n<int32_t>((size_t)b->n_items_e);
+      off = 0;
+      for (int32_t q = 0; q < n; ++q) {
+        if (cnt[q]) bst::emu_build_items(b->plans[q], (int64_t)q << 32, ie0 + off, ke + off, s);
+        off += cnt[q];
+      }
+      b->items_e = b->ar.alloc_n<int64_t>((size_t)b->n_items_e);
+      bst::sort_items(ie0, ke, b->n_items_e, b->items_e, scratch, s);
+      b->epbytes = bst::emu_params_bytes();
+      b->d_eparams = b->ar.alloc(b->epbytes * n);
+      BST_CUDA(cudaMallocHost(&b->h_eparams, b->epbytes * n));
+      b->grid_e = bst::emu_persist_grid(ctx->num_sms);
+      BST_CUDA(cudaStreamSynchronize(s));
+      scratch.release_all();
+      BST_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+      delete b;
+      throw;
+    }
+    *out = b;
+  } catch (const bst::Error &e) {
+    bst::set_error(e.msg);
+    return e.code;
+  } catch (...) {
+    bst::set_error("unexpected internal error");
+    return BST_ERR_INVALID_ARG;
+  }
+  return BST_OK;
+}
+
+bst_status bst_batch_execute(bst_batch *b, const double *alpha, const double *beta,
+                             int32_t precision, void *stream) {
+  try {
+    BST_REQUIRE(b && alpha && beta, BST_ERR_INVALID_ARG, "NULL argument");
+    BST_REQUIRE(precision == BST_FP64 || precision == BST_FP64_EMU_BF16, BST_ERR_UNSUPPORTED,
+                "batches run native FP64 or emulated FP64");
+    int cur = -1;
+    BST_CUDA(cudaGetDevice(&cur));
+    if (cur != b->ctx->device) BST_CUDA(cudaSetDevice(b->ctx->device));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int32_t n = (int32_t)b->plans.size();
+    if (precision == BST_FP64) {
+      for (int32_t q = 0; q < n; ++q) {
+        Args r = plan_args(b->plans[q], alpha[q], beta[q], s);
+        bst::fill_num_params(b->plans[q], r.a, static_cast<char *>(b->h_params) + q * b->pbytes);
+      }
+      BST_CUDA(cudaMemcpyAsync(b->d_params, b->h_params, b->pbytes * n, cudaMemcpyHostToDevice, s));
+      bst::launch_fp64_persist(b->d_params, b->items, b->n_items, b->counter, b->grid, s);
+    } else {
+      for (int32_t q = 0; q < n; ++q) {
+        BST_REQUIRE(!b->plans[q]->contract, BST_ERR_UNSUPPORTED,
+                    "emulated FP64 batches take matrix plans only");
+        Args r = plan_args(b->plans[q], alpha[q], beta[q], s);
+        if (b->plans[q]->C->nblocks > 0)
+          bst::emu_prepare_and_fill(b->plans[q], r.a,
+                                    static_cast<char *>(b->h_eparams) + q * b->epbytes, s);
+      }
+      BST_CUDA(cudaMemcpyAsync(b->d_eparams, b->h_eparams, b->epbytes * n, cudaMemcpyHostToDevice, s));
+      bst::launch_emu_persist(b->d_eparams, b->items_e, b->n_items_e, b->counter, b->grid_e, s);
+    }
+    for (int32_t q = 0; q < n; ++q) {
+      if (b->plans[q]->contract) bst::contract_finish(b->plans[q], s);
+      b->plans[q]->stats.split_k = 1;
+    }
+  } catch (const bst::Error &e) {
+    bst::set_error(e.msg);
+    return e.code;
+  } catch (...) {
+    bst::set_error("unexpected internal error");
+    return BST_ERR_INVALID_ARG;
+  }
+  return BST_OK;
+}
+
+bst_status bst_batch_destroy(bst_batch *b) {
+  delete b;
+  return BST_OK;
+}
+
+}  // extern "C"

@@ -423,6 +423,38 @@ bst_status bst_plan_adjoint(bst_plan *plan, const double *dC, double *dA, double
   API_END
 }
 
+bst_status bst_tune_set(bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t value) {
+  API_BEGIN
+  BST_REQUIRE(ctx, BST_ERR_INVALID_ARG, "ctx is NULL");
+  (void)m;
+  (void)n;
+  switch (key) {
+    case BST_TUNE_EMU_ROW_SCALE:
+      BST_REQUIRE(value == 0 || value == 1, BST_ERR_INVALID_ARG, "value must be 0 or 1");
+      ctx->tune_emu_row_scale = value;
+      break;
+    case BST_TUNE_FP64_ROWS_PER_WARP:
+      BST_REQUIRE(value == 0, BST_ERR_INVALID_ARG, "only variant 0 is built");
+      break;
+    default:
+      throw Error{BST_ERR_INVALID_ARG, "unknown tuning key"};
+  }
+  API_END
+}
+
+bst_status bst_tune_get(const bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t *value) {
+  API_BEGIN
+  BST_REQUIRE(ctx && value, BST_ERR_INVALID_ARG, "NULL argument");
+  (void)m;
+  (void)n;
+  switch (key) {
+    case BST_TUNE_EMU_ROW_SCALE: *value = ctx->tune_emu_row_scale; break;
+    case BST_TUNE_FP64_ROWS_PER_WARP: *value = 0; break;
+    default: throw Error{BST_ERR_INVALID_ARG, "unknown tuning key"};
+  }
+  API_END
+}
+
 bst_status bst_plan_destroy(bst_plan *plan) {
   API_BEGIN
   if (!plan) return BST_OK;

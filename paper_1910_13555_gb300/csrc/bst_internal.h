@@ -75,6 +75,9 @@ struct bst_ctx {
   void *user = nullptr;
   int num_sms = 0;
   size_t max_smem_optin = 0;
+  // kernel choices (bst_tune_set): emulated-FP64 digit scaling per whole op row /
+  // column (1) or per block row / column (0)
+  int tune_emu_row_scale = 1;
 };
 
 namespace bst {
@@ -211,6 +214,9 @@ struct bst_plan {
   int32_t *task_c = nullptr;
   std::vector<int32_t> h_class_ptr;   // Dm*Dn + 1
   int32_t *class_ptr = nullptr;
+  // persistent numeric schedule: C blocks by decreasing cost (item = C block index)
+  int64_t *items = nullptr;
+  unsigned long long *items_counter = nullptr;
   // stats
   bst_stats stats{};
   // emulated-precision state (numeric_emu.cu), built on first use
@@ -251,5 +257,23 @@ void adjoint_fp64(bst_plan *p, const double *A, const double *B, const double *d
 void scale_cin_grad(bst_plan *p, const double *dC, double *dCin, double beta, cudaStream_t s);
 
 int choose_split(const bst_plan *p, int num_sms);
+// persistent FP64 numeric (numeric_fp64.cu)
+size_t num_params_bytes();
+void fill_num_params(bst_plan *p, const NumArgs &a, void *out);
+void build_cost_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys, Arena &scratch,
+                      cudaStream_t s);
+void sort_items(int64_t *items, const int32_t *keys, int64_t n, int64_t *out, Arena &scratch,
+                cudaStream_t s);
+int persist_grid(int num_sms);
+void launch_fp64_persist(const void *params, const int64_t *items, int64_t nitems,
+                         unsigned long long *counter, int grid, cudaStream_t s);
+// persistent emulated-FP64 numeric (numeric_emu.cu)
+size_t emu_params_bytes();
+int64_t emu_item_count(bst_plan *p, cudaStream_t s);
+void emu_build_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys, cudaStream_t s);
+void emu_prepare_and_fill(bst_plan *p, const NumArgs &a, void *out, cudaStream_t s);
+int emu_persist_grid(int num_sms);
+void launch_emu_persist(const void *params, const int64_t *items, int64_t nitems,
+                        unsigned long long *counter, int grid, cudaStream_t s);
 
 }  // namespace bst

@@ -36,6 +36,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 
 #include "bst_internal.h"
@@ -69,6 +70,9 @@ struct EmuState {
   float *a_tf = nullptr, *b_tf = nullptr;
   int32_t *a_exp = nullptr, *b_exp = nullptr;
   bool dig_alloc = false, tf_alloc = false;
+  // persistent schedule of the BF16 warp tiles
+  int64_t *items = nullptr;
+  unsigned long long *counter = nullptr;
 };
 
 namespace {
@@ -108,6 +112,7 @@ struct SideArgs {
   int32_t *bexp;         // per block exponents
   const int64_t *start;  // global start of each op row block (A) / op column block (B)
   int32_t *gexp;         // largest exponent of each whole op row (A) / op column (B)
+  int row_scale;         // digits scaled by the whole op row / column (1) or the block's (0)
   __nv_bfloat16 *dig;
   float *tf;
 };
@@ -158,11 +163,13 @@ __global__ void k_emu_digits(SideArgs S) {
   const int64_t plane = (int64_t)nouter * kp;
   const double *x = S.data + S.off[b];
   __nv_bfloat16 *d = S.dig + S.doff[b];
+  const int obr = S.trans ? S.col[b] : S.row[b], obc = S.trans ? S.row[b] : S.col[b];
+  const int64_t gbase = S.start[S.is_b ? obc : obr];
   for (int e = lane; e < R * Cc; e += 32) {
     int outer, inner;
     op_coords(S, e / Cc, e % Cc, outer, inner);
     const double v = x[e];
-    const int E = S.bexp[S.eoff[b] + outer];
+    const int E = S.row_scale ? S.gexp[gbase + outer] : S.bexp[S.eoff[b] + outer];
     const long long bits = __double_as_longlong(v);
     const int ex = (int)((bits >> 52) & 0x7ff);
     unsigned long long N = 0;
@@ -237,6 +244,10 @@ __global__ void k_max_ktot(int64_t nc, int32_t Dk, const int32_t *run_len, const
 
 // ---- integer -> FP64 ---------------------------------------------------------------
 
+// results outside the normal binary64 range (not met by the test workloads); kept out
+// of line so that the common path issues no FP64 instruction
+__device__ __noinline__ double i64_ldexp_slow(long long v, int e2) { return ldexp((double)v, e2); }
+
 // v * 2^e2 rounded to nearest-even binary64, from the IEEE 754 encoding (sign, biased
 // exponent, 52-bit fraction); integer operations only.  Results outside the normal
 // range take the library conversion.
@@ -263,7 +274,7 @@ __device__ __forceinline__ double i64_ldexp(long long v, int e2) {
     e -= (53 - nb);
   }
   const int be = e + 52 + 1023;  // value = u 2^e with u in [2^52, 2^53)
-  if (be <= 0 || be >= 2047) return ldexp((double)v, e2);
+  if (be <= 0 || be >= 2047) return i64_ldexp_slow(v, e2);
   return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) |
                                           (u & ((1ull << 52) - 1ull))));
 }
@@ -296,6 +307,7 @@ struct EmuParams {
   int32_t Dk, ncls, guard;
   const int64_t *wstart;
   int32_t tiles_n;  // N-tiles of 8 columns per warp (1 or 2)
+  int32_t row_scale;  // 1: digits scaled per whole op row / column (shared by all products)
   const int64_t *a_rowstart, *b_colstart;
   const int32_t *row_exp, *col_exp;
   const int32_t *class_ptr, *task_c, *cls_m, *cls_n, *kval;
@@ -327,13 +339,13 @@ __device__ __forceinline__ WarpTask find_task(const EmuParams &P, int64_t gw) {
   w.m = P.cls_m[cls];
   w.n = P.cls_n[cls];
   const int MT = (w.m + 15) >> 4, NT = (w.n + 7) >> 3, NG = (NT + P.tiles_n - 1) / P.tiles_n;
-  const int64_t local = gw - P.wstart[cls];
-  const int64_t task = P.class_ptr[cls] + local / (MT * NG);
-  const int sub = (int)(local % (MT * NG));
-  w.mt = sub / NG;
-  w.ng = sub % NG;
+  // warps of one class number below 2^31 (a class holds < 2^31 C blocks x a few tiles)
+  const unsigned local = (unsigned)(gw - P.wstart[cls]), per = (unsigned)(MT * NG);
+  const unsigned task = local / per, sub = local - task * per;
+  w.mt = (int)(sub / (unsigned)NG);
+  w.ng = (int)(sub - (unsigned)w.mt * (unsigned)NG);
   w.ntn = min(P.tiles_n, NT - P.tiles_n * w.ng);
-  w.c = P.task_c[task];
+  w.c = P.task_c[P.class_ptr[cls] + (int)task];
   return w;
 }
 
@@ -370,10 +382,99 @@ __device__ __forceinline__ void slot_rc(const WarpTask &w, int nt, int h, int &r
 // digit fragments are loaded once (two 8-byte loads each), each B digit fragment once,
 // and the 21 kept slice products go to six FP32 level accumulators; the levels are then
 // folded into the int64 accumulators at the element's common scale.
-__global__ void __launch_bounds__(256, 2) k_num_emu_bf16(EmuParams P, int64_t nwarps) {
-  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (gw >= nwarps) return;
-  const WarpTask w = find_task(P, gw);
+// Row-scaled form: every product of a C element shares the element's scale
+// 2^{E_row + F_col}, so the FP32 level sums run across products and are folded into the
+// int64 accumulators only when 160 inner elements have been summed (or at the end).
+__device__ __forceinline__ void emu_tile_rows(const EmuParams &P, const WarpTask &w) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = w.mt * 16 + g, r1 = r0 + 8;
+  const bool v0 = r0 < w.m, v1 = r1 < w.m;
+  const int colB = w.ng * 8 + g;
+  const bool vB = colB < w.n;
+  const int cc0 = w.ng * 8 + 2 * t, cc1 = cc0 + 1;
+  const bool vc0 = cc0 < w.n, vc1 = cc1 < w.n;
+  const int i = P.c_row[w.c], j = P.c_col[w.c];
+  int ref[4];
+  {
+    const int E0 = v0 ? P.row_exp[P.a_rowstart[i] + r0] : kExpNone;
+    const int E1 = v1 ? P.row_exp[P.a_rowstart[i] + r1] : kExpNone;
+    const int F0 = vc0 ? P.col_exp[P.b_colstart[j] + cc0] : kExpNone;
+    const int F1 = vc1 ? P.col_exp[P.b_colstart[j] + cc1] : kExpNone;
+    ref[0] = E0 + F0;
+    ref[1] = E0 + F1;
+    ref[2] = E1 + F0;
+    ref[3] = E1 + F1;
+  }
+  long long acc[4] = {0, 0, 0, 0};
+  float accw[kSlices][4];
+#pragma unroll
+  for (int s = 0; s < kSlices; ++s)
+#pragma unroll
+    for (int h = 0; h < 4; ++h) accw[s][h] = 0.f;
+  int used = 0;  // 16-wide chunks summed into accw since the last fold
+  auto fold = [&]() {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      long long I = 0;
+#pragma unroll
+      for (int s = 0; s < kSlices; ++s) {
+        I += (long long)__float2int_rn(accw[s][h]) << (kBeta * (kSlices - 1 - s));
+        accw[s][h] = 0.f;
+      }
+      acc[h] += round_shift(I, P.guard);
+    }
+    used = 0;
+  };
+  for (int kc = 0; kc < P.Dk; ++kc) {
+    const int64_t rr = (int64_t)w.c * P.Dk + kc;
+    const int len = P.run_len[rr];
+    if (len == 0) continue;
+    const int e0 = P.run_start[rr];
+    const int k = P.kval[kc], kp = (k + 15) & ~15, nch = kp >> 4;
+    const int64_t pa = (int64_t)w.m * kp, pb = (int64_t)w.n * kp;
+    for (int e = e0; e < e0 + len; ++e) {
+      const __nv_bfloat16 *Ad = P.a_dig + P.a_doff[P.s_ab[e]];
+      const __nv_bfloat16 *Bd = P.b_dig + P.b_doff[P.s_bb[e]];
+      for (int ch = 0; ch < nch; ++ch) {
+        if (used == kSegChunks) fold();
+        uint32_t af[kSlices][4];
+#pragma unroll
+        for (int s = 0; s < kSlices; ++s) {
+          const uint2 x0 = v0 ? ld8(Ad + s * pa + (int64_t)r0 * kp + ch * 16 + 4 * t) : make_uint2(0, 0);
+          const uint2 x1 = v1 ? ld8(Ad + s * pa + (int64_t)r1 * kp + ch * 16 + 4 * t) : make_uint2(0, 0);
+          af[s][0] = x0.x;
+          af[s][2] = x0.y;
+          af[s][1] = x1.x;
+          af[s][3] = x1.y;
+        }
+#pragma unroll
+        for (int tt = 0; tt < kSlices; ++tt) {
+          const uint2 bf = vB ? ld8(Bd + tt * pb + (int64_t)colB * kp + ch * 16 + 4 * t) : make_uint2(0, 0);
+#pragma unroll
+          for (int s = 0; s + tt < kSlices; ++s) mma_bf16(accw[s + tt], af[s], bf.x, bf.y);
+        }
+        ++used;
+      }
+    }
+  }
+  fold();
+  const int64_t off = P.c_off[w.c];
+  const int cin = P.c_cin[w.c];
+  const double *ci = (P.beta != 0.0 && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
+  const bool scale = P.alpha != 1.0;  // one FP64 compare per thread, not per element
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const int r = h < 2 ? r0 : r1, c = (h & 1) ? cc1 : cc0;
+    if (r < w.m && c < w.n) {
+      double v = i64_ldexp(acc[h], ref[h] - (kSlices + 1) * kBeta + P.guard);
+      if (scale) v *= P.alpha;
+      if (ci) v = fma(P.beta, ci[r * w.n + c], v);
+      P.C[off + r * w.n + c] = v;
+    }
+  }
+}
+
+__device__ __forceinline__ void emu_tile_blocks(const EmuParams &P, const WarpTask &w) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int r0 = w.mt * 16 + g, r1 = r0 + 8;
   const bool v0 = r0 < w.m, v1 = r1 < w.m;
@@ -451,16 +552,72 @@ __global__ void __launch_bounds__(256, 2) k_num_emu_bf16(EmuParams P, int64_t nw
   const int64_t off = P.c_off[w.c];
   const int cin = P.c_cin[w.c];
   const double *ci = (P.beta != 0.0 && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
+  const bool scale = P.alpha != 1.0;  // one FP64 compare per thread, not per element
 #pragma unroll
   for (int h = 0; h < 4; ++h) {
     const int r = h < 2 ? r0 : r1, c = (h & 1) ? cc1 : cc0;
     if (r < w.m && c < w.n) {
       double v = i64_ldexp(acc[h], ref[h] - (kSlices + 1) * kBeta + P.guard);
-      if (P.alpha != 1.0) v *= P.alpha;
+      if (scale) v *= P.alpha;
       if (ci) v = fma(P.beta, ci[r * w.n + c], v);
       P.C[off + r * w.n + c] = v;
     }
   }
+}
+
+__device__ __forceinline__ void emu_tile(const EmuParams &P, int64_t gw) {
+  const WarpTask w = find_task(P, gw);
+  if (P.row_scale)
+    emu_tile_rows(P, w);
+  else
+    emu_tile_blocks(P, w);
+}
+
+__global__ void __launch_bounds__(256, 2) k_num_emu_bf16(EmuParams P, int64_t nwarps) {
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (gw >= nwarps) return;
+  emu_tile(P, gw);
+}
+
+// persistent form over work items (plan << 32 | warp tile), ordered by decreasing cost
+template <class GetP>
+__device__ __forceinline__ void emu_persist_loop(const int64_t *__restrict__ items, int64_t nitems,
+                                                 unsigned long long *counter, GetP get) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1ull);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= (unsigned long long)nitems) return;
+    const int64_t v = items[it];
+    emu_tile(get(v >> 32), v & 0xffffffffll);
+  }
+}
+
+__global__ void __launch_bounds__(256, 2)
+    k_num_emu_bf16_persist1(EmuParams P, const int64_t *__restrict__ items, int64_t nitems,
+                            unsigned long long *counter) {
+  emu_persist_loop(items, nitems, counter, [&](int64_t) -> const EmuParams & { return P; });
+}
+
+__global__ void __launch_bounds__(256, 2)
+    k_num_emu_bf16_persist(const EmuParams *__restrict__ plans, const int64_t *__restrict__ items,
+                           int64_t nitems, unsigned long long *counter) {
+  emu_persist_loop(items, nitems, counter, [&](int64_t pl) -> const EmuParams & { return plans[pl]; });
+}
+
+// cost key of every 16 x 8 warp tile: flops of its C block's products / tiles, as the
+// descending-order key 63 - floor(log2(cost))
+__global__ void k_emu_item_keys(EmuParams P, int64_t nwarps, int64_t base, int64_t *items,
+                                int32_t *keys) {
+  const int64_t gw = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gw >= nwarps) return;
+  const WarpTask w = find_task(P, gw);
+  unsigned long long k = 0;
+  for (int q = 0; q < P.Dk; ++q)
+    k += (unsigned long long)P.run_len[(int64_t)w.c * P.Dk + q] * ((P.kval[q] + 15) & ~15);
+  keys[gw] = __clzll(k * 16ull * 8ull + 1ull);
+  items[gw] = base | gw;
 }
 
 __global__ void __launch_bounds__(256) k_num_tf32x3(EmuParams P, int64_t nwarps) {
@@ -524,6 +681,7 @@ __global__ void __launch_bounds__(256) k_num_tf32x3(EmuParams P, int64_t nwarps)
   const int64_t off = P.c_off[w.c];
   const int cin = P.c_cin[w.c];
   const double *ci = (P.beta != 0.0 && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
+  const bool scale = P.alpha != 1.0;
 #pragma unroll
   for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
@@ -532,7 +690,7 @@ __global__ void __launch_bounds__(256) k_num_tf32x3(EmuParams P, int64_t nwarps)
       slot_rc(w, nt, h, r, c);
       if (nt < w.ntn && r < w.m && c < w.n) {
         double v = f32_to_f64(hi[nt][h]) + f32_to_f64(lo[nt][h]);
-        if (P.alpha != 1.0) v *= P.alpha;
+        if (scale) v *= P.alpha;
         if (ci) v = fma(P.beta, ci[r * w.n + c], v);
         P.C[off + r * w.n + c] = v;
       }
@@ -692,19 +850,21 @@ void emu_state_free(bst_plan *p) {
   p->emu = nullptr;
 }
 
-void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
-  if (p->C->nblocks == 0) return;
-  EmuState &E = emu_state(p, s);
-  if (!E.dig_alloc) {
-    E.a_dig = E.ar.alloc_n<__nv_bfloat16>((size_t)E.a_dsize);
-    E.b_dig = E.ar.alloc_n<__nv_bfloat16>((size_t)E.b_dsize);
-    E.a_exp = E.ar.alloc_n<int32_t>((size_t)E.a_esize);
-    E.b_exp = E.ar.alloc_n<int32_t>((size_t)E.b_esize);
-    E.row_exp = E.ar.alloc_n<int32_t>((size_t)E.nrows);
-    E.col_exp = E.ar.alloc_n<int32_t>((size_t)E.ncols);
-    E.dig_alloc = true;
-  }
-  // slices of the current operand data (padding must read as zero)
+// digit buffers of a plan (allocated once; outside any stream capture)
+static void emu_alloc_digits(EmuState &E) {
+  if (E.dig_alloc) return;
+  E.a_dig = E.ar.alloc_n<__nv_bfloat16>((size_t)E.a_dsize);
+  E.b_dig = E.ar.alloc_n<__nv_bfloat16>((size_t)E.b_dsize);
+  E.a_exp = E.ar.alloc_n<int32_t>((size_t)E.a_esize);
+  E.b_exp = E.ar.alloc_n<int32_t>((size_t)E.b_esize);
+  E.row_exp = E.ar.alloc_n<int32_t>((size_t)E.nrows);
+  E.col_exp = E.ar.alloc_n<int32_t>((size_t)E.ncols);
+  E.dig_alloc = true;
+}
+
+// slices and exponents of the current operand data (launches only)
+static void emu_prepare(bst_plan *p, EmuState &E, const NumArgs &a, cudaStream_t s) {
+  // padding must read as zero
   BST_CUDA(cudaMemsetAsync(E.a_dig, 0, 2 * (size_t)std::max<int64_t>(E.a_dsize, 1), s));
   BST_CUDA(cudaMemsetAsync(E.b_dig, 0, 2 * (size_t)std::max<int64_t>(E.b_dsize, 1), s));
   fill_i32(E.a_exp, kExpNone, E.a_esize, s);
@@ -723,18 +883,93 @@ void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
     S.start = side ? E.b_colstart : E.a_rowstart;
     S.gexp = side ? E.col_exp : E.row_exp;
     S.dig = side ? E.b_dig : E.a_dig;
+    S.row_scale = p->ctx->tune_emu_row_scale;
     k_emu_exponents<<<nblk(X->nblocks, wpb), 32 * wpb, 0, s>>>(S);
     BST_CHECK_LAUNCH();
     k_emu_digits<<<nblk(X->nblocks, wpb), 32 * wpb, 0, s>>>(S);
     BST_CHECK_LAUNCH();
   }
+}
+
+static EmuParams bf16_params(bst_plan *p, const EmuState &E, const NumArgs &a) {
   EmuParams P = emu_params(p, E, a);
   P.a_doff = E.a_doff;
   P.b_doff = E.b_doff;
   P.wstart = E.wstart_b;
   P.tiles_n = 1;
+  P.row_scale = p->ctx->tune_emu_row_scale;
+  return P;
+}
+
+size_t emu_params_bytes() { return sizeof(EmuParams); }
+
+int64_t emu_item_count(bst_plan *p, cudaStream_t s) {
+  if (p->C->nblocks == 0) return 0;
+  EmuState &E = emu_state(p, s);
+  emu_alloc_digits(E);
+  return E.nwarps_b;
+}
+
+void emu_build_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys, cudaStream_t s) {
+  if (p->C->nblocks == 0) return;
+  EmuState &E = emu_state(p, s);
+  NumArgs a{};
+  EmuParams P = bf16_params(p, E, a);
   if (E.nwarps_b > 0) {
-    k_num_emu_bf16<<<nblk(E.nwarps_b, wpb), 32 * wpb, 0, s>>>(P, E.nwarps_b);
+    k_emu_item_keys<<<nblk(E.nwarps_b, 256), 256, 0, s>>>(P, E.nwarps_b, base, items, keys);
+    BST_CHECK_LAUNCH();
+  }
+}
+
+void emu_prepare_and_fill(bst_plan *p, const NumArgs &a, void *out, cudaStream_t s) {
+  EmuState &E = *p->emu;
+  emu_prepare(p, E, a, s);
+  EmuParams P = bf16_params(p, E, a);
+  std::memcpy(out, &P, sizeof(P));
+}
+
+int emu_persist_grid(int num_sms) {
+  int nb = 0;
+  BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_emu_bf16_persist, 256, 0));
+  return std::max(1, nb) * num_sms;
+}
+
+void launch_emu_persist(const void *params, const int64_t *items, int64_t nitems,
+                        unsigned long long *counter, int grid, cudaStream_t s) {
+  if (nitems == 0) return;
+  BST_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+  const int g = (int)std::min<int64_t>(grid, (nitems + 7) / 8);
+  k_num_emu_bf16_persist<<<g, 256, 0, s>>>(static_cast<const EmuParams *>(params), items, nitems,
+                                           counter);
+  BST_CHECK_LAUNCH();
+}
+
+void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
+  if (p->C->nblocks == 0) return;
+  EmuState &E = emu_state(p, s);
+  emu_alloc_digits(E);
+  if (!E.items) {
+    // warp tiles ordered by decreasing cost (built once per plan)
+    Arena scratch;
+    scratch.ctx = static_cast<Ctx *>(p->ctx);
+    scratch.stream = s;
+    int64_t *it0 = scratch.alloc_n<int64_t>((size_t)E.nwarps_b);
+    int32_t *keys = scratch.alloc_n<int32_t>((size_t)E.nwarps_b);
+    E.items = E.ar.alloc_n<int64_t>((size_t)E.nwarps_b);
+    E.counter = E.ar.alloc_n<unsigned long long>(1);
+    emu_build_items(p, 0, it0, keys, s);
+    sort_items(it0, keys, E.nwarps_b, E.items, scratch, s);
+    BST_CUDA(cudaStreamSynchronize(s));
+  }
+  emu_prepare(p, E, a, s);
+  const EmuParams P = bf16_params(p, E, a);
+  if (E.nwarps_b > 0) {
+    int nb = 0;
+    BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_emu_bf16_persist1, 256, 0));
+    const int g = (int)std::min<int64_t>((int64_t)std::max(1, nb) * p->ctx->num_sms,
+                                         (E.nwarps_b + 7) / 8);
+    BST_CUDA(cudaMemsetAsync(E.counter, 0, sizeof(unsigned long long), s));
+    k_num_emu_bf16_persist1<<<g, 256, 0, s>>>(P, E.items, E.nwarps_b, E.counter);
     BST_CHECK_LAUNCH();
   }
 }

@@ -19,6 +19,7 @@
 //     entries whose k block index lies in part s of the K range into a workspace
 //     slice; a second kernel adds the S slices in the fixed order 0..S-1.
 #include <algorithm>
+#include <cstring>
 
 #include "bst_internal.h"
 
@@ -132,11 +133,12 @@ __device__ __forceinline__ void task_mn(const NumParams &P, int c, int s) {
   }
   const int cin = P.c_cin[c];
   const double *ci = (P.beta != 0.0 && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
+  const bool scale = P.alpha != 1.0;  // skip the FP64 multiply when alpha == 1
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int o = lane + 32 * r;
     if (o < MN) {
-      double v = P.alpha * acc[r];
+      double v = scale ? P.alpha * acc[r] : acc[r];
       if (ci) v = fma(P.beta, ci[o], v);
       P.C[off + o] = v;
     }
@@ -196,12 +198,7 @@ __device__ void task_generic(const NumParams &P, int c, int s, int m, int n) {
   }
 }
 
-__global__ void __launch_bounds__(256, 2) k_num_fp64(NumParams P) {
-  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (gw >= P.ntasks * P.split) return;
-  const int64_t t = gw / P.split;
-  const int s = (int)(gw % P.split);
-  const int c = P.task_c[t];
+__device__ __forceinline__ void dispatch_task(const NumParams &P, int c, int s) {
   const int cls = P.c_cls[c];
   const int m = P.cls_m[cls], n = P.cls_n[cls];
 #define BST_MN(MM, NN) \
@@ -217,6 +214,72 @@ __global__ void __launch_bounds__(256, 2) k_num_fp64(NumParams P) {
   BST_MN(23, 23)
 #undef BST_MN
   task_generic(P, c, s, m, n);
+}
+
+// one warp per (C block, K part): used with split-K
+__global__ void __launch_bounds__(256, 2) k_num_fp64(NumParams P) {
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (gw >= P.ntasks * P.split) return;
+  const int64_t t = gw / P.split;
+  const int s = (int)(gw % P.split);
+  dispatch_task(P, P.task_c[t], s);
+}
+
+// Persistent form: a grid sized to fill the GPU once; every warp takes the next work
+// item (plan << 32 | C block) from a global counter until the list is exhausted.  The
+// items are ordered by decreasing cost, so the long C blocks start first and the warps
+// finish together -- with one launch-time task per warp, a CTA holding one long task
+// would keep its SM slot while its other warps sat idle.  No waits: a warp that finds
+// the counter past the end returns.
+template <class GetP>
+__device__ __forceinline__ void persist_loop(const int64_t *__restrict__ items, int64_t nitems,
+                                             unsigned long long *counter, GetP get) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1ull);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= (unsigned long long)nitems) return;
+    const int64_t v = items[it];
+    dispatch_task(get(v >> 32), (int)(v & 0xffffffffll), 0);
+  }
+}
+
+// one plan, parameters by value
+__global__ void __launch_bounds__(256, 2)
+    k_num_fp64_persist1(NumParams P, const int64_t *__restrict__ items, int64_t nitems,
+                        unsigned long long *counter) {
+  persist_loop(items, nitems, counter, [&](int64_t) -> const NumParams & { return P; });
+}
+
+// many plans (a batch), parameters in device memory
+__global__ void __launch_bounds__(256, 2)
+    k_num_fp64_persist(const NumParams *__restrict__ plans, const int64_t *__restrict__ items,
+                       int64_t nitems, unsigned long long *counter) {
+  persist_loop(items, nitems, counter, [&](int64_t pl) -> const NumParams & { return plans[pl]; });
+}
+
+// cost of every C block of one plan (flops of its products) as a descending-order key:
+// key = 63 - floor(log2(cost)), so a stable partition on the key lists costly blocks first
+__global__ void k_task_cost_keys(int64_t nc, int32_t Dk, const int32_t *__restrict__ run_len,
+                                 const int32_t *__restrict__ kval, const int32_t *__restrict__ c_cls,
+                                 const int32_t *__restrict__ cls_m, const int32_t *__restrict__ cls_n,
+                                 int64_t item_base, int64_t *__restrict__ item,
+                                 int32_t *__restrict__ key) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  unsigned long long k = 0;
+  for (int q = 0; q < Dk; ++q) k += (unsigned long long)run_len[c * Dk + q] * kval[q];
+  const int cls = c_cls[c];
+  const unsigned long long cost = k * (unsigned long long)cls_m[cls] * cls_n[cls] + 1ull;
+  key[c] = __clzll(cost);  // 63 - floor(log2(cost)) = leading zeros
+  item[c] = item_base | c;
+}
+
+__global__ void k_gather_items(const int64_t *__restrict__ in, const int32_t *__restrict__ perm,
+                               int64_t n, int64_t *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[perm[i]];
 }
 
 // C = alpha * sum_{s=0..S-1} W_s + beta * C_in, one warp per C block
@@ -239,7 +302,89 @@ __global__ void k_splitk_reduce(NumParams P, int64_t nc, const int32_t *__restri
   }
 }
 
+NumParams make_params(bst_plan *p, const NumArgs &a, int split) {
+  NumParams P;
+  P.A = a.A;
+  P.B = a.B;
+  P.Cin = a.Cin;
+  P.C = a.C;
+  P.W = nullptr;
+  P.alpha = a.alpha;
+  P.beta = a.beta;
+  P.nelemC = p->C->nelem;
+  P.ntasks = p->C->nblocks;
+  P.split = std::max(1, split);
+  P.K = p->K;
+  P.Dk = p->Dk;
+  P.ta = p->ta;
+  P.tb = p->tb;
+  P.task_c = p->task_c;
+  P.c_cls = p->c_cls;
+  P.c_cin = p->c_cin;
+  P.c_off = p->C->off;
+  P.cin_off = p->Cin ? p->Cin->off : nullptr;
+  P.run_start = p->run_start;
+  P.run_len = p->run_len;
+  P.s_a = p->s_a;
+  P.s_b = p->s_b;
+  P.s_k = p->s_k;
+  P.cls_m = p->cls_m;
+  P.cls_n = p->cls_n;
+  P.kval = p->kval;
+  return P;
+}
+
 }  // namespace
+
+size_t num_params_bytes() { return sizeof(NumParams); }
+
+void fill_num_params(bst_plan *p, const NumArgs &a, void *out) {
+  NumParams P = make_params(p, a, 1);
+  std::memcpy(out, &P, sizeof(P));
+}
+
+// Work items of one plan's C blocks, ordered by decreasing cost; item = base | c.
+void build_cost_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys, Arena &scratch,
+                      cudaStream_t s) {
+  const int64_t nc = p->C->nblocks;
+  if (nc == 0) return;
+  k_task_cost_keys<<<nblk(nc, 256), 256, 0, s>>>(nc, p->Dk, p->run_len, p->kval, p->c_cls,
+                                                 p->cls_m, p->cls_n, base, items, keys);
+  BST_CHECK_LAUNCH();
+}
+
+void sort_items(int64_t *items, const int32_t *keys, int64_t n, int64_t *out, Arena &scratch,
+                cudaStream_t s) {
+  if (n == 0) return;
+  int32_t *perm = scratch.alloc_n<int32_t>((size_t)n);
+  int32_t *kp = scratch.alloc_n<int32_t>(65);
+  stable_partition(keys, n, 64, perm, kp, scratch, s);
+  k_gather_items<<<nblk(n, 256), 256, 0, s>>>(items, perm, n, out);
+  BST_CHECK_LAUNCH();
+}
+
+int persist_grid(int num_sms) {
+  int nb = 0;
+  BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_fp64_persist, 256, 0));
+  return std::max(1, nb) * num_sms;
+}
+
+int persist1_grid(int num_sms) {
+  int nb = 0;
+  BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_fp64_persist1, 256, 0));
+  return std::max(1, nb) * num_sms;
+}
+
+void launch_fp64_persist(const void *params, const int64_t *items, int64_t nitems,
+                         unsigned long long *counter, int grid, cudaStream_t s) {
+  if (nitems == 0) return;
+  BST_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+  const int64_t need = (nitems + 7) / 8;
+  const int g = (int)std::min<int64_t>(grid, need);
+  k_num_fp64_persist<<<g, 256, 0, s>>>(static_cast<const NumParams *>(params), items, nitems,
+                                       counter);
+  BST_CHECK_LAUNCH();
+}
 
 int choose_split(const bst_plan *p, int num_sms) {
   const int64_t nc = p->C->nblocks;
@@ -256,6 +401,14 @@ int choose_split(const bst_plan *p, int num_sms) {
 void execute_fp64(bst_plan *p, const NumArgs &a, int split, cudaStream_t s) {
   const int64_t nc = p->C->nblocks;
   if (nc == 0) return;
+  if (split <= 1 && p->items) {
+    BST_CUDA(cudaMemsetAsync(p->items_counter, 0, sizeof(unsigned long long), s));
+    const int64_t need = (nc + 7) / 8;
+    const int g = (int)std::min<int64_t>(persist1_grid(p->ctx->num_sms), need);
+    k_num_fp64_persist1<<<g, 256, 0, s>>>(make_params(p, a, 1), p->items, nc, p->items_counter);
+    BST_CHECK_LAUNCH();
+    return;
+  }
   NumParams P;
   P.A = a.A;
   P.B = a.B;
