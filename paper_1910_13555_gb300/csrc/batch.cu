@@ -2,10 +2,10 @@
 //
 // A batch holds plans that were built with bst_multiply_plan / bst_contract_plan
 // (their symbolic phases are done).  Its work list is every C block of every plan
-// (every 16 x 8 warp tile for emulated FP64), tagged with the plan's index and ordered
-// by decreasing cost across the whole batch, so one persistent grid balances products
-// of very different sizes (longest-processing-time first, dynamic fetch from one
-// counter).  bst_batch_execute only queues work: a parameter copy from the batch's
+// (every 16 x 8 warp tile for emulated FP64), tagged with the plan's index; plans are
+// listed by decreasing flops and each plan's C blocks in CSR order, and warps fetch
+// items dynamically from one counter, so one persistent grid balances products of very
+// different sizes while neighbouring warps keep sharing operand blocks.  bst_batch_execute only queues work: a parameter copy from the batch's
 // pinned staging buffer, the counter reset and the launches (plus the per-plan slicing
 // kernels for emulated FP64 and the permutations of contraction views), so a call can be
 // captured into a CUDA graph and replayed; everything that allocates or synchronises
@@ -21,14 +21,14 @@ struct bst_batch {
   bst_ctx *ctx = nullptr;
   std::vector<bst_plan *> plans;
   bst::Arena ar;
-  // native FP64 schedule
+  // native FP64 schedule (item = plan << 32 | C block)
   int64_t n_items = 0;
   int64_t *items = nullptr;
   unsigned long long *counter = nullptr;
   void *d_params = nullptr, *h_params = nullptr;
   size_t pbytes = 0;
   int grid = 0;
-  // emulated FP64 schedule
+  // emulated FP64 schedule (item = plan << 48 | C block << 16 | tile)
   int64_t n_items_e = 0;
   int64_t *items_e = nullptr;
   void *d_eparams = nullptr, *h_eparams = nullptr;
@@ -93,13 +93,20 @@ bst_status bst_batch_create(bst_ctx *ctx, int32_t n, bst_plan *const *plans, bst
       bst::Arena scratch;
       scratch.ctx = b->ar.ctx;
       scratch.stream = s;
-      // native FP64: every C block of every plan
+      // plans by decreasing flops (the longest problems start first); inside a plan,
+      // C blocks in CSR order for locality
+      std::vector<int32_t> order(n);
+      for (int32_t q = 0; q < n; ++q) order[q] = q;
+      std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return b->plans[x]->stats.flops > b->plans[y]->stats.flops;
+      });
+      // native FP64: every C block of every plan, by decreasing cost across the batch
       for (auto *p : b->plans) b->n_items += p->C->nblocks;
       int64_t *it0 = scratch.alloc_n<int64_t>((size_t)b->n_items);
       int32_t *keys = scratch.alloc_n<int32_t>((size_t)b->n_items);
       int64_t off = 0;
-      for (int32_t q = 0; q < n; ++q) {
-        bst::build_cost_items(b->plans[q], (int64_t)q << 32, it0 + off, keys + off, scratch, s);
+      for (int32_t q : order) {
+        bst::build_plan_items(b->plans[q], (int64_t)q << 32, it0 + off, keys + off, s);
         off += b->plans[q]->C->nblocks;
       }
       b->items = b->ar.alloc_n<int64_t>((size_t)b->n_items);
@@ -115,15 +122,12 @@ bst_status bst_batch_create(bst_ctx *ctx, int32_t n, bst_plan *const *plans, bst
         cnt[q] = b->plans[q]->contract ? 0 : bst::emu_item_count(b->plans[q], s);
         b->n_items_e += cnt[q];
       }
-      int64_t *ie0 = scratch.alloc_n<int64_t>((size_t)b->n_items_e);
-      int32_t *ke = scratch.alloc_n<int32_t>((size_t)b->n_items_e);
+      b->items_e = b->ar.alloc_n<int64_t>((size_t)b->n_items_e);
       off = 0;
-      for (int32_t q = 0; q < n; ++q) {
-        if (cnt[q]) bst::emu_build_items(b->plans[q], (int64_t)q << 32, ie0 + off, ke + off, s);
+      for (int32_t q : order) {
+        if (cnt[q]) bst::emu_build_items(b->plans[q], (int64_t)q << 48, b->items_e + off, s);
         off += cnt[q];
       }
-      b->items_e = b->ar.alloc_n<int64_t>((size_t)b->n_items_e);
-      bst::sort_items(ie0, ke, b->n_items_e, b->items_e, scratch, s);
       b->epbytes = bst::emu_params_bytes();
       b->d_eparams = b->ar.alloc(b->epbytes * n);
       BST_CUDA(cudaMallocHost(&b->h_eparams, b->epbytes * n));
@@ -174,7 +178,8 @@ bst_status bst_batch_execute(bst_batch *b, const double *alpha, const double *be
                                     static_cast<char *>(b->h_eparams) + q * b->epbytes, s);
       }
       BST_CUDA(cudaMemcpyAsync(b->d_eparams, b->h_eparams, b->epbytes * n, cudaMemcpyHostToDevice, s));
-      bst::launch_emu_persist(b->d_eparams, b->items_e, b->n_items_e, b->counter, b->grid_e, s);
+      bst::launch_emu_persist(b->d_eparams, b->items_e, b->n_items_e, b->counter, b->grid_e,
+                              b->ctx->tune_emu_row_scale, s);
     }
     for (int32_t q = 0; q < n; ++q) {
       if (b->plans[q]->contract) bst::contract_finish(b->plans[q], s);

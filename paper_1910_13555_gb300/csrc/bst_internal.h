@@ -214,7 +214,7 @@ struct bst_plan {
   int32_t *task_c = nullptr;
   std::vector<int32_t> h_class_ptr;   // Dm*Dn + 1
   int32_t *class_ptr = nullptr;
-  // persistent numeric schedule: C blocks by decreasing cost (item = C block index)
+  // persistent numeric schedule: C blocks by decreasing cost, counter of taken items
   int64_t *items = nullptr;
   unsigned long long *items_counter = nullptr;
   // stats
@@ -260,9 +260,8 @@ int choose_split(const bst_plan *p, int num_sms);
 // persistent FP64 numeric (numeric_fp64.cu)
 size_t num_params_bytes();
 void fill_num_params(bst_plan *p, const NumArgs &a, void *out);
-void build_cost_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys, Arena &scratch,
-                      cudaStream_t s);
-void sort_items(int64_t *items, const int32_t *keys, int64_t n, int64_t *out, Arena &scratch,
+void build_plan_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys, cudaStream_t s);
+void sort_items(const int64_t *items, const int32_t *keys, int64_t n, int64_t *out, Arena &scratch,
                 cudaStream_t s);
 int persist_grid(int num_sms);
 void launch_fp64_persist(const void *params, const int64_t *items, int64_t nitems,
@@ -270,10 +269,10 @@ void launch_fp64_persist(const void *params, const int64_t *items, int64_t nitem
 // persistent emulated-FP64 numeric (numeric_emu.cu)
 size_t emu_params_bytes();
 int64_t emu_item_count(bst_plan *p, cudaStream_t s);
-void emu_build_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys, cudaStream_t s);
+void emu_build_items(bst_plan *p, int64_t base, int64_t *items, cudaStream_t s);
 void emu_prepare_and_fill(bst_plan *p, const NumArgs &a, void *out, cudaStream_t s);
 int emu_persist_grid(int num_sms);
 void launch_emu_persist(const void *params, const int64_t *items, int64_t nitems,
-                        unsigned long long *counter, int grid, cudaStream_t s);
+                        unsigned long long *counter, int grid, int row_scale, cudaStream_t s);
 
 }  // namespace bst

@@ -70,6 +70,8 @@ struct EmuState {
   float *a_tf = nullptr, *b_tf = nullptr;
   int32_t *a_exp = nullptr, *b_exp = nullptr;
   bool dig_alloc = false, tf_alloc = false;
+  // per stack entry: offsets of its A and B digit blocks
+  int64_t *e_adoff = nullptr, *e_bdoff = nullptr;
   // persistent schedule of the BF16 warp tiles
   int64_t *items = nullptr;
   unsigned long long *counter = nullptr;
@@ -232,6 +234,16 @@ __global__ void k_side_sizes(SideArgs S, int64_t *dsz, int64_t *tsz, int64_t *es
   esz[b] = nouter;
 }
 
+__global__ void k_entry_doffs(int64_t T, const int32_t *__restrict__ s_ab,
+                              const int32_t *__restrict__ s_bb, const int64_t *__restrict__ a_doff,
+                              const int64_t *__restrict__ b_doff, int64_t *__restrict__ ea,
+                              int64_t *__restrict__ eb) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= T) return;
+  ea[e] = a_doff[s_ab[e]];
+  eb[e] = b_doff[s_bb[e]];
+}
+
 // largest sum of inner sizes over the products of one C block
 __global__ void k_max_ktot(int64_t nc, int32_t Dk, const int32_t *run_len, const int32_t *kval,
                            unsigned long long *out) {
@@ -292,6 +304,17 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   return __longlong_as_double((long long)bits);
 }
 
+// an integer-valued binary32 x with |x| < 2^24 as an int, read from its encoding
+// (value = significand * 2^(exponent - 150)); integer operations only
+__device__ __forceinline__ int f32_exact_int(float x) {
+  const unsigned b = __float_as_uint(x);
+  const int e = (int)((b >> 23) & 0xffu);
+  const unsigned m = (b & 0x7fffffu) | 0x800000u;
+  const int sh = 150 - e;
+  const int v = (e < 127) ? 0 : (int)(m >> sh);
+  return (b >> 31) ? -v : v;
+}
+
 __device__ __forceinline__ long long round_shift(long long v, int sh) {
   if (sh <= 0) return v;
   if (sh >= 62) return 0;
@@ -311,9 +334,10 @@ struct EmuParams {
   const int64_t *a_rowstart, *b_colstart;
   const int32_t *row_exp, *col_exp;
   const int32_t *class_ptr, *task_c, *cls_m, *cls_n, *kval;
-  const int32_t *c_row, *c_col, *c_cin;
+  const int32_t *c_row, *c_col, *c_cin, *c_cls;
   const int64_t *c_off, *cin_off;
   const int32_t *run_start, *run_len, *s_ab, *s_bb;
+  const int64_t *e_adoff, *e_bdoff;  // per entry digit offsets (row-scaled kernel)
   const int64_t *a_doff, *b_doff, *a_eoff, *b_eoff;
   const __nv_bfloat16 *a_dig, *b_dig;
   const float *a_tf, *b_tf;
@@ -418,7 +442,7 @@ __device__ __forceinline__ void emu_tile_rows(const EmuParams &P, const WarpTask
       long long I = 0;
 #pragma unroll
       for (int s = 0; s < kSlices; ++s) {
-        I += (long long)__float2int_rn(accw[s][h]) << (kBeta * (kSlices - 1 - s));
+        I += (long long)f32_exact_int(accw[s][h]) << (kBeta * (kSlices - 1 - s));
         accw[s][h] = 0.f;
       }
       acc[h] += round_shift(I, P.guard);
@@ -432,9 +456,14 @@ __device__ __forceinline__ void emu_tile_rows(const EmuParams &P, const WarpTask
     const int e0 = P.run_start[rr];
     const int k = P.kval[kc], kp = (k + 15) & ~15, nch = kp >> 4;
     const int64_t pa = (int64_t)w.m * kp, pb = (int64_t)w.n * kp;
+    int64_t ao = P.e_adoff[e0], bo = P.e_bdoff[e0];
     for (int e = e0; e < e0 + len; ++e) {
-      const __nv_bfloat16 *Ad = P.a_dig + P.a_doff[P.s_ab[e]];
-      const __nv_bfloat16 *Bd = P.b_dig + P.b_doff[P.s_bb[e]];
+      const __nv_bfloat16 *Ad = P.a_dig + ao;
+      const __nv_bfloat16 *Bd = P.b_dig + bo;
+      if (e + 1 < e0 + len) {  // next entry's offsets, loaded ahead of this entry's MMAs
+        ao = P.e_adoff[e + 1];
+        bo = P.e_bdoff[e + 1];
+      }
       for (int ch = 0; ch < nch; ++ch) {
         if (used == kSegChunks) fold();
         uint32_t af[kSlices][4];
@@ -543,7 +572,7 @@ __device__ __forceinline__ void emu_tile_blocks(const EmuParams &P, const WarpTa
           long long I = 0;
 #pragma unroll
           for (int s = 0; s < kSlices; ++s)
-            I += (long long)__float2int_rn(accw[s][h]) << (kBeta * (kSlices - 1 - s));
+            I += (long long)f32_exact_int(accw[s][h]) << (kBeta * (kSlices - 1 - s));
           acc[h] += round_shift(I, ref[h] - eas[h] + P.guard);
         }
       }
@@ -565,22 +594,32 @@ __device__ __forceinline__ void emu_tile_blocks(const EmuParams &P, const WarpTa
   }
 }
 
-__device__ __forceinline__ void emu_tile(const EmuParams &P, int64_t gw) {
-  const WarpTask w = find_task(P, gw);
-  if (P.row_scale)
+// A BF16 work item is one 16 x 8 warp tile of one C block:
+//   item = plan << 48 | C block << 16 | row tile << 8 | column tile.
+// Items are listed in C block (CSR) order, so consecutive warps work on neighbouring C
+// blocks of one block row and share its op(A) digits in L1/L2.
+__device__ __forceinline__ WarpTask task_of_item(const EmuParams &P, int64_t v) {
+  WarpTask w;
+  w.c = (int)((v >> 16) & 0xffffffffll);
+  w.mt = (int)((v >> 8) & 0xff);
+  w.ng = (int)(v & 0xff);
+  const int cls = P.c_cls[w.c];
+  w.m = P.cls_m[cls];
+  w.n = P.cls_n[cls];
+  w.ntn = min(P.tiles_n, ((w.n + 7) >> 3) - P.tiles_n * w.ng);
+  return w;
+}
+
+template <int ROWS>
+__device__ __forceinline__ void emu_tile(const EmuParams &P, const WarpTask &w) {
+  if (ROWS)
     emu_tile_rows(P, w);
   else
     emu_tile_blocks(P, w);
 }
 
-__global__ void __launch_bounds__(256, 2) k_num_emu_bf16(EmuParams P, int64_t nwarps) {
-  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (gw >= nwarps) return;
-  emu_tile(P, gw);
-}
-
-// persistent form over work items (plan << 32 | warp tile), ordered by decreasing cost
-template <class GetP>
+// persistent: every warp takes the next item from one counter until the list is done
+template <int ROWS, class GetP>
 __device__ __forceinline__ void emu_persist_loop(const int64_t *__restrict__ items, int64_t nitems,
                                                  unsigned long long *counter, GetP get) {
   const int lane = threadIdx.x & 31;
@@ -590,34 +629,47 @@ __device__ __forceinline__ void emu_persist_loop(const int64_t *__restrict__ ite
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= (unsigned long long)nitems) return;
     const int64_t v = items[it];
-    emu_tile(get(v >> 32), v & 0xffffffffll);
+    const EmuParams &P = get(v >> 48);
+    emu_tile<ROWS>(P, task_of_item(P, v));
   }
 }
 
+template <int ROWS>
 __global__ void __launch_bounds__(256, 2)
     k_num_emu_bf16_persist1(EmuParams P, const int64_t *__restrict__ items, int64_t nitems,
                             unsigned long long *counter) {
-  emu_persist_loop(items, nitems, counter, [&](int64_t) -> const EmuParams & { return P; });
+  emu_persist_loop<ROWS>(items, nitems, counter, [&](int64_t) -> const EmuParams & { return P; });
 }
 
+template <int ROWS>
 __global__ void __launch_bounds__(256, 2)
     k_num_emu_bf16_persist(const EmuParams *__restrict__ plans, const int64_t *__restrict__ items,
                            int64_t nitems, unsigned long long *counter) {
-  emu_persist_loop(items, nitems, counter, [&](int64_t pl) -> const EmuParams & { return plans[pl]; });
+  emu_persist_loop<ROWS>(items, nitems, counter,
+                         [&](int64_t pl) -> const EmuParams & { return plans[pl]; });
 }
 
-// cost key of every 16 x 8 warp tile: flops of its C block's products / tiles, as the
-// descending-order key 63 - floor(log2(cost))
-__global__ void k_emu_item_keys(EmuParams P, int64_t nwarps, int64_t base, int64_t *items,
-                                int32_t *keys) {
-  const int64_t gw = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gw >= nwarps) return;
-  const WarpTask w = find_task(P, gw);
-  unsigned long long k = 0;
-  for (int q = 0; q < P.Dk; ++q)
-    k += (unsigned long long)P.run_len[(int64_t)w.c * P.Dk + q] * ((P.kval[q] + 15) & ~15);
-  keys[gw] = __clzll(k * 16ull * 8ull + 1ull);
-  items[gw] = base | gw;
+// warp tiles of every C block (16 x 8 per tile)
+__global__ void k_emu_tile_counts(int64_t nc, const int32_t *__restrict__ c_cls,
+                                  const int32_t *__restrict__ cls_m, const int32_t *__restrict__ cls_n,
+                                  int32_t *__restrict__ cnt) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int cls = c_cls[c];
+  cnt[c] = ((cls_m[cls] + 15) >> 4) * ((cls_n[cls] + 7) >> 3);
+}
+
+__global__ void k_emu_tile_fill(int64_t nc, const int32_t *__restrict__ c_cls,
+                                const int32_t *__restrict__ cls_m, const int32_t *__restrict__ cls_n,
+                                const int64_t *__restrict__ start, int64_t base,
+                                int64_t *__restrict__ items) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int cls = c_cls[c];
+  const int MT = (cls_m[cls] + 15) >> 4, NT = (cls_n[cls] + 7) >> 3;
+  int64_t q = start[c];
+  for (int mt = 0; mt < MT; ++mt)
+    for (int ng = 0; ng < NT; ++ng) items[q++] = base | (c << 16) | ((int64_t)mt << 8) | ng;
 }
 
 __global__ void __launch_bounds__(256) k_num_tf32x3(EmuParams P, int64_t nwarps) {
@@ -745,6 +797,13 @@ void emu_index(bst_plan *p, EmuState &E, cudaStream_t s) {
   };
   side(p->A, p->ta, false, E.a_doff, E.a_toff, E.a_eoff, E.a_dsize, E.a_tsize, E.a_esize);
   side(p->B, p->tb, true, E.b_doff, E.b_toff, E.b_eoff, E.b_dsize, E.b_tsize, E.b_esize);
+  E.e_adoff = ar.alloc_n<int64_t>((size_t)p->T);
+  E.e_bdoff = ar.alloc_n<int64_t>((size_t)p->T);
+  if (p->T > 0) {
+    k_entry_doffs<<<nblk(p->T, 256), 256, 0, s>>>(p->T, p->s_ab, p->s_bb, E.a_doff, E.b_doff,
+                                                  E.e_adoff, E.e_bdoff);
+    BST_CHECK_LAUNCH();
+  }
   // warps per (m,n) class: one per 16-row x 16-column tile of each C block (3xTF32),
   // one per 16-row x 8-column tile (BF16 slices)
   const int32_t ncls = p->Dm * p->Dn;
@@ -824,6 +883,7 @@ EmuParams emu_params(bst_plan *p, const EmuState &E, const NumArgs &a) {
   P.cls_n = p->cls_n;
   P.kval = p->kval;
   P.c_row = p->C->row;
+  P.c_cls = p->c_cls;
   P.c_col = p->C->col;
   P.c_cin = p->c_cin;
   P.c_off = p->C->off;
@@ -832,6 +892,8 @@ EmuParams emu_params(bst_plan *p, const EmuState &E, const NumArgs &a) {
   P.run_len = p->run_len;
   P.s_ab = p->s_ab;
   P.s_bb = p->s_bb;
+  P.e_adoff = E.e_adoff;
+  P.e_bdoff = E.e_bdoff;
   P.a_eoff = E.a_eoff;
   P.b_eoff = E.b_eoff;
   P.a_dig = E.a_dig;
@@ -910,15 +972,21 @@ int64_t emu_item_count(bst_plan *p, cudaStream_t s) {
   return E.nwarps_b;
 }
 
-void emu_build_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys, cudaStream_t s) {
-  if (p->C->nblocks == 0) return;
-  EmuState &E = emu_state(p, s);
-  NumArgs a{};
-  EmuParams P = bf16_params(p, E, a);
-  if (E.nwarps_b > 0) {
-    k_emu_item_keys<<<nblk(E.nwarps_b, 256), 256, 0, s>>>(P, E.nwarps_b, base, items, keys);
-    BST_CHECK_LAUNCH();
-  }
+// the BF16 warp tiles of a plan in C block order; item = base | c << 16 | mt << 8 | nt
+void emu_build_items(bst_plan *p, int64_t base, int64_t *items, cudaStream_t s) {
+  const int64_t nc = p->C->nblocks;
+  if (nc == 0) return;
+  Arena scratch;
+  scratch.ctx = static_cast<Ctx *>(p->ctx);
+  scratch.stream = s;
+  int32_t *cnt = scratch.alloc_n<int32_t>((size_t)nc);
+  int64_t *start = scratch.alloc_n<int64_t>((size_t)nc + 1);
+  k_emu_tile_counts<<<nblk(nc, 256), 256, 0, s>>>(nc, p->c_cls, p->cls_m, p->cls_n, cnt);
+  BST_CHECK_LAUNCH();
+  exscan_i32_i64(cnt, start, nc, scratch, s);
+  k_emu_tile_fill<<<nblk(nc, 256), 256, 0, s>>>(nc, p->c_cls, p->cls_m, p->cls_n, start, base, items);
+  BST_CHECK_LAUNCH();
+  BST_CUDA(cudaStreamSynchronize(s));
 }
 
 void emu_prepare_and_fill(bst_plan *p, const NumArgs &a, void *out, cudaStream_t s) {
@@ -929,18 +997,22 @@ void emu_prepare_and_fill(bst_plan *p, const NumArgs &a, void *out, cudaStream_t
 }
 
 int emu_persist_grid(int num_sms) {
-  int nb = 0;
-  BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_emu_bf16_persist, 256, 0));
-  return std::max(1, nb) * num_sms;
+  int nb0 = 0, nb1 = 0;
+  BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, k_num_emu_bf16_persist<0>, 256, 0));
+  BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_num_emu_bf16_persist<1>, 256, 0));
+  return std::max(1, std::min(nb0, nb1)) * num_sms;
 }
 
 void launch_emu_persist(const void *params, const int64_t *items, int64_t nitems,
-                        unsigned long long *counter, int grid, cudaStream_t s) {
+                        unsigned long long *counter, int grid, int row_scale, cudaStream_t s) {
   if (nitems == 0) return;
   BST_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
   const int g = (int)std::min<int64_t>(grid, (nitems + 7) / 8);
-  k_num_emu_bf16_persist<<<g, 256, 0, s>>>(static_cast<const EmuParams *>(params), items, nitems,
-                                           counter);
+  const EmuParams *P = static_cast<const EmuParams *>(params);
+  if (row_scale)
+    k_num_emu_bf16_persist<1><<<g, 256, 0, s>>>(P, items, nitems, counter);
+  else
+    k_num_emu_bf16_persist<0><<<g, 256, 0, s>>>(P, items, nitems, counter);
   BST_CHECK_LAUNCH();
 }
 
@@ -949,27 +1021,26 @@ void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
   EmuState &E = emu_state(p, s);
   emu_alloc_digits(E);
   if (!E.items) {
-    // warp tiles ordered by decreasing cost (built once per plan)
-    Arena scratch;
-    scratch.ctx = static_cast<Ctx *>(p->ctx);
-    scratch.stream = s;
-    int64_t *it0 = scratch.alloc_n<int64_t>((size_t)E.nwarps_b);
-    int32_t *keys = scratch.alloc_n<int32_t>((size_t)E.nwarps_b);
+    // warp tiles in C block order (built once per plan)
     E.items = E.ar.alloc_n<int64_t>((size_t)E.nwarps_b);
     E.counter = E.ar.alloc_n<unsigned long long>(1);
-    emu_build_items(p, 0, it0, keys, s);
-    sort_items(it0, keys, E.nwarps_b, E.items, scratch, s);
-    BST_CUDA(cudaStreamSynchronize(s));
+    emu_build_items(p, 0, E.items, s);
   }
   emu_prepare(p, E, a, s);
   const EmuParams P = bf16_params(p, E, a);
   if (E.nwarps_b > 0) {
     int nb = 0;
-    BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_emu_bf16_persist1, 256, 0));
+    if (P.row_scale)
+      BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_emu_bf16_persist1<1>, 256, 0));
+    else
+      BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_emu_bf16_persist1<0>, 256, 0));
     const int g = (int)std::min<int64_t>((int64_t)std::max(1, nb) * p->ctx->num_sms,
                                          (E.nwarps_b + 7) / 8);
     BST_CUDA(cudaMemsetAsync(E.counter, 0, sizeof(unsigned long long), s));
-    k_num_emu_bf16_persist1<<<g, 256, 0, s>>>(P, E.items, E.nwarps_b, E.counter);
+    if (P.row_scale)
+      k_num_emu_bf16_persist1<1><<<g, 256, 0, s>>>(P, E.items, E.nwarps_b, E.counter);
+    else
+      k_num_emu_bf16_persist1<0><<<g, 256, 0, s>>>(P, E.items, E.nwarps_b, E.counter);
     BST_CHECK_LAUNCH();
   }
 }

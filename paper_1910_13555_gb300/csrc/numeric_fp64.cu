@@ -133,15 +133,20 @@ __device__ __forceinline__ void task_mn(const NumParams &P, int c, int s) {
   }
   const int cin = P.c_cin[c];
   const double *ci = (P.beta != 0.0 && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
-  const bool scale = P.alpha != 1.0;  // skip the FP64 multiply when alpha == 1
+  if (P.alpha != 1.0 || ci) {
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int o = lane + 32 * r;
-    if (o < MN) {
-      double v = scale ? P.alpha * acc[r] : acc[r];
-      if (ci) v = fma(P.beta, ci[o], v);
-      P.C[off + o] = v;
+    for (int r = 0; r < R; ++r) {
+      const int o = lane + 32 * r;
+      if (o < MN) {
+        double v = P.alpha * acc[r];
+        if (ci) v = fma(P.beta, ci[o], v);
+        P.C[off + o] = v;
+      }
     }
+  } else {  // alpha == 1, no C_in: store the sums without an FP64 multiply
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (lane + 32 * r < MN) P.C[off + lane + 32 * r] = acc[r];
   }
 }
 
@@ -259,21 +264,23 @@ __global__ void __launch_bounds__(256, 2)
   persist_loop(items, nitems, counter, [&](int64_t pl) -> const NumParams & { return plans[pl]; });
 }
 
-// cost of every C block of one plan (flops of its products) as a descending-order key:
-// key = 63 - floor(log2(cost)), so a stable partition on the key lists costly blocks first
+__global__ void k_plan_items(int64_t nc, int64_t base, int64_t *__restrict__ item) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc) item[c] = base | c;
+}
+
+// cost of every C block (flops of its products) as a descending-order key
+// 63 - floor(log2(cost)): a stable partition on it lists costly blocks first
 __global__ void k_task_cost_keys(int64_t nc, int32_t Dk, const int32_t *__restrict__ run_len,
                                  const int32_t *__restrict__ kval, const int32_t *__restrict__ c_cls,
                                  const int32_t *__restrict__ cls_m, const int32_t *__restrict__ cls_n,
-                                 int64_t item_base, int64_t *__restrict__ item,
                                  int32_t *__restrict__ key) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   unsigned long long k = 0;
   for (int q = 0; q < Dk; ++q) k += (unsigned long long)run_len[c * Dk + q] * kval[q];
   const int cls = c_cls[c];
-  const unsigned long long cost = k * (unsigned long long)cls_m[cls] * cls_n[cls] + 1ull;
-  key[c] = __clzll(cost);  // 63 - floor(log2(cost)) = leading zeros
-  item[c] = item_base | c;
+  key[c] = __clzll(k * (unsigned long long)cls_m[cls] * cls_n[cls] + 1ull);
 }
 
 __global__ void k_gather_items(const int64_t *__restrict__ in, const int32_t *__restrict__ perm,
@@ -343,17 +350,22 @@ void fill_num_params(bst_plan *p, const NumArgs &a, void *out) {
   std::memcpy(out, &P, sizeof(P));
 }
 
-// Work items of one plan's C blocks, ordered by decreasing cost; item = base | c.
-void build_cost_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys, Arena &scratch,
-                      cudaStream_t s) {
+// Work items of one plan's C blocks in CSR order (item = base | c) and their
+// decreasing-cost keys.
+void build_plan_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys, cudaStream_t s) {
   const int64_t nc = p->C->nblocks;
   if (nc == 0) return;
-  k_task_cost_keys<<<nblk(nc, 256), 256, 0, s>>>(nc, p->Dk, p->run_len, p->kval, p->c_cls,
-                                                 p->cls_m, p->cls_n, base, items, keys);
+  k_plan_items<<<nblk(nc, 256), 256, 0, s>>>(nc, base, items);
   BST_CHECK_LAUNCH();
+  if (keys) {
+    k_task_cost_keys<<<nblk(nc, 256), 256, 0, s>>>(nc, p->Dk, p->run_len, p->kval, p->c_cls,
+                                                   p->cls_m, p->cls_n, keys);
+    BST_CHECK_LAUNCH();
+  }
 }
 
-void sort_items(int64_t *items, const int32_t *keys, int64_t n, int64_t *out, Arena &scratch,
+// items reordered by their keys (stable): costly C blocks first
+void sort_items(const int64_t *items, const int32_t *keys, int64_t n, int64_t *out, Arena &scratch,
                 cudaStream_t s) {
   if (n == 0) return;
   int32_t *perm = scratch.alloc_n<int32_t>((size_t)n);
