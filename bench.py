@@ -174,6 +174,43 @@ def run_reference(args):
     return 0
 
 
+def keep_plan_index(A, B, p, device):
+    """C block index of the workload's product (rows, cols, offsets) from one plan."""
+    from paper_1910_13555_gb300 import bst
+    plan = bst.multiply_plan(A, B, None, p.eps, device=device)
+    r, c, o = bst.bst_matrix_get_index(bst.bst_plan_result(plan.handle))
+    return r, c, o
+
+
+class SampledError:
+    """Relative Frobenius error of a result on 64 seeded C blocks against the CPU oracle
+    (the oracle computes exactly those blocks from the definition)."""
+
+    def __init__(self, p, index, nsample=64, seed=0):
+        import numpy as np
+
+        import oracle
+        rows, cols, offs = index
+        rng = np.random.default_rng(seed)
+        self.sel = np.sort(rng.choice(len(rows), min(nsample, len(rows)), replace=False))
+        self.bi, self.bj, self.offs = rows[self.sel], cols[self.sel], offs[self.sel]
+        self.m = p.A.row_sizes[self.bi].astype(np.int64)
+        self.n = p.B.col_sizes[self.bj].astype(np.int64)
+        self.ref, _ = oracle.multiply_sample(p.A, p.B, None, 1.0, 0.0, p.eps, self.bi, self.bj,
+                                             row_sizes=p.A.row_sizes, col_sizes=p.B.col_sizes)
+
+    def error(self, plan):
+        import numpy as np
+        import torch
+        d = plan.result.data
+        idx = np.concatenate([np.arange(o, o + m * n) for o, m, n in zip(self.offs, self.m, self.n)])
+        got = d[torch.as_tensor(idx, device=d.device)].cpu().numpy()
+        return float(np.linalg.norm(got - self.ref) / np.linalg.norm(self.ref))
+
+    def describe(self):
+        return f"{len(self.sel)} seeded C blocks ({int((self.m * self.n).sum())} elements)"
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -272,12 +309,23 @@ def run_ours(args):
         line["e2e"] = e2e_leg(p, local_rank, min(args.steps, 3), stream, barrier, world, dev)
 
     if not args.no_extras:
+        from paper_1910_13555_gb300 import tune
         extras = {}
+        sample = SampledError(p, keep_plan_index(A, B, p, local_rank)) if rank == 0 else None
+        if sample is not None:
+            fp = step(bst.BST_FP64)
+            torch.cuda.synchronize()
+            line["numeric_only"]["rel_err_vs_oracle_sample"] = sample.error(fp)
+            del fp
         for name, prec in (("emu_bf16", bst.BST_FP64_EMU_BF16), ("tf32x3", bst.BST_TF32X3)):
             try:
                 ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                 pl = step(prec)
                 torch.cuda.synchronize()
+                if prec == bst.BST_FP64_EMU_BF16:
+                    # the project's autotuner picks the tile mapping per (m, n) class
+                    table = tune.tune_emulated(pl, device=local_rank, reps=2)
+                    extras["emu_tuned_swap"] = {f"{m}x{n}": v["swap"] for (m, n), v in table.items()}
                 times = []
                 for _ in range(3):
                     pl2 = step(prec, ev)
@@ -285,9 +333,13 @@ def run_ours(args):
                     times.append(ev[0].elapsed_time(ev[1]))
                 extras[name] = {"numeric_gflops": flops / (min(times) * 1e-3) / 1e9,
                                 "speedup_vs_fp64_numeric": num_avg / min(times)}
+                if sample is not None:
+                    extras[name]["rel_err_vs_oracle_sample"] = sample.error(pl2)
                 del pl, pl2
             except bst.BstError as e:
                 extras[name] = {"unavailable": e.name}
+        if sample is not None:
+            extras["error_sample"] = sample.describe()
         line["precision_variants"] = extras
 
     if rank == 0 and world == 1 and not args.no_cpu:

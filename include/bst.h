@@ -208,17 +208,21 @@ bst_status bst_plan_adjoint(bst_plan *plan, const double *dC, double *dA, double
 
 bst_status bst_plan_destroy(bst_plan *plan);
 
-/* Kernel choices of a context, set by the project's autotuner (tune.py) or by hand.
+/* Kernel choices of a context, set by the project's autotuner
+ * (paper_1910_13555_gb300/tune.py) or by hand.
  *   BST_TUNE_EMU_ROW_SCALE (m, n ignored): 1 = emulated-FP64 digits scaled by the
  *     largest exponent of the whole op(A) row / op(B) column, so all products of a C
  *     element share a scale and their exact FP32 level sums run across products
  *     (default); 0 = scaled per block row / column, each product folded on its own
  *     (more robust to blocks of very different magnitudes in one row, slower).
- *   BST_TUNE_FP64_ROWS_PER_WARP (per (m, n) C block class): native-FP64 thread
- *     mapping; 0 = one warp per C block with lanes over its elements (default),
- *     1 = the same with the C block's operands staged in shared memory.
+ *   BST_TUNE_EMU_SWAP (per (m, n) C block class): thread mapping of the emulated-FP64
+ *     kernel; 0 = the 16-row MMA tiles run over the C block's rows, 1 = over its columns
+ *     (C^T = op(B)^T op(A)^T on the same digit planes, fewer tiles when n > m);
+ *     -1 = back to the built-in rule (fewer 16 x 8 tiles wins).  Row-scaled mode only.
+ * Changing a choice takes effect at the next execute of a plan; a batch built before
+ * the change refuses emulated-FP64 execution (BST_ERR_STATE) and must be created again.
  * Errors: INVALID_ARG for an unknown key or value. */
-enum { BST_TUNE_EMU_ROW_SCALE = 0, BST_TUNE_FP64_ROWS_PER_WARP = 1 };
+enum { BST_TUNE_EMU_ROW_SCALE = 0, BST_TUNE_EMU_SWAP = 1 };
 bst_status bst_tune_set(bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t value);
 bst_status bst_tune_get(const bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t *value);
 

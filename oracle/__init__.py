@@ -91,6 +91,9 @@ def _load():
         lib.or_contract_adjoint.argtypes = [vp, vp, C.c_int32, vp, vp, C.c_int32, vp, C.c_int32,
                                             vp, vp, vp, C.c_double, C.c_double, C.c_double, vp,
                                             vp, vp, vp]
+        lib.or_contract_sample.argtypes = [vp, vp, C.c_int32, vp, vp, C.c_int32, vp, C.c_int32,
+                                           vp, vp, vp, C.c_double, C.c_double, C.c_double,
+                                           C.c_int64, vp, vp, vp]
         lib.or_tresult_sizes.argtypes = [vp, vp]
         lib.or_tresult_flops.argtypes = [vp]
         lib.or_tresult_flops.restype = C.c_double
@@ -259,6 +262,29 @@ def contract(T1, T2, c1, c2, f1, f2, result_order=None, R_in=None, alpha=1.0, be
         return out
     finally:
         lib.or_tresult_free(res)
+
+
+def contract_sample(T1, T2, c1, c2, f1, f2, result_order, R_in, alpha, beta, eps, req,
+                    result_block_sizes):
+    """Values of the requested result blocks (req: nreq x rank tuples in result order),
+    same definition as :func:`contract`.  Returns (packed values, present flags)."""
+    lib = _load()
+    t1, t2 = _TenArgs(T1), _TenArgs(T2)
+    ri = _TenArgs(R_in) if R_in is not None else None
+    c1, c2, f1, f2 = _i32(c1), _i32(c2), _i32(f1), _i32(f2)
+    ro = _i32(result_order) if result_order is not None else None
+    req = np.ascontiguousarray(req, np.int32)
+    lens = np.ones(len(req), np.int64)
+    for d, sz in enumerate(result_block_sizes):
+        lens *= np.asarray(sz, np.int64)[req[:, d]]
+    out = np.empty(int(lens.sum()), np.float64)
+    present = np.empty(len(req), np.int8)
+    st = lib.or_contract_sample(t1.ref, t2.ref, len(c1), _p(c1), _p(c2), len(f1), _p(f1),
+                                len(f2), _p(f2), _p(ro), ri.ref if ri else None, alpha, beta,
+                                eps, len(req), _p(req), _p(out), _p(present))
+    if st:
+        raise OracleError(st, "contract_sample")
+    return out, present.astype(bool)
 
 
 def contract_adjoint(T1, T2, c1, c2, f1, f2, result_order, R_in, alpha, beta, eps, dR):

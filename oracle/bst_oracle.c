@@ -1393,3 +1393,92 @@ int or_contract_adjoint(const or_tensor *T1, const or_tensor *T2, int32_t nc, co
   or_tresult_free(res);
   return OR_OK;
 }
+
+/* Values of selected result blocks only (tuples req[nreq * rank] in the result's mode
+ * order), from the same definition as or_contract: alpha * the sum over the kept block
+ * pairs that land on each requested block + beta * R_in.  out is packed in request
+ * order, each block row-major; present[e] = 0 for a block outside the result pattern
+ * (its values come back as zeros). */
+int or_contract_sample(const or_tensor *T1, const or_tensor *T2, int32_t nc, const int32_t *c1,
+                       const int32_t *c2, int32_t nf1, const int32_t *f1, int32_t nf2,
+                       const int32_t *f2, const int32_t *result_order, const or_tensor *Rin,
+                       double alpha, double beta, double eps, int64_t nreq, const int32_t *req,
+                       double *out, int8_t *present) {
+  if (!(eps >= 0.0)) return OR_ERR_INVALID_ARG;
+  cset_t s;
+  int st = cset_make(T1, T2, nc, c1, c2, nf1, f1, nf2, f2, result_order, Rin, &s);
+  if (st) return st;
+  pair_t *pairs = NULL;
+  int64_t np = 0, nfilt = 0;
+  st = kept_pairs(&s, eps, &pairs, &np, &nfilt);
+  if (st) {
+    cset_free(&s);
+    return st;
+  }
+  int32_t rr = s.rrank;
+  /* block sizes of the result modes, and the requested blocks in canonical form */
+  int32_t rnblk[2 * OR_MAXRANK];
+  tcanon_t rq;
+  memset(&rq, 0, sizeof(rq));
+  rq.rank = rr;
+  int32_t *rsz_all = NULL;
+  {
+    int64_t tot = 0;
+    for (int32_t q = 0; q < rr; ++q) {
+      int32_t slot = s.ro[q];
+      rnblk[q] = slot < s.nf1 ? s.t1.nblk[s.f1[slot]] : s.t2.nblk[s.f2[slot - s.nf1]];
+      tot += rnblk[q];
+    }
+    rsz_all = (int32_t *)malloc(sizeof(int32_t) * (size_t)(tot ? tot : 1));
+    if (!rsz_all) {
+      free(pairs);
+      cset_free(&s);
+      return OR_ERR_ALLOC;
+    }
+    int64_t so = 0;
+    for (int32_t q = 0; q < rr; ++q) {
+      for (int32_t b = 0; b < rnblk[q]; ++b) rsz_all[so + b] = free_slot_mode_size(&s, s.ro[q], b);
+      rq.sz[q] = rsz_all + so;
+      rq.nblk[q] = rnblk[q];
+      so += rnblk[q];
+    }
+  }
+  int64_t *roff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nreq ? nreq : 1));
+  if (!roff) st = OR_ERR_ALLOC;
+  int64_t total = 0;
+  for (int64_t e = 0; !st && e < nreq; ++e) {
+    for (int32_t q = 0; q < rr; ++q)
+      if (req[e * rr + q] < 0 || req[e * rr + q] >= rnblk[q]) st = OR_ERR_OUT_OF_RANGE;
+    if (st) break;
+    roff[e] = total;
+    total += tblock_len(&rq, req + e * rr);
+    present[e] = 0;
+  }
+  if (!st) {
+    for (int64_t x = 0; x < total; ++x) out[x] = 0.0;
+    for (int64_t p = 0; p < np; ++p) {
+      int32_t tp[2 * OR_MAXRANK];
+      result_tuple(&s, pairs[p].b1, pairs[p].b2, tp);
+      for (int64_t e = 0; e < nreq; ++e) {
+        if (memcmp(tp, req + e * rr, sizeof(int32_t) * (size_t)rr) != 0) continue;
+        pair_kernel(&s, pairs[p].b1, pairs[p].b2, 0, NULL, out + roff[e], 1.0);
+        present[e] = 1;
+      }
+    }
+    for (int64_t e = 0; e < nreq; ++e) {
+      int64_t ib = s.has_rin ? tfind(&s.ri, req + e * rr) : -1;
+      if (ib >= 0) present[e] = 1;
+      int64_t len = tblock_len(&rq, req + e * rr);
+      for (int64_t x = 0; x < len; ++x) {
+        double v = alpha * out[roff[e] + x];
+        if (ib >= 0 && beta != 0.0) v += beta * s.ri.data[s.ri.off[ib] + x];
+        out[roff[e] + x] = v;
+      }
+    }
+  }
+  free(roff);
+  free(rsz_all);
+  free(pairs);
+  cset_free(&s);
+  return st;
+}

@@ -253,7 +253,7 @@ def bst_plan_destroy(plan):
 
 
 BST_TUNE_EMU_ROW_SCALE = 0
-BST_TUNE_FP64_ROWS_PER_WARP = 1
+BST_TUNE_EMU_SWAP = 1
 
 
 def bst_tune_set(ctx, key, value, m=0, n=0):

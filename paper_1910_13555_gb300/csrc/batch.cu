@@ -34,6 +34,7 @@ struct bst_batch {
   void *d_eparams = nullptr, *h_eparams = nullptr;
   size_t epbytes = 0;
   int grid_e = 0;
+  int64_t tune_version = 0;  // the context's tuning state the schedules were built for
   ~bst_batch() {
     if (h_params) cudaFreeHost(h_params);
     if (h_eparams) cudaFreeHost(h_eparams);
@@ -132,6 +133,7 @@ bst_status bst_batch_create(bst_ctx *ctx, int32_t n, bst_plan *const *plans, bst
       b->d_eparams = b->ar.alloc(b->epbytes * n);
       BST_CUDA(cudaMallocHost(&b->h_eparams, b->epbytes * n));
       b->grid_e = bst::emu_persist_grid(ctx->num_sms);
+      b->tune_version = ctx->tune_version;
       BST_CUDA(cudaStreamSynchronize(s));
       scratch.release_all();
       BST_CUDA(cudaStreamSynchronize(s));
@@ -161,6 +163,8 @@ bst_status bst_batch_execute(bst_batch *b, const double *alpha, const double *be
     if (cur != b->ctx->device) BST_CUDA(cudaSetDevice(b->ctx->device));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int32_t n = (int32_t)b->plans.size();
+    BST_REQUIRE(precision == BST_FP64 || b->tune_version == b->ctx->tune_version, BST_ERR_STATE,
+                "the context's tuning changed after the batch was created; create it again");
     if (precision == BST_FP64) {
       for (int32_t q = 0; q < n; ++q) {
         Args r = plan_args(b->plans[q], alpha[q], beta[q], s);

@@ -426,31 +426,40 @@ bst_status bst_plan_adjoint(bst_plan *plan, const double *dC, double *dA, double
 bst_status bst_tune_set(bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t value) {
   API_BEGIN
   BST_REQUIRE(ctx, BST_ERR_INVALID_ARG, "ctx is NULL");
-  (void)m;
-  (void)n;
   switch (key) {
     case BST_TUNE_EMU_ROW_SCALE:
       BST_REQUIRE(value == 0 || value == 1, BST_ERR_INVALID_ARG, "value must be 0 or 1");
       ctx->tune_emu_row_scale = value;
       break;
-    case BST_TUNE_FP64_ROWS_PER_WARP:
-      BST_REQUIRE(value == 0, BST_ERR_INVALID_ARG, "only variant 0 is built");
+    case BST_TUNE_EMU_SWAP:
+      BST_REQUIRE(value >= -1 && value <= 1, BST_ERR_INVALID_ARG, "value must be -1, 0 or 1");
+      BST_REQUIRE(m >= 1 && n >= 1, BST_ERR_INVALID_ARG, "m and n must be >= 1");
+      if (value < 0)
+        ctx->tune_emu_swap.erase({m, n});
+      else
+        ctx->tune_emu_swap[{m, n}] = value;
       break;
     default:
       throw Error{BST_ERR_INVALID_ARG, "unknown tuning key"};
   }
+  ++ctx->tune_version;
   API_END
 }
 
 bst_status bst_tune_get(const bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t *value) {
   API_BEGIN
   BST_REQUIRE(ctx && value, BST_ERR_INVALID_ARG, "NULL argument");
-  (void)m;
-  (void)n;
   switch (key) {
-    case BST_TUNE_EMU_ROW_SCALE: *value = ctx->tune_emu_row_scale; break;
-    case BST_TUNE_FP64_ROWS_PER_WARP: *value = 0; break;
-    default: throw Error{BST_ERR_INVALID_ARG, "unknown tuning key"};
+    case BST_TUNE_EMU_ROW_SCALE:
+      *value = ctx->tune_emu_row_scale;
+      break;
+    case BST_TUNE_EMU_SWAP: {
+      auto it = ctx->tune_emu_swap.find({m, n});
+      *value = it == ctx->tune_emu_swap.end() ? -1 : it->second;
+      break;
+    }
+    default:
+      throw Error{BST_ERR_INVALID_ARG, "unknown tuning key"};
   }
   API_END
 }

@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/bst.h"
@@ -76,8 +78,12 @@ struct bst_ctx {
   int num_sms = 0;
   size_t max_smem_optin = 0;
   // kernel choices (bst_tune_set): emulated-FP64 digit scaling per whole op row /
-  // column (1) or per block row / column (0)
+  // column (1) or per block row / column (0); per (m, n) C block class, the tile
+  // orientation of the emulated kernel (1 = MMA rows run over the C block's columns);
+  // tune_version changes whenever a choice does
   int tune_emu_row_scale = 1;
+  std::map<std::pair<int32_t, int32_t>, int32_t> tune_emu_swap;
+  int64_t tune_version = 0;
 };
 
 namespace bst {

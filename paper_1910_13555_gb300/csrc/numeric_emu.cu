@@ -3,36 +3,37 @@
 //
 // Emulated FP64 (BST_FP64_EMU_BF16).  The error-free splitting of Ozaki, Ogita, Oishi
 // and Rump (Numer. Algorithms 59, 2012) cuts every operand into slices whose pairwise
-// products a low-precision unit computes exactly.  Here, for each block row p of every
-// op(A) block (block column q of every op(B) block), the largest exponent E of the row
-// fixes the scale; the row is written as fixed point with 42 fraction bits,
-//     a = 2^E * sum_{s=0..5} d_s 2^{-7(s+1)},   d_s integers, |d_0| <= 128, |d_s| <= 127,
-// so every digit is exact in BF16.  A digit product d_s e_t is exact in FP32, and any
-// sum of at most 6 * 160 of them stays below 2^24, so the tensor core's FP32
-// accumulation is exact for up to 160 inner elements.  Products are grouped by level
-// w = s + t; levels w <= 5 are kept (21 of the 36 slice products; the dropped ones
-// weigh at most about 2^-42 of the scale).  After each block product (or 160-element
-// segment of it) the level sums become one exact integer
-//     I = sum_w D_w 2^{7 (5 - w)}          (|I| < 2^60)
-// in units of 2^{ea + eb - 49} (ea, eb: the row / column scales of this block pair),
-// which is shifted (with rounding) to the C element's common scale 2^{ref - 49 + G}
-// (ref: the largest exponent of the whole op(A) row plus that of the whole op(B)
-// column, so ref >= ea + eb for every product; G guard bits against int64 overflow)
-// and added into an int64 accumulator.  The result is exact up to the digit truncation and one rounding per
-// shift; it is turned into FP64 by an integer-only, round-to-nearest-even conversion
-// (IEEE 754 binary64 encoding), so C is formed in FP64 without FP64 multiply-adds --
-// on GB300 the FP64 pipe runs at 1/64 of the FP32 rate.
+// products a low-precision unit computes exactly.  Each op(A) row (op(B) column) is
+// scaled by a power of two 2^E with E its largest exponent -- over the whole op(A) row
+// of the matrix (row-scaled mode, the default) or over the row of one block
+// (block-scaled mode) -- and written in fixed point with 48 fraction bits,
+//     a = 2^E * sum_{s=0..5} d_s 2^{-8(s+1)},  d_s integers, |d_0| <= 256, |d_s| <= 255,
+// so every digit is exact in BF16 (8 significant bits).  A digit product is at most
+// 2^16 and exact in FP32; a sum of 6 * 32 of them stays below 2^24, so the tensor core's
+// FP32 accumulation is exact over 32 inner elements.  Slice products are grouped by
+// level w = s + t and levels w <= 5 are kept (21 of 36; the dropped ones weigh about
+// 2^-48 of the scale).  Every 32 inner elements the six exact level sums are folded into
+// one integer I = sum_w D_w 2^{8(5-w)} (|I| < 2^62) and added into an int64 accumulator
+// at the element's common scale 2^{ref - 56 + G}: in row-scaled mode all products of a C
+// element share ref = E_row + F_col, in block-scaled mode each product's I is first
+// shifted (with rounding) from its own scale ea + eb to the element's ref = the largest
+// E_row + F_col; G guard bits keep K_tot * 2^56 below 2^62.  The int64 sum becomes FP64
+// through an integer-only, round-to-nearest-even conversion written from the IEEE 754
+// binary64 encoding, so no FP64 multiply-add is issued -- GB300's FP64 pipe runs at
+// 1/64 of the FP32 rate.
 //
 // 3xTF32 (BST_TF32X3), after Ootomo and Yokota (IJHPCA 2022): x = hi + lo with hi, lo
-// TF32; C += hi*hi + hi*lo + lo*hi on the TF32 tensor cores, FP32 accumulation over
-// the whole C block, then converted to FP64 and combined with alpha, beta.
+// TF32; per block product hi*hi + hi*lo + lo*hi on the TF32 tensor cores with FP32
+// accumulation, and the products summed as an unevaluated FP32 pair (TwoSum), then
+// converted to FP64 and combined with alpha, beta.
 //
 // Both use warp-level mma.sync tiles (m16n8k16 BF16, m16n8k8 TF32): one warp owns a
 // 16 x 8 (BF16) or 16 x 16 (TF32) tile of one C block (no two warps write the same
-// element),
-// and the operand slices are staged once per execute in a padded, permuted layout that
-// makes every fragment a single 8-byte load (inner dimension padded with zeros to the
-// MMA K and permuted inside each chunk so a thread's four values are adjacent).
+// element); for the BF16 kernel the tile rows may run over the C block's columns instead
+// (C^T = op(B)^T op(A)^T on the same slices), chosen per (m, n) class by the autotuner.
+// The operand slices are staged once per execute in a padded, permuted layout that makes
+// every fragment a single 8-byte load (inner dimension padded with zeros to the MMA K
+// and permuted inside each chunk so a thread's four values are adjacent).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -44,8 +45,8 @@
 namespace bst {
 
 constexpr int kSlices = 6;     // BF16 digits per operand
-constexpr int kBeta = 7;       // bits per digit
-constexpr int kSegChunks = 10; // 16-wide K chunks per exact FP32 segment (160 elements)
+constexpr int kBeta = 8;       // bits per digit
+constexpr int kSegChunks = 2;  // 16-wide K chunks per exact FP32 segment (32 elements)
 constexpr int kExpNone = -4000;
 
 struct EmuState {
@@ -72,7 +73,11 @@ struct EmuState {
   bool dig_alloc = false, tf_alloc = false;
   // per stack entry: offsets of its A and B digit blocks
   int64_t *e_adoff = nullptr, *e_bdoff = nullptr;
-  // persistent schedule of the BF16 warp tiles
+  // persistent schedule of the BF16 warp tiles, built for one tuning state
+  int32_t *cls_swap = nullptr;
+  int64_t sched_version = -1;
+  int sched_rows = -1;
+  int64_t items_cap = 0;
   int64_t *items = nullptr;
   unsigned long long *counter = nullptr;
 };
@@ -185,7 +190,9 @@ __global__ void k_emu_digits(SideArgs S) {
     const int64_t pos = (int64_t)outer * kp + perm16(inner);
 #pragma unroll
     for (int s = 0; s < kSlices; ++s) {
-      int dg = (int)((N >> (kBeta * (kSlices - 1 - s))) & (s == 0 ? 0xffu : 0x7fu));
+      // the leading digit may reach 2^kBeta after rounding; the others stay below it
+      const unsigned mask = s == 0 ? (2u << kBeta) - 1u : (1u << kBeta) - 1u;
+      int dg = (int)((N >> (kBeta * (kSlices - 1 - s))) & mask);
       if (neg) dg = -dg;
       d[s * plane + pos] = __float2bfloat16_rn((float)dg);
     }
@@ -330,6 +337,9 @@ struct EmuParams {
   int32_t Dk, ncls, guard;
   const int64_t *wstart;
   int32_t tiles_n;  // N-tiles of 8 columns per warp (1 or 2)
+  const int32_t *cls_swap;  // per (m,n) class: tile orientation of the BF16 kernel
+  int32_t alpha_one, has_beta;  // alpha == 1, beta != 0 (set on the host: FP64 compares
+                                // would occupy GB300's slow FP64 pipe in every tile)
   int32_t row_scale;  // 1: digits scaled per whole op row / column (shared by all products)
   const int64_t *a_rowstart, *b_colstart;
   const int32_t *row_exp, *col_exp;
@@ -346,6 +356,7 @@ struct EmuParams {
 
 struct WarpTask {
   int c, m, n, mt, ng, ntn;
+  int sw = 0;  // 1: tile rows run over the C block's columns (C^T = op(B)^T op(A)^T)
 };
 
 __device__ __forceinline__ WarpTask find_task(const EmuParams &P, int64_t gw) {
@@ -408,22 +419,34 @@ __device__ __forceinline__ void slot_rc(const WarpTask &w, int nt, int h, int &r
 // folded into the int64 accumulators at the element's common scale.
 // Row-scaled form: every product of a C element shares the element's scale
 // 2^{E_row + F_col}, so the FP32 level sums run across products and are folded into the
-// int64 accumulators only when 160 inner elements have been summed (or at the end).
+// int64 accumulators only when 32 inner elements have been summed (or at the end).
+// Folding and output touch only the lane's valid elements; offsets are 32-bit element
+// counts (a plan's digit arrays hold fewer than 2^31 elements).
 __device__ __forceinline__ void emu_tile_rows(const EmuParams &P, const WarpTask &w) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  // tile space: RM rows x RN columns; with w.sw the rows are the C block's columns and the
+  // row operand is op(B)^T (its digit planes are stored column by column already)
+  const int sw = w.sw;
+  const int RM = sw ? w.n : w.m, RN = sw ? w.m : w.n;
+  const __nv_bfloat16 *Xa = sw ? P.b_dig : P.a_dig, *Xb = sw ? P.a_dig : P.b_dig;
+  const int64_t *eXa = sw ? P.e_bdoff : P.e_adoff, *eXb = sw ? P.e_adoff : P.e_bdoff;
   const int r0 = w.mt * 16 + g, r1 = r0 + 8;
-  const bool v0 = r0 < w.m, v1 = r1 < w.m;
+  const bool v0 = r0 < RM, v1 = r1 < RM;
   const int colB = w.ng * 8 + g;
-  const bool vB = colB < w.n;
+  const bool vB = colB < RN;
   const int cc0 = w.ng * 8 + 2 * t, cc1 = cc0 + 1;
-  const bool vc0 = cc0 < w.n, vc1 = cc1 < w.n;
+  const bool vc0 = cc0 < RN, vc1 = cc1 < RN;
+  const bool valid[4] = {v0 && vc0, v0 && vc1, v1 && vc0, v1 && vc1};
   const int i = P.c_row[w.c], j = P.c_col[w.c];
+  // largest exponent of a whole op(A) row (index x of block row i) / op(B) column
+  auto erow = [&](int x) { return P.row_exp[P.a_rowstart[i] + x]; };
+  auto ecol = [&](int x) { return P.col_exp[P.b_colstart[j] + x]; };
   int ref[4];
   {
-    const int E0 = v0 ? P.row_exp[P.a_rowstart[i] + r0] : kExpNone;
-    const int E1 = v1 ? P.row_exp[P.a_rowstart[i] + r1] : kExpNone;
-    const int F0 = vc0 ? P.col_exp[P.b_colstart[j] + cc0] : kExpNone;
-    const int F1 = vc1 ? P.col_exp[P.b_colstart[j] + cc1] : kExpNone;
+    const int E0 = v0 ? (sw ? ecol(r0) : erow(r0)) : kExpNone;
+    const int E1 = v1 ? (sw ? ecol(r1) : erow(r1)) : kExpNone;
+    const int F0 = vc0 ? (sw ? erow(cc0) : ecol(cc0)) : kExpNone;
+    const int F1 = vc1 ? (sw ? erow(cc1) : ecol(cc1)) : kExpNone;
     ref[0] = E0 + F0;
     ref[1] = E0 + F1;
     ref[2] = E1 + F0;
@@ -439,48 +462,49 @@ __device__ __forceinline__ void emu_tile_rows(const EmuParams &P, const WarpTask
   auto fold = [&]() {
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-      long long I = 0;
+      if (valid[h]) {
+        long long I = __float2int_rn(accw[0][h]);
 #pragma unroll
-      for (int s = 0; s < kSlices; ++s) {
-        I += (long long)f32_exact_int(accw[s][h]) << (kBeta * (kSlices - 1 - s));
-        accw[s][h] = 0.f;
+        for (int s = 1; s < kSlices; ++s) I = (I << kBeta) + __float2int_rn(accw[s][h]);
+        acc[h] += round_shift(I, P.guard);
       }
-      acc[h] += round_shift(I, P.guard);
+#pragma unroll
+      for (int s = 0; s < kSlices; ++s) accw[s][h] = 0.f;
     }
     used = 0;
   };
+  const uint2 zero = make_uint2(0u, 0u);
   for (int kc = 0; kc < P.Dk; ++kc) {
     const int64_t rr = (int64_t)w.c * P.Dk + kc;
     const int len = P.run_len[rr];
     if (len == 0) continue;
     const int e0 = P.run_start[rr];
     const int k = P.kval[kc], kp = (k + 15) & ~15, nch = kp >> 4;
-    const int64_t pa = (int64_t)w.m * kp, pb = (int64_t)w.n * kp;
-    int64_t ao = P.e_adoff[e0], bo = P.e_bdoff[e0];
+    // per-thread element offsets inside one digit plane of the row and column operands
+    const int pa = RM * kp, pb = RN * kp;
+    const int oa0 = r0 * kp + 4 * t, oa1 = r1 * kp + 4 * t, ob = colB * kp + 4 * t;
+    int64_t ao = eXa[e0], bo = eXb[e0];
     for (int e = e0; e < e0 + len; ++e) {
-      const __nv_bfloat16 *Ad = P.a_dig + ao;
-      const __nv_bfloat16 *Bd = P.b_dig + bo;
+      const __nv_bfloat16 *Ad = Xa + ao;
+      const __nv_bfloat16 *Bd = Xb + bo;
       if (e + 1 < e0 + len) {  // next entry's offsets, loaded ahead of this entry's MMAs
-        ao = P.e_adoff[e + 1];
-        bo = P.e_bdoff[e + 1];
+        ao = eXa[e + 1];
+        bo = eXb[e + 1];
       }
       for (int ch = 0; ch < nch; ++ch) {
         if (used == kSegChunks) fold();
-        uint32_t af[kSlices][4];
+        const int cofs = ch * 16;
+        // the six B digit fragments (one 8-byte load each), then A digit by digit
+        uint2 bf[kSlices];
+#pragma unroll
+        for (int tt = 0; tt < kSlices; ++tt) bf[tt] = vB ? ld8(Bd + (tt * pb + ob + cofs)) : zero;
 #pragma unroll
         for (int s = 0; s < kSlices; ++s) {
-          const uint2 x0 = v0 ? ld8(Ad + s * pa + (int64_t)r0 * kp + ch * 16 + 4 * t) : make_uint2(0, 0);
-          const uint2 x1 = v1 ? ld8(Ad + s * pa + (int64_t)r1 * kp + ch * 16 + 4 * t) : make_uint2(0, 0);
-          af[s][0] = x0.x;
-          af[s][2] = x0.y;
-          af[s][1] = x1.x;
-          af[s][3] = x1.y;
-        }
+          const uint2 x0 = v0 ? ld8(Ad + (s * pa + oa0 + cofs)) : zero;
+          const uint2 x1 = v1 ? ld8(Ad + (s * pa + oa1 + cofs)) : zero;
+          const uint32_t af[4] = {x0.x, x1.x, x0.y, x1.y};
 #pragma unroll
-        for (int tt = 0; tt < kSlices; ++tt) {
-          const uint2 bf = vB ? ld8(Bd + tt * pb + (int64_t)colB * kp + ch * 16 + 4 * t) : make_uint2(0, 0);
-#pragma unroll
-          for (int s = 0; s + tt < kSlices; ++s) mma_bf16(accw[s + tt], af[s], bf.x, bf.y);
+          for (int tt = 0; s + tt < kSlices; ++tt) mma_bf16(accw[s + tt], af, bf[tt].x, bf[tt].y);
         }
         ++used;
       }
@@ -489,17 +513,25 @@ __device__ __forceinline__ void emu_tile_rows(const EmuParams &P, const WarpTask
   fold();
   const int64_t off = P.c_off[w.c];
   const int cin = P.c_cin[w.c];
-  const double *ci = (P.beta != 0.0 && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
-  const bool scale = P.alpha != 1.0;  // one FP64 compare per thread, not per element
+  const double *ci = (P.has_beta && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
+  const int sh = (kSlices + 1) * kBeta - P.guard;
+  // element (x, y) of the tile is C(x, y), or C(y, x) when swapped
+  auto cidx = [&](int h) {
+    const int x = h < 2 ? r0 : r1, y = (h & 1) ? cc1 : cc0;
+    return sw ? y * w.n + x : x * w.n + y;
+  };
+  if (P.alpha_one && !ci) {  // plain stores: no FP64 instruction at all
 #pragma unroll
-  for (int h = 0; h < 4; ++h) {
-    const int r = h < 2 ? r0 : r1, c = (h & 1) ? cc1 : cc0;
-    if (r < w.m && c < w.n) {
-      double v = i64_ldexp(acc[h], ref[h] - (kSlices + 1) * kBeta + P.guard);
-      if (scale) v *= P.alpha;
-      if (ci) v = fma(P.beta, ci[r * w.n + c], v);
-      P.C[off + r * w.n + c] = v;
-    }
+    for (int h = 0; h < 4; ++h)
+      if (valid[h]) P.C[off + cidx(h)] = i64_ldexp(acc[h], ref[h] - sh);
+  } else {
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+      if (valid[h]) {
+        double v = P.alpha * i64_ldexp(acc[h], ref[h] - sh);
+        if (ci) v = fma(P.beta, ci[cidx(h)], v);
+        P.C[off + cidx(h)] = v;
+      }
   }
 }
 
@@ -580,8 +612,8 @@ __device__ __forceinline__ void emu_tile_blocks(const EmuParams &P, const WarpTa
   }
   const int64_t off = P.c_off[w.c];
   const int cin = P.c_cin[w.c];
-  const double *ci = (P.beta != 0.0 && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
-  const bool scale = P.alpha != 1.0;  // one FP64 compare per thread, not per element
+  const double *ci = (P.has_beta && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
+  const bool scale = !P.alpha_one;
 #pragma unroll
   for (int h = 0; h < 4; ++h) {
     const int r = h < 2 ? r0 : r1, c = (h & 1) ? cc1 : cc0;
@@ -606,7 +638,8 @@ __device__ __forceinline__ WarpTask task_of_item(const EmuParams &P, int64_t v) 
   const int cls = P.c_cls[w.c];
   w.m = P.cls_m[cls];
   w.n = P.cls_n[cls];
-  w.ntn = min(P.tiles_n, ((w.n + 7) >> 3) - P.tiles_n * w.ng);
+  w.sw = P.cls_swap ? P.cls_swap[cls] : 0;
+  w.ntn = min(P.tiles_n, (((w.sw ? w.m : w.n) + 7) >> 3) - P.tiles_n * w.ng);
   return w;
 }
 
@@ -649,24 +682,34 @@ __global__ void __launch_bounds__(256, 2)
                          [&](int64_t pl) -> const EmuParams & { return plans[pl]; });
 }
 
-// warp tiles of every C block (16 x 8 per tile)
+// warp tiles of every C block (16 x 8 per tile; rows and columns exchanged for a
+// swapped class)
+__device__ __forceinline__ void tile_grid(int m, int n, int sw, int &MT, int &NT) {
+  MT = ((sw ? n : m) + 15) >> 4;
+  NT = ((sw ? m : n) + 7) >> 3;
+}
+
 __global__ void k_emu_tile_counts(int64_t nc, const int32_t *__restrict__ c_cls,
                                   const int32_t *__restrict__ cls_m, const int32_t *__restrict__ cls_n,
-                                  int32_t *__restrict__ cnt) {
+                                  const int32_t *__restrict__ cls_swap, int32_t *__restrict__ cnt) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const int cls = c_cls[c];
-  cnt[c] = ((cls_m[cls] + 15) >> 4) * ((cls_n[cls] + 7) >> 3);
+  int MT, NT;
+  tile_grid(cls_m[cls], cls_n[cls], cls_swap[cls], MT, NT);
+  cnt[c] = MT * NT;
 }
 
 __global__ void k_emu_tile_fill(int64_t nc, const int32_t *__restrict__ c_cls,
                                 const int32_t *__restrict__ cls_m, const int32_t *__restrict__ cls_n,
+                                const int32_t *__restrict__ cls_swap,
                                 const int64_t *__restrict__ start, int64_t base,
                                 int64_t *__restrict__ items) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const int cls = c_cls[c];
-  const int MT = (cls_m[cls] + 15) >> 4, NT = (cls_n[cls] + 7) >> 3;
+  int MT, NT;
+  tile_grid(cls_m[cls], cls_n[cls], cls_swap[cls], MT, NT);
   int64_t q = start[c];
   for (int mt = 0; mt < MT; ++mt)
     for (int ng = 0; ng < NT; ++ng) items[q++] = base | (c << 16) | ((int64_t)mt << 8) | ng;
@@ -732,8 +775,8 @@ __global__ void __launch_bounds__(256) k_num_tf32x3(EmuParams P, int64_t nwarps)
   }
   const int64_t off = P.c_off[w.c];
   const int cin = P.c_cin[w.c];
-  const double *ci = (P.beta != 0.0 && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
-  const bool scale = P.alpha != 1.0;
+  const double *ci = (P.has_beta && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
+  const bool scale = !P.alpha_one;
 #pragma unroll
   for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
@@ -847,7 +890,8 @@ void emu_index(bst_plan *p, EmuState &E, cudaStream_t s) {
   BST_CUDA(cudaStreamSynchronize(s));
   int lg = 0;
   while ((1ull << lg) <= hk) ++lg;
-  E.guard = std::max(0, lg - 12);
+  // per inner element |a'b'| <= 1, i.e. 2^((S+1) beta) units; keep K_tot * that < 2^62
+  E.guard = std::max(0, lg - (62 - (kSlices + 1) * kBeta));
   scratch.release_all();
   E.index_ready = true;
 }
@@ -867,6 +911,8 @@ EmuParams emu_params(bst_plan *p, const EmuState &E, const NumArgs &a) {
   P.Cin = a.Cin;
   P.C = a.C;
   P.alpha = a.alpha;
+  P.alpha_one = a.alpha == 1.0;
+  P.has_beta = a.beta != 0.0;
   P.beta = a.beta;
   P.Dk = p->Dk;
   P.ncls = E.ncls;
@@ -960,15 +1006,58 @@ static EmuParams bf16_params(bst_plan *p, const EmuState &E, const NumArgs &a) {
   P.wstart = E.wstart_b;
   P.tiles_n = 1;
   P.row_scale = p->ctx->tune_emu_row_scale;
+  P.cls_swap = E.cls_swap;
   return P;
 }
 
 size_t emu_params_bytes() { return sizeof(EmuParams); }
 
+void emu_build_items(bst_plan *p, int64_t base, int64_t *items, cudaStream_t s);
+
+// Tile orientation of class (m, n): the tuned choice when there is one, else the one
+// with fewer 16 x 8 tiles (ties keep rows over rows).  Block-scaled mode never swaps.
+static int class_swap(const bst_ctx *ctx, int m, int n) {
+  if (!ctx->tune_emu_row_scale) return 0;
+  auto it = ctx->tune_emu_swap.find({m, n});
+  if (it != ctx->tune_emu_swap.end()) return it->second;
+  const int plain = ((m + 15) / 16) * ((n + 7) / 8), swapped = ((n + 15) / 16) * ((m + 7) / 8);
+  return swapped < plain ? 1 : 0;
+}
+
+// (Re)build the BF16 work list when the tuning state changed since the last build.
+static void emu_schedule(bst_plan *p, EmuState &E, cudaStream_t s) {
+  const bst_ctx *ctx = p->ctx;
+  if (E.items && E.sched_version == ctx->tune_version && E.sched_rows == ctx->tune_emu_row_scale)
+    return;
+  const int32_t ncls = p->Dm * p->Dn;
+  std::vector<int32_t> sw((size_t)ncls, 0);
+  int64_t total = 0;
+  for (int32_t c = 0; c < ncls; ++c) {
+    const int m = p->m_vals.empty() ? 0 : p->m_vals[c / p->Dn];
+    const int n = p->n_vals.empty() ? 0 : p->n_vals[c % p->Dn];
+    const int64_t cnt = (int64_t)p->h_class_ptr[c + 1] - p->h_class_ptr[c];
+    if (cnt > 0 && m > 0 && n > 0) sw[(size_t)c] = class_swap(ctx, m, n);
+    const int rm = sw[(size_t)c] ? n : m, rn = sw[(size_t)c] ? m : n;
+    total += cnt * (int64_t)((rm + 15) / 16) * ((rn + 7) / 8);
+  }
+  if (!E.cls_swap) E.cls_swap = E.ar.alloc_n<int32_t>((size_t)ncls);
+  BST_CUDA(cudaMemcpyAsync(E.cls_swap, sw.data(), 4 * (size_t)ncls, cudaMemcpyHostToDevice, s));
+  if (total > E.items_cap) {
+    E.items = E.ar.alloc_n<int64_t>((size_t)total);
+    E.items_cap = total;
+  }
+  if (!E.counter) E.counter = E.ar.alloc_n<unsigned long long>(1);
+  E.nwarps_b = total;
+  E.sched_version = ctx->tune_version;
+  E.sched_rows = ctx->tune_emu_row_scale;
+  emu_build_items(p, 0, E.items, s);  // synchronises: the host vector ends here
+}
+
 int64_t emu_item_count(bst_plan *p, cudaStream_t s) {
   if (p->C->nblocks == 0) return 0;
   EmuState &E = emu_state(p, s);
   emu_alloc_digits(E);
+  emu_schedule(p, E, s);
   return E.nwarps_b;
 }
 
@@ -976,15 +1065,17 @@ int64_t emu_item_count(bst_plan *p, cudaStream_t s) {
 void emu_build_items(bst_plan *p, int64_t base, int64_t *items, cudaStream_t s) {
   const int64_t nc = p->C->nblocks;
   if (nc == 0) return;
+  const int32_t *cls_swap = p->emu->cls_swap;
   Arena scratch;
   scratch.ctx = static_cast<Ctx *>(p->ctx);
   scratch.stream = s;
   int32_t *cnt = scratch.alloc_n<int32_t>((size_t)nc);
   int64_t *start = scratch.alloc_n<int64_t>((size_t)nc + 1);
-  k_emu_tile_counts<<<nblk(nc, 256), 256, 0, s>>>(nc, p->c_cls, p->cls_m, p->cls_n, cnt);
+  k_emu_tile_counts<<<nblk(nc, 256), 256, 0, s>>>(nc, p->c_cls, p->cls_m, p->cls_n, cls_swap, cnt);
   BST_CHECK_LAUNCH();
   exscan_i32_i64(cnt, start, nc, scratch, s);
-  k_emu_tile_fill<<<nblk(nc, 256), 256, 0, s>>>(nc, p->c_cls, p->cls_m, p->cls_n, start, base, items);
+  k_emu_tile_fill<<<nblk(nc, 256), 256, 0, s>>>(nc, p->c_cls, p->cls_m, p->cls_n, cls_swap, start,
+                                                base, items);
   BST_CHECK_LAUNCH();
   BST_CUDA(cudaStreamSynchronize(s));
 }
@@ -1020,12 +1111,7 @@ void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
   if (p->C->nblocks == 0) return;
   EmuState &E = emu_state(p, s);
   emu_alloc_digits(E);
-  if (!E.items) {
-    // warp tiles in C block order (built once per plan)
-    E.items = E.ar.alloc_n<int64_t>((size_t)E.nwarps_b);
-    E.counter = E.ar.alloc_n<unsigned long long>(1);
-    emu_build_items(p, 0, E.items, s);
-  }
+  emu_schedule(p, E, s);  // warp tiles in C block order, rebuilt when tuning changed
   emu_prepare(p, E, a, s);
   const EmuParams P = bf16_params(p, E, a);
   if (E.nwarps_b > 0) {

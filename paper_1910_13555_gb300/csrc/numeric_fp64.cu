@@ -38,6 +38,8 @@ struct NumParams {
   int32_t split, K;
   int32_t Dk;
   int32_t ta, tb;
+  int32_t alpha_one, has_beta;  // alpha == 1, beta != 0 (host-side: FP64 compares would
+                                // occupy the slow FP64 pipe once per C block)
   const int32_t *task_c, *c_cls, *c_cin;
   const int64_t *c_off, *cin_off;
   const int32_t *run_start, *run_len;
@@ -132,8 +134,8 @@ __device__ __forceinline__ void task_mn(const NumParams &P, int c, int s) {
     return;
   }
   const int cin = P.c_cin[c];
-  const double *ci = (P.beta != 0.0 && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
-  if (P.alpha != 1.0 || ci) {
+  const double *ci = (P.has_beta && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
+  if (!P.alpha_one || ci) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int o = lane + 32 * r;
@@ -158,7 +160,7 @@ __device__ void task_generic(const NumParams &P, int c, int s, int m, int n) {
   const int mn = m * n;
   const int64_t off = P.c_off[c];
   const int cin = P.c_cin[c];
-  const double *ci = (P.split == 1 && P.beta != 0.0 && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
+  const double *ci = (P.split == 1 && P.has_beta && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
   for (int o0 = 0; o0 < mn; o0 += 32 * RG) {
     double acc[RG];
     int pr[RG], qr[RG];
@@ -299,7 +301,7 @@ __global__ void k_splitk_reduce(NumParams P, int64_t nc, const int32_t *__restri
   const int64_t off = P.c_off[c];
   const int len = msz[c_row[c]] * nsz[c_col[c]];
   const int cin = P.c_cin[c];
-  const double *ci = (P.beta != 0.0 && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
+  const double *ci = (P.has_beta && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
   for (int o = lane; o < len; o += 32) {
     double v = 0.0;
     for (int s = 0; s < P.split; ++s) v += P.W[(int64_t)s * P.nelemC + off + o];
@@ -317,6 +319,8 @@ NumParams make_params(bst_plan *p, const NumArgs &a, int split) {
   P.C = a.C;
   P.W = nullptr;
   P.alpha = a.alpha;
+  P.alpha_one = a.alpha == 1.0;
+  P.has_beta = a.beta != 0.0;
   P.beta = a.beta;
   P.nelemC = p->C->nelem;
   P.ntasks = p->C->nblocks;
@@ -428,6 +432,8 @@ void execute_fp64(bst_plan *p, const NumArgs &a, int split, cudaStream_t s) {
   P.C = a.C;
   P.W = nullptr;
   P.alpha = a.alpha;
+  P.alpha_one = a.alpha == 1.0;
+  P.has_beta = a.beta != 0.0;
   P.beta = a.beta;
   P.nelemC = p->C->nelem;
   P.ntasks = nc;
@@ -482,6 +488,8 @@ void execute_fp64_workspace(bst_plan *p, const NumArgs &a, int split, double *W,
   P.C = a.C;
   P.W = W;
   P.alpha = a.alpha;
+  P.alpha_one = a.alpha == 1.0;
+  P.has_beta = a.beta != 0.0;
   P.beta = a.beta;
   P.nelemC = p->C->nelem;
   P.ntasks = nc;

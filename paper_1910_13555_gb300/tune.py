@@ -1,0 +1,104 @@
+"""Autotuner of the library's kernel choices (bst_tune_set), written for this library.
+
+What it tunes: the thread mapping of the emulated-FP64 tensor-core kernel per (m, n) C
+block class -- whether the 16-row MMA tiles run over the C block's rows (0) or over its
+columns (1, computing C^T = op(B)^T op(A)^T on the same digit planes).  The two
+mappings use different numbers of 16 x 8 tiles and load the two operands' fragments in
+different proportions, so which one is faster depends on m, n and the inner sizes k of
+the products.  For every class present in a plan the tuner times the plan's execute with
+that class set to each mapping (the others unchanged), keeps the faster one, and returns
+a table that can be saved as JSON (keyed by GPU name) and applied to a context later.
+
+Timing uses CUDA events on the current stream, after a warm-up, minimum over repeats.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import bst
+
+
+def plan_classes(plan) -> list:
+    """Distinct (m, n) C block classes of a plan's stacks (from its (m, n, k) buckets)."""
+    st = bst.bst_plan_get_stacks(plan.handle)
+    return sorted({(int(m), int(n)) for m, n, _ in st["mnk"].tolist()})
+
+
+def time_execute(plan, precision, reps=3, warmup=1) -> float:
+    import torch
+    s = torch.cuda.current_stream()
+    for _ in range(warmup):
+        plan.execute(1.0, 0.0, precision, 1)
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        plan.execute(1.0, 0.0, precision, 1)
+        e1.record(s)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def tune_emulated(plan, device=0, reps=3) -> dict:
+    """Choose the emulated-FP64 tile mapping per (m, n) class of `plan` (which must have
+    its result bound) and leave the choices set in the context.  Returns
+    {(m, n): {"swap": best, "ms": {0: t0, 1: t1}}}."""
+    ctx = bst.context(device)
+    table = {}
+    for (m, n) in plan_classes(plan):
+        times = {}
+        for v in (0, 1):
+            bst.bst_tune_set(ctx, bst.BST_TUNE_EMU_SWAP, v, m, n)
+            times[v] = time_execute(plan, bst.BST_FP64_EMU_BF16, reps)
+        best = min(times, key=times.get)
+        bst.bst_tune_set(ctx, bst.BST_TUNE_EMU_SWAP, best, m, n)
+        table[(m, n)] = {"swap": best, "ms": times}
+    return table
+
+
+def gpu_name(device=0) -> str:
+    import torch
+    return torch.cuda.get_device_name(device)
+
+
+def table_to_json(table: dict, gpu: str) -> dict:
+    return {"gpu": gpu, "precision": "fp64_emu_bf16", "key": "emu_swap",
+            "entries": [{"m": m, "n": n, "swap": v["swap"], "ms": v["ms"]}
+                        for (m, n), v in sorted(table.items())]}
+
+
+def table_from_json(doc: dict) -> dict:
+    return {(int(e["m"]), int(e["n"])): {"swap": int(e["swap"]), "ms": e.get("ms", {})}
+            for e in doc["entries"]}
+
+
+def save_table(table: dict, path: str, gpu: str) -> None:
+    """Write (or update the `gpu` entry of) a JSON tune file."""
+    docs = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            docs = json.load(f)
+    docs[gpu] = table_to_json(table, gpu)
+    with open(path, "w") as f:
+        json.dump(docs, f, indent=1, default=str)
+
+
+def apply_table(table: dict, device=0) -> None:
+    ctx = bst.context(device)
+    for (m, n), v in table.items():
+        bst.bst_tune_set(ctx, bst.BST_TUNE_EMU_SWAP, int(v["swap"]), m, n)
+
+
+def load_table(path: str, gpu: str, device=0) -> dict:
+    """Apply the saved choices for `gpu` to the context; {} when the file has none."""
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        docs = json.load(f)
+    if gpu not in docs:
+        return {}
+    table = table_from_json(docs[gpu])
+    apply_table(table, device)
+    return table

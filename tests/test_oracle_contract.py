@@ -183,3 +183,21 @@ def test_contract_errors():
     with pytest.raises(oracle.OracleError) as e:
         oracle.contract(T1, T2, [2, 2], [0, 1], [0], [2])   # mode listed twice
     assert e.value.name == "INVALID_ARG"
+
+
+def test_contract_sample_matches_full():
+    case = CASES[3]
+    r1, r2, c1, c2, f1, f2, ro = case
+    T1, T2 = _make(42, case)
+    rs = _result_sizes(T1, T2, case)
+    Rin = random_tensor(np.random.default_rng(3), [len(s) for s in rs], rs, 0.4)
+    full = oracle.contract(T1, T2, c1, c2, f1, f2, ro, Rin, 0.5, 2.0, 0.0)
+    sel = np.arange(0, len(full["index"]), 3)
+    vals, present = oracle.contract_sample(T1, T2, c1, c2, f1, f2, ro, Rin, 0.5, 2.0, 0.0,
+                                           full["index"][sel], rs)
+    assert present.all()
+    lens = np.ones(len(full["index"]), np.int64)
+    for d, sz in enumerate(rs):
+        lens *= np.asarray(sz, np.int64)[full["index"][:, d]]
+    ref = np.concatenate([full["data"][full["offsets"][b]:full["offsets"][b] + lens[b]] for b in sel])
+    np.testing.assert_allclose(vals, ref, rtol=1e-14, atol=1e-14)
