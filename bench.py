@@ -36,6 +36,10 @@ WORKLOAD = ("banded 4000x4000 blocks, sizes {5:.4,13:.4,23:.2}, ~1% occupancy "
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 CPU_SAMPLE_ROWS = (1000, 3000)     # cpu_baseline: block rows of A in the sample
 REF_SAMPLE_ROWS = (1800, 2200)     # --impl reference: block rows per step
+# timed-step precision -> (library constant name, numeric kernel launched by execute)
+PRECISIONS = {"fp64": ("BST_FP64", "k_num_fp64_persist1"),
+              "emu": ("BST_FP64_EMU_BF16", "k_num_emu_bf16_persist1"),
+              "tf32x3": ("BST_TF32X3", "k_num_tf32x3")}
 
 
 def parse():
@@ -47,6 +51,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the precision-variant legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nb", type=int, default=4000,
+                    help="block rows/columns of the banded workload (smaller for profiler captures)")
+    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS),
+                    help="precision of the timed step (the headline is native fp64)")
     return ap.parse_args()
 
 
@@ -225,13 +233,16 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     bst.load()
-    p = banded(seed=1002 + 1000 * rank)
+    p = banded(seed=1002 + 1000 * rank, nb=args.nb)
+    workload = WORKLOAD if args.nb == 4000 else WORKLOAD.replace("4000x4000", f"{args.nb}x{args.nb}")
+    prec_name, kernel = PRECISIONS[args.precision]
+    main_prec = getattr(bst, prec_name)
     mk = lambda m: bst.Matrix.from_host(m.row_sizes, m.col_sizes, m.rows, m.cols, m.data,
                                         device=local_rank)
     A, B = mk(p.A), mk(p.B)
     stream = torch.cuda.current_stream()
 
-    def step(precision=bst.BST_FP64, events=None):
+    def step(precision=main_prec, events=None):
         plan = bst.multiply_plan(A, B, None, p.eps, device=local_rank)
         plan.alloc_result(local_rank)
         if events is not None:
@@ -252,7 +263,9 @@ def run_ours(args):
     barrier()
     flops = keep.stats()["flops"]
     stats = keep.stats()
+    c_bytes = 8 * int(keep.result.info[3])
     del keep
+    ab_bytes = p.A.data.nbytes + p.B.data.nbytes
     clocks = ClockSampler(local_rank)
     clocks.start()
     l0 = bst.bst_kernel_launches()
@@ -289,18 +302,26 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "native fp64", "global_batch": world,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "emu": "bf16", "tf32x3": "tf32"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": workload,
+                   "precision": {"fp64": "native fp64", "emu": "fp64 emulated on bf16 slices",
+                                 "tf32x3": "3xtf32"}[args.precision],
+                   "global_batch": world,
                    "parallelism": f"{world} independent products, one per GPU",
-                   "l2": "inputs larger than L2 (A+B 0.36 GB read per step, C 4.1 GB written)",
+                   "l2": f"inputs larger than L2 (A+B {ab_bytes / 1e9:.2f} GB read per step, "
+                         f"C {c_bytes / 1e9:.2f} GB written)",
                    "flop_per_step_per_gpu": flops, "c_blocks": stats["n_c_blocks"],
                    "stack_entries": stats["n_stack"], "filtered": stats["n_filtered"]},
         "numeric_only": {"value": flops / (num_avg * 1e-3) / 1e9, "unit": UNIT,
                          "ms": num_avg},
-        "roofline": {"bound": "alu", "kernel": "k_num_fp64", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "peak_note": "FP64 FMA pipe: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz",
-                     "traffic": load_traffic("k_num_fp64_banded")},
+        "roofline": ({"bound": "alu", "kernel": kernel, "achieved": achieved,
+                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                      "frac": achieved / FP64_PEAK_TFLOPS,
+                      "peak_note": "FP64 FMA pipe: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz",
+                      "traffic": load_traffic("k_num_fp64_persist1_banded") if args.nb == 4000 else None}
+                     if args.precision == "fp64" else None),
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -343,10 +364,11 @@ def run_ours(args):
         line["precision_variants"] = extras
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        fl, times = cpu_baseline(p, CPU_SAMPLE_ROWS, steps=1)
+        rows = CPU_SAMPLE_ROWS if args.nb == 4000 else (args.nb // 4, 3 * args.nb // 4)
+        fl, times = cpu_baseline(p, rows, steps=1)
         line["cpu_baseline"] = {
             "value": fl / times[0] / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"block rows {CPU_SAMPLE_ROWS[0]}..{CPU_SAMPLE_ROWS[1]} of A times all of B "
+            "sample": f"block rows {rows[0]}..{rows[1]} of A times all of B "
                       f"({fl:.3e} flop, {times[0]:.1f} s, single thread)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
