@@ -1,15 +1,18 @@
 // Batches: many independent block-sparse products in one persistent kernel launch.
 //
 // A batch holds plans that were built with bst_multiply_plan / bst_contract_plan
-// (their symbolic phases are done).  Its work list is every C block of every plan
-// (every 16 x 8 warp tile for emulated FP64), tagged with the plan's index; plans are
-// listed by decreasing flops and each plan's C blocks in CSR order, and warps fetch
-// items dynamically from one counter, so one persistent grid balances products of very
-// different sizes while neighbouring warps keep sharing operand blocks.  bst_batch_execute only queues work: a parameter copy from the batch's
-// pinned staging buffer, the counter reset and the launches (plus the per-plan slicing
-// kernels for emulated FP64 and the permutations of contraction views), so a call can be
-// captured into a CUDA graph and replayed; everything that allocates or synchronises
-// happens in bst_batch_create.
+// (their symbolic phases are done).  Its work list is every C block of every plan,
+// tagged with the plan's index.  For native FP64 the list is sorted by decreasing cost
+// across the batch, so one persistent grid balances products of very different sizes
+// (the staged kernel takes items in a fixed stride, the direct-load kernel from a
+// counter).  For emulated FP64 the plans are listed by
+// decreasing flops and each plan's C blocks in CSR order, and warps take a few
+// consecutive items at a time from a counter, so neighbouring warps share operand
+// digits.  bst_batch_execute only
+// queues work: a parameter copy from the batch's pinned staging buffer, the counter
+// reset and the launches (plus the per-plan slicing kernels for emulated FP64 and the
+// permutations of contraction views), so a call can be captured into a CUDA graph and
+// replayed; everything that allocates or synchronises happens in bst_batch_create.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -28,7 +31,8 @@ struct bst_batch {
   void *d_params = nullptr, *h_params = nullptr;
   size_t pbytes = 0;
   int grid = 0;
-  // emulated FP64 schedule (item = plan << 48 | C block << 16 | tile)
+  int stage_elems = 0;  // staged FP64 kernel slot size (0: some plan needs direct loads)
+  // emulated FP64 schedule (item = plan << 32 | C block)
   int64_t n_items_e = 0;
   int64_t *items_e = nullptr;
   void *d_eparams = nullptr, *h_eparams = nullptr;
@@ -117,7 +121,18 @@ bst_status bst_batch_create(bst_ctx *ctx, int32_t n, bst_plan *const *plans, bst
       b->d_params = b->ar.alloc(b->pbytes * n);
       BST_CUDA(cudaMallocHost(&b->h_params, b->pbytes * n));
       b->grid = bst::persist_grid(ctx->num_sms);
-      // emulated FP64: every 16 x 8 tile (slicing state built per plan here)
+      b->stage_elems = 0;
+      {
+        bool all = true;
+        int mx = 0;
+        for (auto *p : b->plans) {
+          if (p->C->nblocks == 0) continue;
+          if (p->stage_elems == 0) all = false;
+          mx = std::max(mx, (int)p->stage_elems);
+        }
+        if (all) b->stage_elems = std::max(mx, 1);
+      }
+      // emulated FP64: every C block (slicing state built per plan here)
       std::vector<int64_t> cnt(n);
       for (int32_t q = 0; q < n; ++q) {
         cnt[q] = b->plans[q]->contract ? 0 : bst::emu_item_count(b->plans[q], s);
@@ -126,7 +141,7 @@ bst_status bst_batch_create(bst_ctx *ctx, int32_t n, bst_plan *const *plans, bst
       b->items_e = b->ar.alloc_n<int64_t>((size_t)b->n_items_e);
       off = 0;
       for (int32_t q : order) {
-        if (cnt[q]) bst::emu_build_items(b->plans[q], (int64_t)q << 48, b->items_e + off, s);
+        if (cnt[q]) bst::emu_build_items(b->plans[q], (int64_t)q << 32, b->items_e + off, s);
         off += cnt[q];
       }
       b->epbytes = bst::emu_params_bytes();
@@ -171,7 +186,11 @@ bst_status bst_batch_execute(bst_batch *b, const double *alpha, const double *be
         bst::fill_num_params(b->plans[q], r.a, static_cast<char *>(b->h_params) + q * b->pbytes);
       }
       BST_CUDA(cudaMemcpyAsync(b->d_params, b->h_params, b->pbytes * n, cudaMemcpyHostToDevice, s));
-      bst::launch_fp64_persist(b->d_params, b->items, b->n_items, b->counter, b->grid, s);
+      if (b->stage_elems > 0)
+        bst::launch_fp64_staged(b->d_params, b->items, b->n_items, b->stage_elems,
+                                b->ctx->num_sms, s);
+      else
+        bst::launch_fp64_persist(b->d_params, b->items, b->n_items, b->counter, b->grid, s);
     } else {
       for (int32_t q = 0; q < n; ++q) {
         BST_REQUIRE(!b->plans[q]->contract, BST_ERR_UNSUPPORTED,

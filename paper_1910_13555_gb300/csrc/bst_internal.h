@@ -223,6 +223,11 @@ struct bst_plan {
   // persistent numeric schedule: C blocks by decreasing cost, counter of taken items
   int64_t *items = nullptr;
   unsigned long long *items_counter = nullptr;
+  // staged numeric kernel: C-major entries, C block descriptors, doubles per slot
+  // (0: products too large for a slot, the direct-load kernel runs)
+  int4 *fents = nullptr;
+  int32_t *fdesc = nullptr;
+  int32_t stage_elems = 0;
   // stats
   bst_stats stats{};
   // emulated-precision state (numeric_emu.cu), built on first use
@@ -272,6 +277,9 @@ void sort_items(const int64_t *items, const int32_t *keys, int64_t n, int64_t *o
 int persist_grid(int num_sms);
 void launch_fp64_persist(const void *params, const int64_t *items, int64_t nitems,
                          unsigned long long *counter, int grid, cudaStream_t s);
+void build_f64_schedule(bst_plan *p, cudaStream_t s);
+void launch_fp64_staged(const void *params, const int64_t *items, int64_t nitems,
+                        int slot_elems, int num_sms, cudaStream_t s);
 // persistent emulated-FP64 numeric (numeric_emu.cu)
 size_t emu_params_bytes();
 int64_t emu_item_count(bst_plan *p, cudaStream_t s);

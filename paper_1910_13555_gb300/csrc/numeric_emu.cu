@@ -48,6 +48,7 @@ constexpr int kSlices = 6;     // BF16 digits per operand
 constexpr int kBeta = 8;       // bits per digit
 constexpr int kSegChunks = 2;  // 16-wide K chunks per exact FP32 segment (32 elements)
 constexpr int kExpNone = -4000;
+constexpr int kDescWords = 8;  // int32 words per C block descriptor of the BF16 kernel
 
 struct EmuState {
   Arena ar;
@@ -56,10 +57,9 @@ struct EmuState {
   int64_t *a_doff = nullptr, *b_doff = nullptr, *a_toff = nullptr, *b_toff = nullptr;
   int64_t *a_eoff = nullptr, *b_eoff = nullptr;
   int64_t a_dsize = 0, b_dsize = 0, a_tsize = 0, b_tsize = 0, a_esize = 0, b_esize = 0;
-  int32_t guard = 0;
-  int64_t nwarps = 0, nwarps_b = 0;
+  int64_t nwarps = 0;            // 3xTF32 warps (one per 16 x 16 tile)
+  int64_t nitems_b = 0;          // BF16 work items (one per C block)
   int64_t *wstart = nullptr;    // per (m,n) class: first warp, 16 x 16 tiles (3xTF32)
-  int64_t *wstart_b = nullptr;  // per (m,n) class: first warp, 16 x 8 tiles (BF16 slices)
   int32_t ncls = 0;
   // global start of every op(A) row block / op(B) column block, and the largest
   // exponent of every op(A) row / op(B) column over all blocks
@@ -71,15 +71,15 @@ struct EmuState {
   float *a_tf = nullptr, *b_tf = nullptr;
   int32_t *a_exp = nullptr, *b_exp = nullptr;
   bool dig_alloc = false, tf_alloc = false;
-  // per stack entry: offsets of its A and B digit blocks
-  int64_t *e_adoff = nullptr, *e_bdoff = nullptr;
-  // persistent schedule of the BF16 warp tiles, built for one tuning state
+  // C-major stack entries of the BF16 kernel (int4 each) and where each C block's start
+  int4 *ents = nullptr;
+  int64_t *ebeg = nullptr;
+  // C block descriptors, built for one tuning state (the tile orientation per class)
+  int32_t *desc = nullptr;
   int32_t *cls_swap = nullptr;
+  unsigned long long *counter = nullptr;  // work counter of the persistent kernel
   int64_t sched_version = -1;
   int sched_rows = -1;
-  int64_t items_cap = 0;
-  int64_t *items = nullptr;
-  unsigned long long *counter = nullptr;
 };
 
 namespace {
@@ -139,63 +139,111 @@ __device__ __forceinline__ void op_coords(const SideArgs &S, int rs, int cs, int
   }
 }
 
-__global__ void k_emu_exponents(SideArgs S) {
-  const int lane = threadIdx.x & 31;
-  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (b >= S.nblocks) return;
+// Both side kernels run one warp per stored block; four lanes share one 16-wide chunk of
+// one op row (A side) or op column (B side) and lane t of the four takes the inner
+// indices 2t, 2t+1, 2t+8, 2t+9 of the chunk -- the four values that the digit layout
+// stores next to each other (positions 4t..4t+3).  Elements are read in the stored
+// block's layout: element (outer, inner) sits at outer * Cc + inner when the op keeps
+// the stored rows as outer (op(A) = A, op(B) = B^T), else at inner * Cc + outer.
+struct SideBlock {
+  const double *x;
+  int Cc, nouter, ninner, nch;
+  bool outer_major;
+  int64_t gbase;
+};
+
+__device__ __forceinline__ SideBlock side_block(const SideArgs &S, int64_t b) {
+  SideBlock B;
   const int R = S.rsz[S.row[b]], Cc = S.csz[S.col[b]];
-  const double *x = S.data + S.off[b];
+  B.x = S.data + S.off[b];
+  B.Cc = Cc;
+  B.nouter = S.is_b ? (S.trans ? R : Cc) : (S.trans ? Cc : R);
+  B.ninner = S.is_b ? (S.trans ? Cc : R) : (S.trans ? R : Cc);
+  B.nch = (B.ninner + 15) >> 4;
+  B.outer_major = S.is_b == S.trans;
   // op block index along the exponent dimension (rows of op(A), columns of op(B))
   const int obr = S.trans ? S.col[b] : S.row[b], obc = S.trans ? S.row[b] : S.col[b];
-  const int64_t gbase = S.start[S.is_b ? obc : obr];
-  for (int e = lane; e < R * Cc; e += 32) {
-    int outer, inner;
-    op_coords(S, e / Cc, e % Cc, outer, inner);
-    const int E = exp_of(x[e]);
-    if (E != kExpNone) {
+  B.gbase = S.start[S.is_b ? obc : obr];
+  return B;
+}
+
+__device__ __forceinline__ double side_value(const SideBlock &B, int outer, int inner) {
+  if (inner >= B.ninner) return 0.0;
+  return B.x[B.outer_major ? outer * B.Cc + inner : inner * B.Cc + outer];
+}
+
+// inner index (within its chunk) of digit position 4t + u
+__device__ __forceinline__ int chunk_inner(int t, int u) { return 2 * t + (u & 1) + 8 * (u >> 1); }
+
+// largest exponent of every op row (column) of a block and of the whole op row (column):
+// the four lanes of a chunk combine their maxima, then one atomic per chunk and target
+__global__ void k_emu_exponents(SideArgs S) {
+  const int lane = threadIdx.x & 31, t = lane & 3;
+  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (b >= S.nblocks) return;
+  const SideBlock B = side_block(S, b);
+  const int total = B.nouter * B.nch;
+  for (int q0 = 0; q0 < total; q0 += 8) {  // uniform trip count: every lane shuffles
+    const int q = q0 + (lane >> 2);
+    const bool ok = q < total;
+    const int outer = ok ? q / B.nch : 0, ch = ok ? q - outer * B.nch : 0;
+    int E = kExpNone;
+    if (ok)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) E = max(E, exp_of(side_value(B, outer, ch * 16 + chunk_inner(t, u))));
+    E = max(E, __shfl_xor_sync(0xffffffffu, E, 1));
+    E = max(E, __shfl_xor_sync(0xffffffffu, E, 2));
+    if (ok && t == 0 && E != kExpNone) {
       atomicMax(&S.bexp[S.eoff[b] + outer], E);
-      atomicMax(&S.gexp[gbase + outer], E);
+      atomicMax(&S.gexp[B.gbase + outer], E);
     }
   }
 }
 
+// The six digit planes of a block, every position written (zero padding included), one
+// 8-byte store per plane and lane.  With 2^E the scale of the element's op row (column),
+// N = round(|v| 2^(48 - E)) < 2^48 (+1) is cut into 8-bit digits, the leading one taking
+// the rounding carry (it may reach 2^8); all are exact in BF16.
 __global__ void k_emu_digits(SideArgs S) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, t = lane & 3;
   const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (b >= S.nblocks) return;
-  const int R = S.rsz[S.row[b]], Cc = S.csz[S.col[b]];
-  const int nouter = S.is_b ? (S.trans ? R : Cc) : (S.trans ? Cc : R);
-  const int ninner = S.is_b ? (S.trans ? Cc : R) : (S.trans ? R : Cc);
-  const int kp = (ninner + 15) & ~15;
-  const int64_t plane = (int64_t)nouter * kp;
-  const double *x = S.data + S.off[b];
+  const SideBlock B = side_block(S, b);
+  const int kp = B.nch * 16;
+  const int64_t plane = (int64_t)B.nouter * kp;
   __nv_bfloat16 *d = S.dig + S.doff[b];
-  const int obr = S.trans ? S.col[b] : S.row[b], obc = S.trans ? S.row[b] : S.col[b];
-  const int64_t gbase = S.start[S.is_b ? obc : obr];
-  for (int e = lane; e < R * Cc; e += 32) {
-    int outer, inner;
-    op_coords(S, e / Cc, e % Cc, outer, inner);
-    const double v = x[e];
-    const int E = S.row_scale ? S.gexp[gbase + outer] : S.bexp[S.eoff[b] + outer];
-    const long long bits = __double_as_longlong(v);
-    const int ex = (int)((bits >> 52) & 0x7ff);
-    unsigned long long N = 0;
-    if (ex != 0 && E != kExpNone) {
-      const unsigned long long M = (unsigned long long)(bits & 0xfffffffffffffLL) | (1ull << 52);
-      // N = round(|v| 2^(42 - E)) = round(M 2^(ex - 1075 + 42 - E)); the shift is >= 11
-      const int rsh = 1075 - kSlices * kBeta - ex + E;
-      if (rsh < 64) N = (M + (1ull << (rsh - 1))) >> rsh;
-    }
-    const bool neg = bits < 0;
-    const int64_t pos = (int64_t)outer * kp + perm16(inner);
+  const int total = B.nouter * B.nch;
+  for (int q = lane >> 2; q < total; q += 8) {
+    const int outer = q / B.nch, ch = q - outer * B.nch;
+    const int E = S.row_scale ? S.gexp[B.gbase + outer] : S.bexp[S.eoff[b] + outer];
+    uint32_t w[kSlices][2];
 #pragma unroll
-    for (int s = 0; s < kSlices; ++s) {
-      // the leading digit may reach 2^kBeta after rounding; the others stay below it
-      const unsigned mask = s == 0 ? (2u << kBeta) - 1u : (1u << kBeta) - 1u;
-      int dg = (int)((N >> (kBeta * (kSlices - 1 - s))) & mask);
-      if (neg) dg = -dg;
-      d[s * plane + pos] = __float2bfloat16_rn((float)dg);
+    for (int s = 0; s < kSlices; ++s) w[s][0] = w[s][1] = 0u;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long bits = __double_as_longlong(side_value(B, outer, ch * 16 + chunk_inner(t, u)));
+      const int ex = (int)((bits >> 52) & 0x7ff);
+      unsigned long long N = 0;
+      if (ex != 0 && E != kExpNone) {
+        const unsigned long long M = (unsigned long long)(bits & 0xfffffffffffffLL) | (1ull << 52);
+        // N = round(M 2^(ex - 1075 + 48 - E)); |v| < 2^E makes the shift >= 5
+        const int rsh = 1075 - kSlices * kBeta - ex + E;
+        if (rsh < 64) N = (M + (1ull << (rsh - 1))) >> rsh;
+      }
+      const bool neg = bits < 0;
+#pragma unroll
+      for (int s = 0; s < kSlices; ++s) {
+        const unsigned mask = s == 0 ? (2u << kBeta) - 1u : (1u << kBeta) - 1u;
+        int dg = (int)((N >> (kBeta * (kSlices - 1 - s))) & mask);
+        if (neg) dg = -dg;
+        const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn((float)dg));
+        w[s][u >> 1] |= h << (16 * (u & 1));
+      }
     }
+    __nv_bfloat16 *p = d + (int64_t)outer * kp + ch * 16 + 4 * t;
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s)
+      *reinterpret_cast<uint2 *>(p + s * plane) = make_uint2(w[s][0], w[s][1]);
   }
 }
 
@@ -241,24 +289,73 @@ __global__ void k_side_sizes(SideArgs S, int64_t *dsz, int64_t *tsz, int64_t *es
   esz[b] = nouter;
 }
 
-__global__ void k_entry_doffs(int64_t T, const int32_t *__restrict__ s_ab,
-                              const int32_t *__restrict__ s_bb, const int64_t *__restrict__ a_doff,
-                              const int64_t *__restrict__ b_doff, int64_t *__restrict__ ea,
-                              int64_t *__restrict__ eb) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= T) return;
-  ea[e] = a_doff[s_ab[e]];
-  eb[e] = b_doff[s_bb[e]];
-}
+// ---- per-plan index of the BF16 kernel ------------------------------------------------
 
-// largest sum of inner sizes over the products of one C block
-__global__ void k_max_ktot(int64_t nc, int32_t Dk, const int32_t *run_len, const int32_t *kval,
-                           unsigned long long *out) {
+// number of stack entries of every C block (over all its k classes)
+__global__ void k_emu_ent_count(int64_t nc, int32_t Dk, const int32_t *__restrict__ run_len,
+                                int32_t *__restrict__ cnt) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
-  unsigned long long s = 0;
-  for (int kc = 0; kc < Dk; ++kc) s += (unsigned long long)run_len[c * Dk + kc] * kval[kc];
-  atomicMax(out, s);
+  int s = 0;
+  for (int kc = 0; kc < Dk; ++kc) s += run_len[c * Dk + kc];
+  cnt[c] = s;
+}
+
+// C-major entry list: the entries of C block c at [ebeg[c], ebeg[c+1]), k classes in
+// order; entry = {A digit block offset / 16, B digit block offset / 16, 16-chunks of the
+// inner size, stack entry}.  Digit blocks start on multiples of 16 elements (every
+// block's digit size is 6 * outer * inner rounded up to 16).
+__global__ void k_emu_ents(int64_t nc, int32_t Dk, const int32_t *__restrict__ run_start,
+                           const int32_t *__restrict__ run_len, const int32_t *__restrict__ kval,
+                           const int32_t *__restrict__ s_ab, const int32_t *__restrict__ s_bb,
+                           const int64_t *__restrict__ a_doff, const int64_t *__restrict__ b_doff,
+                           const int64_t *__restrict__ ebeg, int4 *__restrict__ ents) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  int64_t q = ebeg[c];
+  for (int kc = 0; kc < Dk; ++kc) {
+    const int len = run_len[c * Dk + kc];
+    if (len == 0) continue;
+    const int e0 = run_start[c * Dk + kc], nch = (kval[kc] + 15) >> 4;
+    for (int e = e0; e < e0 + len; ++e)
+      ents[q++] = make_int4((int)(unsigned)(a_doff[s_ab[e]] >> 4),
+                            (int)(unsigned)(b_doff[s_bb[e]] >> 4), nch, e);
+  }
+}
+
+// C block descriptors (kDescWords words each; see EmuBlk).  The guard G of a block keeps
+// its K_tot products of at most 2^56 units each below 2^62 after the shift by G.
+__global__ void k_emu_desc(int64_t nc, int32_t Dk, const int32_t *__restrict__ run_len,
+                           const int32_t *__restrict__ kval, const int64_t *__restrict__ ebeg,
+                           const int64_t *__restrict__ c_off, const int32_t *__restrict__ c_row,
+                           const int32_t *__restrict__ c_col, const int32_t *__restrict__ c_cls,
+                           const int32_t *__restrict__ cls_m, const int32_t *__restrict__ cls_n,
+                           const int32_t *__restrict__ cls_swap, const int32_t *__restrict__ c_cin,
+                           const int64_t *__restrict__ a_rowstart,
+                           const int64_t *__restrict__ b_colstart, int32_t *__restrict__ desc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  long long ktot = 0;
+  for (int kc = 0; kc < Dk; ++kc) ktot += (long long)run_len[c * Dk + kc] * kval[kc];
+  int lg = 0;
+  while (lg < 63 && (1ll << lg) <= ktot) ++lg;
+  const int guard = max(0, lg - (62 - (kSlices + 1) * kBeta));
+  const int cls = c_cls[c];
+  int32_t *d = desc + c * kDescWords;
+  d[0] = (int32_t)c_off[c];
+  d[1] = (int32_t)ebeg[c];
+  d[2] = (int32_t)(ebeg[c + 1] - ebeg[c]);
+  d[3] = (int32_t)a_rowstart[c_row[c]];
+  d[4] = (int32_t)b_colstart[c_col[c]];
+  d[5] = cls_m[cls] | (cls_n[cls] << 12) | (cls_swap[cls] << 24) | (guard << 25);
+  d[6] = c_cin[c];
+  d[7] = (int32_t)c;
+}
+
+// items of a plan in a batch: base | C block
+__global__ void k_emu_items(int64_t nc, int64_t base, int64_t *__restrict__ items) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc) items[c] = base | c;
 }
 
 // ---- integer -> FP64 ---------------------------------------------------------------
@@ -334,10 +431,9 @@ struct EmuParams {
   const double *Cin;
   double *C;
   double alpha, beta;
-  int32_t Dk, ncls, guard;
+  int32_t Dk, ncls;
   const int64_t *wstart;
   int32_t tiles_n;  // N-tiles of 8 columns per warp (1 or 2)
-  const int32_t *cls_swap;  // per (m,n) class: tile orientation of the BF16 kernel
   int32_t alpha_one, has_beta;  // alpha == 1, beta != 0 (set on the host: FP64 compares
                                 // would occupy GB300's slow FP64 pipe in every tile)
   int32_t row_scale;  // 1: digits scaled per whole op row / column (shared by all products)
@@ -347,7 +443,8 @@ struct EmuParams {
   const int32_t *c_row, *c_col, *c_cin, *c_cls;
   const int64_t *c_off, *cin_off;
   const int32_t *run_start, *run_len, *s_ab, *s_bb;
-  const int64_t *e_adoff, *e_bdoff;  // per entry digit offsets (row-scaled kernel)
+  const int32_t *desc;  // BF16 kernel: C block descriptors (kDescWords each)
+  const int4 *ents;     // BF16 kernel: C-major entries
   const int64_t *a_doff, *b_doff, *a_eoff, *b_eoff;
   const __nv_bfloat16 *a_dig, *b_dig;
   const float *a_tf, *b_tf;
@@ -413,306 +510,320 @@ __device__ __forceinline__ void slot_rc(const WarpTask &w, int nt, int h, int &r
   c = (2 * w.ng + nt) * 8 + 2 * t + (h & 1);
 }
 
-// One warp per 16 x 8 tile (w.mt, w.ng) of one C block.  Per stack entry: the six A
-// digit fragments are loaded once (two 8-byte loads each), each B digit fragment once,
-// and the 21 kept slice products go to six FP32 level accumulators; the levels are then
-// folded into the int64 accumulators at the element's common scale.
-// Row-scaled form: every product of a C element shares the element's scale
-// 2^{E_row + F_col}, so the FP32 level sums run across products and are folded into the
-// int64 accumulators only when 32 inner elements have been summed (or at the end).
-// Folding and output touch only the lane's valid elements; offsets are 32-bit element
-// counts (a plan's digit arrays hold fewer than 2^31 elements).
-__device__ __forceinline__ void emu_tile_rows(const EmuParams &P, const WarpTask &w) {
+// ---- the BF16 slice kernel: one warp per C block -----------------------------------
+//
+// A warp takes C blocks in a fixed stride over the work list (C block order, so warps
+// running at the same time share op(A) digit rows in L2) and prefetches the descriptor
+// of its next block while it computes the current one.  A block's stack entries (most
+// blocks have one or two) are loaded once, one per lane, and broadcast with shuffles;
+// the warp then runs the block's 16 x 8 tiles one after another.
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// a C block as the kernel sees it, decoded from its descriptor words
+//   0 element offset, 1 first entry, 2 entry count, 3 first global op(A) row of its
+//   block row, 4 first global op(B) column of its block column,
+//   5 m | n << 12 | swap << 24 | guard << 25, 6 C_in block (-1: none), 7 C block
+struct EmuBlk {
+  int off, eb, ne, rbase, cbase, m, n, sw, guard, cin;
+};
+
+__device__ __forceinline__ EmuBlk emu_blk(int dw) {
+  EmuBlk b;
+  b.off = __shfl_sync(kFull, dw, 0);
+  b.eb = __shfl_sync(kFull, dw, 1);
+  b.ne = __shfl_sync(kFull, dw, 2);
+  b.rbase = __shfl_sync(kFull, dw, 3);
+  b.cbase = __shfl_sync(kFull, dw, 4);
+  const int mn = __shfl_sync(kFull, dw, 5);
+  b.cin = __shfl_sync(kFull, dw, 6);
+  b.m = mn & 0xfff;
+  b.n = (mn >> 12) & 0xfff;
+  b.sw = (mn >> 24) & 1;
+  b.guard = (mn >> 25) & 0x3f;
+  return b;
+}
+
+// The four elements a lane owns in tile (mt, ng): tile rows r0, r1 = mt*16 + g (+8),
+// tile columns cc0, cc1 = ng*8 + 2t (+1); tile space is the C block, or its transpose
+// when the class runs swapped.
+struct TileLane {
+  int r0, r1, cc0, cc1, colB;
+  bool v0, v1, vB;
+  bool valid[4];
+  int ref[4];  // exponent of each element's common scale (whole op row + op column)
+};
+
+__device__ __forceinline__ TileLane tile_lane(const EmuParams &P, const EmuBlk &b, int mt, int ng) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  // tile space: RM rows x RN columns; with w.sw the rows are the C block's columns and the
-  // row operand is op(B)^T (its digit planes are stored column by column already)
-  const int sw = w.sw;
-  const int RM = sw ? w.n : w.m, RN = sw ? w.m : w.n;
-  const __nv_bfloat16 *Xa = sw ? P.b_dig : P.a_dig, *Xb = sw ? P.a_dig : P.b_dig;
-  const int64_t *eXa = sw ? P.e_bdoff : P.e_adoff, *eXb = sw ? P.e_adoff : P.e_bdoff;
-  const int r0 = w.mt * 16 + g, r1 = r0 + 8;
-  const bool v0 = r0 < RM, v1 = r1 < RM;
-  const int colB = w.ng * 8 + g;
-  const bool vB = colB < RN;
-  const int cc0 = w.ng * 8 + 2 * t, cc1 = cc0 + 1;
-  const bool vc0 = cc0 < RN, vc1 = cc1 < RN;
-  const bool valid[4] = {v0 && vc0, v0 && vc1, v1 && vc0, v1 && vc1};
-  const int i = P.c_row[w.c], j = P.c_col[w.c];
-  // largest exponent of a whole op(A) row (index x of block row i) / op(B) column
-  auto erow = [&](int x) { return P.row_exp[P.a_rowstart[i] + x]; };
-  auto ecol = [&](int x) { return P.col_exp[P.b_colstart[j] + x]; };
-  int ref[4];
-  {
-    const int E0 = v0 ? (sw ? ecol(r0) : erow(r0)) : kExpNone;
-    const int E1 = v1 ? (sw ? ecol(r1) : erow(r1)) : kExpNone;
-    const int F0 = vc0 ? (sw ? erow(cc0) : ecol(cc0)) : kExpNone;
-    const int F1 = vc1 ? (sw ? erow(cc1) : ecol(cc1)) : kExpNone;
-    ref[0] = E0 + F0;
-    ref[1] = E0 + F1;
-    ref[2] = E1 + F0;
-    ref[3] = E1 + F1;
+  const int RM = b.sw ? b.n : b.m, RN = b.sw ? b.m : b.n;
+  TileLane L;
+  L.r0 = mt * 16 + g;
+  L.r1 = L.r0 + 8;
+  L.v0 = L.r0 < RM;
+  L.v1 = L.r1 < RM;
+  L.colB = ng * 8 + g;
+  L.vB = L.colB < RN;
+  L.cc0 = ng * 8 + 2 * t;
+  L.cc1 = L.cc0 + 1;
+  const bool vc0 = L.cc0 < RN, vc1 = L.cc1 < RN;
+  L.valid[0] = L.v0 && vc0;
+  L.valid[1] = L.v0 && vc1;
+  L.valid[2] = L.v1 && vc0;
+  L.valid[3] = L.v1 && vc1;
+  const int32_t *ER = b.sw ? P.col_exp + b.cbase : P.row_exp + b.rbase;  // tile rows
+  const int32_t *EC = b.sw ? P.row_exp + b.rbase : P.col_exp + b.cbase;  // tile columns
+  const int E0 = L.v0 ? ER[L.r0] : kExpNone, E1 = L.v1 ? ER[L.r1] : kExpNone;
+  const int F0 = vc0 ? EC[L.cc0] : kExpNone, F1 = vc1 ? EC[L.cc1] : kExpNone;
+  L.ref[0] = E0 + F0;
+  L.ref[1] = E0 + F1;
+  L.ref[2] = E1 + F0;
+  L.ref[3] = E1 + F1;
+  return L;
+}
+
+// C = alpha * acc * 2^(ref - 56 + G) + beta * C_in for the lane's valid elements
+__device__ __forceinline__ void emu_store(const EmuParams &P, const EmuBlk &b, const TileLane &L,
+                                          const long long (&acc)[4]) {
+  const double *ci = (P.has_beta && b.cin >= 0) ? P.Cin + P.cin_off[b.cin] : nullptr;
+  const int sh = (kSlices + 1) * kBeta - b.guard;
+  // element (x, y) of the tile is C(x, y), or C(y, x) when swapped
+  auto cidx = [&](int h) {
+    const int x = h < 2 ? L.r0 : L.r1, y = (h & 1) ? L.cc1 : L.cc0;
+    return b.sw ? y * b.n + x : x * b.n + y;
+  };
+  if (P.alpha_one && !ci) {  // plain stores: no FP64 instruction at all
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+      if (L.valid[h]) P.C[b.off + cidx(h)] = i64_ldexp(acc[h], L.ref[h] - sh);
+  } else {
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+      if (L.valid[h]) {
+        double v = P.alpha * i64_ldexp(acc[h], L.ref[h] - sh);
+        if (ci) v = fma(P.beta, ci[cidx(h)], v);
+        P.C[b.off + cidx(h)] = v;
+      }
   }
+}
+
+// the six exact FP32 level sums of element h as one integer in units of 2^-56 of the
+// scale: I = sum_w D_w 2^(8(5 - w)), |I| < 2^62.  Levels weighted below 2^32 go
+// through 32 x 32 -> 64-bit multiply-adds; the two top levels (|D_0| < 2^21.1,
+// |D_1| < 2^22) are combined in 32 bits and added to the upper word.
+__device__ __forceinline__ long long fold_levels(const float (&lv)[kSlices][4], int h) {
+  long long lo = __float2int_rn(lv[kSlices - 1][h]);
+  int hi = 0;
+#pragma unroll
+  for (int s = kSlices - 2; s >= 0; --s) {
+    const int sh = kBeta * (kSlices - 1 - s);
+    const int d = __float2int_rn(lv[s][h]);
+    if (sh < 32)
+      lo += (long long)d * (long long)(1u << sh);
+    else
+      hi += d * (1 << (sh - 32));
+  }
+  return lo + (long long)((unsigned long long)(unsigned)hi << 32);
+}
+
+__device__ __forceinline__ int4 load_ent(const EmuParams &P, const EmuBlk &b, int q) {
+  return q < b.ne ? P.ents[(int64_t)b.eb + q] : make_int4(0, 0, 0, 0);
+}
+
+// Row-scaled tile: per entry, the row operand's six digit fragments (two 8-byte loads
+// each) and the column operand's six (one each) feed the 21 kept slice products into
+// six FP32 level sums.  All products of an element share its scale, so the level sums
+// run across entries and are folded into the int64 accumulators every 32 inner
+// elements (or at the end).
+__device__ __forceinline__ void emu_tile_rs(const EmuParams &P, const EmuBlk &b, int mt, int ng,
+                                            const int4 &ent0) {
+  const int lane = threadIdx.x & 31, t = lane & 3;
+  const TileLane L = tile_lane(P, b, mt, ng);
+  const int RM = b.sw ? b.n : b.m, RN = b.sw ? b.m : b.n;
+  const __nv_bfloat16 *Xa = b.sw ? P.b_dig : P.a_dig, *Xb = b.sw ? P.a_dig : P.b_dig;
   long long acc[4] = {0, 0, 0, 0};
-  float accw[kSlices][4];
+  float lv[kSlices][4];
 #pragma unroll
   for (int s = 0; s < kSlices; ++s)
 #pragma unroll
-    for (int h = 0; h < 4; ++h) accw[s][h] = 0.f;
-  int used = 0;  // 16-wide chunks summed into accw since the last fold
+    for (int h = 0; h < 4; ++h) lv[s][h] = 0.f;
+  int used = 0;  // 16-wide chunks summed into lv since the last fold
   auto fold = [&]() {
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-      if (valid[h]) {
-        long long I = __float2int_rn(accw[0][h]);
-#pragma unroll
-        for (int s = 1; s < kSlices; ++s) I = (I << kBeta) + __float2int_rn(accw[s][h]);
-        acc[h] += round_shift(I, P.guard);
+      if (L.valid[h]) {
+        const long long I = fold_levels(lv, h);
+        acc[h] += b.guard ? round_shift(I, b.guard) : I;
       }
 #pragma unroll
-      for (int s = 0; s < kSlices; ++s) accw[s][h] = 0.f;
+      for (int s = 0; s < kSlices; ++s) lv[s][h] = 0.f;
     }
     used = 0;
   };
   const uint2 zero = make_uint2(0u, 0u);
-  for (int kc = 0; kc < P.Dk; ++kc) {
-    const int64_t rr = (int64_t)w.c * P.Dk + kc;
-    const int len = P.run_len[rr];
-    if (len == 0) continue;
-    const int e0 = P.run_start[rr];
-    const int k = P.kval[kc], kp = (k + 15) & ~15, nch = kp >> 4;
-    // per-thread element offsets inside one digit plane of the row and column operands
-    const int pa = RM * kp, pb = RN * kp;
-    const int oa0 = r0 * kp + 4 * t, oa1 = r1 * kp + 4 * t, ob = colB * kp + 4 * t;
-    int64_t ao = eXa[e0], bo = eXb[e0];
-    for (int e = e0; e < e0 + len; ++e) {
-      const __nv_bfloat16 *Ad = Xa + ao;
-      const __nv_bfloat16 *Bd = Xb + bo;
-      if (e + 1 < e0 + len) {  // next entry's offsets, loaded ahead of this entry's MMAs
-        ao = eXa[e + 1];
-        bo = eXb[e + 1];
-      }
+  for (int g0 = 0; g0 < b.ne; g0 += 32) {
+    const int4 ent = g0 == 0 ? ent0 : load_ent(P, b, g0 + lane);
+    const int cnt = min(32, b.ne - g0);
+    for (int j = 0; j < cnt; ++j) {
+      const unsigned ea = (unsigned)__shfl_sync(kFull, ent.x, j);
+      const unsigned eb = (unsigned)__shfl_sync(kFull, ent.y, j);
+      const int nch = __shfl_sync(kFull, ent.z, j);
+      const __nv_bfloat16 *Ad = Xa + 16 * (size_t)(b.sw ? eb : ea);
+      const __nv_bfloat16 *Bd = Xb + 16 * (size_t)(b.sw ? ea : eb);
+      // per-thread element offsets inside one digit plane of the row / column operand
+      const int kp = nch * 16, pa = RM * kp, pb = RN * kp;
+      const int oa0 = L.r0 * kp + 4 * t, oa1 = L.r1 * kp + 4 * t, ob = L.colB * kp + 4 * t;
       for (int ch = 0; ch < nch; ++ch) {
         if (used == kSegChunks) fold();
         const int cofs = ch * 16;
-        // the six B digit fragments (one 8-byte load each), then A digit by digit
         uint2 bf[kSlices];
 #pragma unroll
-        for (int tt = 0; tt < kSlices; ++tt) bf[tt] = vB ? ld8(Bd + (tt * pb + ob + cofs)) : zero;
+        for (int tt = 0; tt < kSlices; ++tt) bf[tt] = L.vB ? ld8(Bd + (tt * pb + ob + cofs)) : zero;
 #pragma unroll
         for (int s = 0; s < kSlices; ++s) {
-          const uint2 x0 = v0 ? ld8(Ad + (s * pa + oa0 + cofs)) : zero;
-          const uint2 x1 = v1 ? ld8(Ad + (s * pa + oa1 + cofs)) : zero;
+          const uint2 x0 = L.v0 ? ld8(Ad + (s * pa + oa0 + cofs)) : zero;
+          const uint2 x1 = L.v1 ? ld8(Ad + (s * pa + oa1 + cofs)) : zero;
           const uint32_t af[4] = {x0.x, x1.x, x0.y, x1.y};
 #pragma unroll
-          for (int tt = 0; s + tt < kSlices; ++tt) mma_bf16(accw[s + tt], af, bf[tt].x, bf[tt].y);
+          for (int tt = 0; s + tt < kSlices; ++tt) mma_bf16(lv[s + tt], af, bf[tt].x, bf[tt].y);
         }
         ++used;
       }
     }
   }
   fold();
-  const int64_t off = P.c_off[w.c];
-  const int cin = P.c_cin[w.c];
-  const double *ci = (P.has_beta && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
-  const int sh = (kSlices + 1) * kBeta - P.guard;
-  // element (x, y) of the tile is C(x, y), or C(y, x) when swapped
-  auto cidx = [&](int h) {
-    const int x = h < 2 ? r0 : r1, y = (h & 1) ? cc1 : cc0;
-    return sw ? y * w.n + x : x * w.n + y;
-  };
-  if (P.alpha_one && !ci) {  // plain stores: no FP64 instruction at all
-#pragma unroll
-    for (int h = 0; h < 4; ++h)
-      if (valid[h]) P.C[off + cidx(h)] = i64_ldexp(acc[h], ref[h] - sh);
-  } else {
-#pragma unroll
-    for (int h = 0; h < 4; ++h)
-      if (valid[h]) {
-        double v = P.alpha * i64_ldexp(acc[h], ref[h] - sh);
-        if (ci) v = fma(P.beta, ci[cidx(h)], v);
-        P.C[off + cidx(h)] = v;
-      }
-  }
+  emu_store(P, b, L, acc);
 }
 
-__device__ __forceinline__ void emu_tile_blocks(const EmuParams &P, const WarpTask &w) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int r0 = w.mt * 16 + g, r1 = r0 + 8;
-  const bool v0 = r0 < w.m, v1 = r1 < w.m;
-  const int colB = w.ng * 8 + g;
-  const bool vB = colB < w.n;
-  const int cc0 = w.ng * 8 + 2 * t, cc1 = cc0 + 1;
-  const bool vc0 = cc0 < w.n, vc1 = cc1 < w.n;
-  const int i = P.c_row[w.c], j = P.c_col[w.c];
-  // common scale of the four elements: largest exponent of the whole op(A) row plus
-  // that of the whole op(B) column, never below any product's ea + eb
-  int ref[4];
-  {
-    const int E0 = v0 ? P.row_exp[P.a_rowstart[i] + r0] : kExpNone;
-    const int E1 = v1 ? P.row_exp[P.a_rowstart[i] + r1] : kExpNone;
-    const int F0 = vc0 ? P.col_exp[P.b_colstart[j] + cc0] : kExpNone;
-    const int F1 = vc1 ? P.col_exp[P.b_colstart[j] + cc1] : kExpNone;
-    ref[0] = E0 + F0;
-    ref[1] = E0 + F1;
-    ref[2] = E1 + F0;
-    ref[3] = E1 + F1;
-  }
+// Block-scaled tile (never swapped): each product has its own scale 2^(ea + eb) per
+// element, so its level sums are folded after every 32 inner elements of that product
+// and shifted (with rounding) to the element's common scale.
+__device__ __forceinline__ void emu_tile_bs(const EmuParams &P, const EmuBlk &b, int mt, int ng,
+                                            const int4 &ent0) {
+  const int lane = threadIdx.x & 31, t = lane & 3;
+  const TileLane L = tile_lane(P, b, mt, ng);
   long long acc[4] = {0, 0, 0, 0};
-  for (int kc = 0; kc < P.Dk; ++kc) {
-    const int64_t rr = (int64_t)w.c * P.Dk + kc;
-    const int len = P.run_len[rr];
-    if (len == 0) continue;
-    const int e0 = P.run_start[rr];
-    const int k = P.kval[kc], kp = (k + 15) & ~15, nch = kp >> 4;
-    const int64_t pa = (int64_t)w.m * kp, pb = (int64_t)w.n * kp;
-    for (int e = e0; e < e0 + len; ++e) {
-      const int ab = P.s_ab[e], bb = P.s_bb[e];
-      const __nv_bfloat16 *Ad = P.a_dig + P.a_doff[ab];
-      const __nv_bfloat16 *Bd = P.b_dig + P.b_doff[bb];
-      const int64_t aeo = P.a_eoff[ab], beo = P.b_eoff[bb];
-      const int ea0 = v0 ? P.a_exp[aeo + r0] : kExpNone, ea1 = v1 ? P.a_exp[aeo + r1] : kExpNone;
-      const int eb0 = vc0 ? P.b_exp[beo + cc0] : kExpNone, eb1 = vc1 ? P.b_exp[beo + cc1] : kExpNone;
+  const uint2 zero = make_uint2(0u, 0u);
+  for (int g0 = 0; g0 < b.ne; g0 += 32) {
+    const int4 ent = g0 == 0 ? ent0 : load_ent(P, b, g0 + lane);
+    const int cnt = min(32, b.ne - g0);
+    for (int j = 0; j < cnt; ++j) {
+      const unsigned ea = (unsigned)__shfl_sync(kFull, ent.x, j);
+      const unsigned eb = (unsigned)__shfl_sync(kFull, ent.y, j);
+      const int nch = __shfl_sync(kFull, ent.z, j);
+      const int e = __shfl_sync(kFull, ent.w, j);
+      const __nv_bfloat16 *Ad = P.a_dig + 16 * (size_t)ea;
+      const __nv_bfloat16 *Bd = P.b_dig + 16 * (size_t)eb;
+      const int kp = nch * 16, pa = b.m * kp, pb = b.n * kp;
+      const int oa0 = L.r0 * kp + 4 * t, oa1 = L.r1 * kp + 4 * t, ob = L.colB * kp + 4 * t;
+      const int64_t aeo = P.a_eoff[P.s_ab[e]], beo = P.b_eoff[P.s_bb[e]];
+      const bool vc0 = L.valid[0] || L.valid[2], vc1 = L.valid[1] || L.valid[3];
+      const int ea0 = L.v0 ? P.a_exp[aeo + L.r0] : kExpNone, ea1 = L.v1 ? P.a_exp[aeo + L.r1] : kExpNone;
+      const int eb0 = vc0 ? P.b_exp[beo + L.cc0] : kExpNone, eb1 = vc1 ? P.b_exp[beo + L.cc1] : kExpNone;
+      const int eas[4] = {ea0 + eb0, ea0 + eb1, ea1 + eb0, ea1 + eb1};
       for (int cs = 0; cs < nch; cs += kSegChunks) {
-        float accw[kSlices][4];
+        float lv[kSlices][4];
 #pragma unroll
         for (int s = 0; s < kSlices; ++s)
 #pragma unroll
-          for (int h = 0; h < 4; ++h) accw[s][h] = 0.f;
+          for (int h = 0; h < 4; ++h) lv[s][h] = 0.f;
         const int ce = min(nch, cs + kSegChunks);
         for (int ch = cs; ch < ce; ++ch) {
-          uint32_t af[kSlices][4];
+          const int cofs = ch * 16;
+          uint2 bf[kSlices];
+#pragma unroll
+          for (int tt = 0; tt < kSlices; ++tt) bf[tt] = L.vB ? ld8(Bd + (tt * pb + ob + cofs)) : zero;
 #pragma unroll
           for (int s = 0; s < kSlices; ++s) {
-            const uint2 x0 = v0 ? ld8(Ad + s * pa + (int64_t)r0 * kp + ch * 16 + 4 * t) : make_uint2(0, 0);
-            const uint2 x1 = v1 ? ld8(Ad + s * pa + (int64_t)r1 * kp + ch * 16 + 4 * t) : make_uint2(0, 0);
-            af[s][0] = x0.x;
-            af[s][2] = x0.y;
-            af[s][1] = x1.x;
-            af[s][3] = x1.y;
-          }
+            const uint2 x0 = L.v0 ? ld8(Ad + (s * pa + oa0 + cofs)) : zero;
+            const uint2 x1 = L.v1 ? ld8(Ad + (s * pa + oa1 + cofs)) : zero;
+            const uint32_t af[4] = {x0.x, x1.x, x0.y, x1.y};
 #pragma unroll
-          for (int tt = 0; tt < kSlices; ++tt) {
-            const uint2 bf = vB ? ld8(Bd + tt * pb + (int64_t)colB * kp + ch * 16 + 4 * t) : make_uint2(0, 0);
-#pragma unroll
-            for (int s = 0; s + tt < kSlices; ++s) mma_bf16(accw[s + tt], af[s], bf.x, bf.y);
+            for (int tt = 0; s + tt < kSlices; ++tt) mma_bf16(lv[s + tt], af, bf[tt].x, bf[tt].y);
           }
         }
-        // fold the exact level sums into the int64 accumulators
-        const int eas[4] = {ea0 + eb0, ea0 + eb1, ea1 + eb0, ea1 + eb1};
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          long long I = 0;
-#pragma unroll
-          for (int s = 0; s < kSlices; ++s)
-            I += (long long)f32_exact_int(accw[s][h]) << (kBeta * (kSlices - 1 - s));
-          acc[h] += round_shift(I, ref[h] - eas[h] + P.guard);
-        }
+        for (int h = 0; h < 4; ++h)
+          if (L.valid[h]) acc[h] += round_shift(fold_levels(lv, h), L.ref[h] - eas[h] + b.guard);
       }
     }
   }
-  const int64_t off = P.c_off[w.c];
-  const int cin = P.c_cin[w.c];
-  const double *ci = (P.has_beta && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
-  const bool scale = !P.alpha_one;
-#pragma unroll
-  for (int h = 0; h < 4; ++h) {
-    const int r = h < 2 ? r0 : r1, c = (h & 1) ? cc1 : cc0;
-    if (r < w.m && c < w.n) {
-      double v = i64_ldexp(acc[h], ref[h] - (kSlices + 1) * kBeta + P.guard);
-      if (scale) v *= P.alpha;
-      if (ci) v = fma(P.beta, ci[r * w.n + c], v);
-      P.C[off + r * w.n + c] = v;
-    }
-  }
-}
-
-// A BF16 work item is one 16 x 8 warp tile of one C block:
-//   item = plan << 48 | C block << 16 | row tile << 8 | column tile.
-// Items are listed in C block (CSR) order, so consecutive warps work on neighbouring C
-// blocks of one block row and share its op(A) digits in L1/L2.
-__device__ __forceinline__ WarpTask task_of_item(const EmuParams &P, int64_t v) {
-  WarpTask w;
-  w.c = (int)((v >> 16) & 0xffffffffll);
-  w.mt = (int)((v >> 8) & 0xff);
-  w.ng = (int)(v & 0xff);
-  const int cls = P.c_cls[w.c];
-  w.m = P.cls_m[cls];
-  w.n = P.cls_n[cls];
-  w.sw = P.cls_swap ? P.cls_swap[cls] : 0;
-  w.ntn = min(P.tiles_n, (((w.sw ? w.m : w.n) + 7) >> 3) - P.tiles_n * w.ng);
-  return w;
+  emu_store(P, b, L, acc);
 }
 
 template <int ROWS>
-__device__ __forceinline__ void emu_tile(const EmuParams &P, const WarpTask &w) {
-  if (ROWS)
-    emu_tile_rows(P, w);
-  else
-    emu_tile_blocks(P, w);
+__device__ __forceinline__ void emu_block(const EmuParams &P, const EmuBlk &b) {
+  const int lane = threadIdx.x & 31;
+  const int4 ent0 = load_ent(P, b, lane);
+  const int RM = b.sw ? b.n : b.m, RN = b.sw ? b.m : b.n;
+  const int MT = (RM + 15) >> 4, NT = (RN + 7) >> 3;
+  for (int mt = 0; mt < MT; ++mt)
+    for (int ng = 0; ng < NT; ++ng) {
+      if (ROWS)
+        emu_tile_rs(P, b, mt, ng, ent0);
+      else
+        emu_tile_bs(P, b, mt, ng, ent0);
+    }
 }
 
-// persistent: every warp takes the next item from one counter until the list is done
+// Persistent: warps take kChunk consecutive work items at a time from one counter, so
+// the blocks in flight stay within a narrow window of the C order (their op(A) digit
+// rows and op(B) digit columns stay in L2) and one atomic serves kChunk blocks.  An item
+// is plan << 32 | C block (the identity when `items` is null).  The next chunk's index
+// is requested when a chunk starts, and its descriptors (lane l holds word l % 8 of
+// block l / 8) are loaded after the chunk's first block, so both arrive off the critical
+// path.  No waits: a warp whose chunk starts past the end returns.
+constexpr int kChunk = 4;
+static_assert(kChunk * kDescWords == 32, "one descriptor word per lane");
+
 template <int ROWS, class GetP>
-__device__ __forceinline__ void emu_persist_loop(const int64_t *__restrict__ items, int64_t nitems,
-                                                 unsigned long long *counter, GetP get) {
+__device__ __forceinline__ void emu_persist(const int64_t *__restrict__ items, int64_t nitems,
+                                            unsigned long long *counter, GetP get) {
   const int lane = threadIdx.x & 31;
+  // lane 0 issues the atomic; the result is shuffled to the warp only when needed
+  auto request = [&]() -> unsigned long long {
+    return lane == 0 ? atomicAdd(counter, (unsigned long long)kChunk) : 0ull;
+  };
+  auto item = [&](int64_t i) -> int64_t { return i < nitems ? (items ? items[i] : i) : -1; };
+  // lane l: word l % 8 of the descriptor of item c0 + l / 8
+  auto words = [&](int64_t c0) -> int {
+    const int64_t v = item(c0 + lane / kDescWords);
+    return v >= 0 ? get(v >> 32).desc[(v & 0xffffffffll) * kDescWords + lane % kDescWords] : 0;
+  };
+  int64_t c0 = (int64_t)__shfl_sync(kFull, request(), 0);
+  if (c0 >= nitems) return;
+  int dw = words(c0);
   for (;;) {
-    unsigned long long it = 0;
-    if (lane == 0) it = atomicAdd(counter, 1ull);
-    it = __shfl_sync(0xffffffffu, it, 0);
-    if (it >= (unsigned long long)nitems) return;
-    const int64_t v = items[it];
-    const EmuParams &P = get(v >> 48);
-    emu_tile<ROWS>(P, task_of_item(P, v));
+    const unsigned long long req = request();  // the next chunk, in flight during block 0
+    int64_t cn = 0;
+    int dwn = 0;
+    for (int q = 0; q < kChunk && c0 + q < nitems; ++q) {
+      const int64_t v = item(c0 + q);
+      const int w = __shfl_sync(kFull, dw, q * kDescWords + (lane & (kDescWords - 1)));
+      emu_block<ROWS>(get(v >> 32), emu_blk(w));
+      if (q == 0) {
+        cn = (int64_t)__shfl_sync(kFull, req, 0);
+        dwn = words(cn);
+      }
+    }
+    if (cn >= nitems) return;
+    c0 = cn;
+    dw = dwn;
   }
 }
 
 template <int ROWS>
 __global__ void __launch_bounds__(256, 2)
-    k_num_emu_bf16_persist1(EmuParams P, const int64_t *__restrict__ items, int64_t nitems,
-                            unsigned long long *counter) {
-  emu_persist_loop<ROWS>(items, nitems, counter, [&](int64_t) -> const EmuParams & { return P; });
+    k_num_emu_bf16_persist1(EmuParams P, int64_t nitems, unsigned long long *counter) {
+  emu_persist<ROWS>(nullptr, nitems, counter, [&](int64_t) -> const EmuParams & { return P; });
 }
 
 template <int ROWS>
 __global__ void __launch_bounds__(256, 2)
     k_num_emu_bf16_persist(const EmuParams *__restrict__ plans, const int64_t *__restrict__ items,
                            int64_t nitems, unsigned long long *counter) {
-  emu_persist_loop<ROWS>(items, nitems, counter,
-                         [&](int64_t pl) -> const EmuParams & { return plans[pl]; });
-}
-
-// warp tiles of every C block (16 x 8 per tile; rows and columns exchanged for a
-// swapped class)
-__device__ __forceinline__ void tile_grid(int m, int n, int sw, int &MT, int &NT) {
-  MT = ((sw ? n : m) + 15) >> 4;
-  NT = ((sw ? m : n) + 7) >> 3;
-}
-
-__global__ void k_emu_tile_counts(int64_t nc, const int32_t *__restrict__ c_cls,
-                                  const int32_t *__restrict__ cls_m, const int32_t *__restrict__ cls_n,
-                                  const int32_t *__restrict__ cls_swap, int32_t *__restrict__ cnt) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
-  const int cls = c_cls[c];
-  int MT, NT;
-  tile_grid(cls_m[cls], cls_n[cls], cls_swap[cls], MT, NT);
-  cnt[c] = MT * NT;
-}
-
-__global__ void k_emu_tile_fill(int64_t nc, const int32_t *__restrict__ c_cls,
-                                const int32_t *__restrict__ cls_m, const int32_t *__restrict__ cls_n,
-                                const int32_t *__restrict__ cls_swap,
-                                const int64_t *__restrict__ start, int64_t base,
-                                int64_t *__restrict__ items) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
-  const int cls = c_cls[c];
-  int MT, NT;
-  tile_grid(cls_m[cls], cls_n[cls], cls_swap[cls], MT, NT);
-  int64_t q = start[c];
-  for (int mt = 0; mt < MT; ++mt)
-    for (int ng = 0; ng < NT; ++ng) items[q++] = base | (c << 16) | ((int64_t)mt << 8) | ng;
+  emu_persist<ROWS>(items, nitems, counter,
+                    [&](int64_t pl) -> const EmuParams & { return plans[pl]; });
 }
 
 __global__ void __launch_bounds__(256) k_num_tf32x3(EmuParams P, int64_t nwarps) {
@@ -840,32 +951,41 @@ void emu_index(bst_plan *p, EmuState &E, cudaStream_t s) {
   };
   side(p->A, p->ta, false, E.a_doff, E.a_toff, E.a_eoff, E.a_dsize, E.a_tsize, E.a_esize);
   side(p->B, p->tb, true, E.b_doff, E.b_toff, E.b_eoff, E.b_dsize, E.b_tsize, E.b_esize);
-  E.e_adoff = ar.alloc_n<int64_t>((size_t)p->T);
-  E.e_bdoff = ar.alloc_n<int64_t>((size_t)p->T);
-  if (p->T > 0) {
-    k_entry_doffs<<<nblk(p->T, 256), 256, 0, s>>>(p->T, p->s_ab, p->s_bb, E.a_doff, E.b_doff,
-                                                  E.e_adoff, E.e_bdoff);
-    BST_CHECK_LAUNCH();
+  // entries hold digit offsets in units of 16 elements as 32-bit values
+  BST_REQUIRE(E.a_dsize < (1ll << 36) && E.b_dsize < (1ll << 36), BST_ERR_UNSUPPORTED,
+              "emulated FP64 digit planes above 2^36 elements");
+  // C-major entries of the BF16 kernel
+  const int64_t nc = p->C->nblocks;
+  E.ebeg = ar.alloc_n<int64_t>((size_t)nc + 1);
+  E.ents = ar.alloc_n<int4>((size_t)std::max<int64_t>(p->T, 1));
+  {
+    int32_t *cnt = scratch.alloc_n<int32_t>((size_t)std::max<int64_t>(nc, 1));
+    if (nc > 0) {
+      k_emu_ent_count<<<nblk(nc, 256), 256, 0, s>>>(nc, p->Dk, p->run_len, cnt);
+      BST_CHECK_LAUNCH();
+    }
+    exscan_i32_i64(cnt, E.ebeg, nc, scratch, s);
+    if (nc > 0) {
+      k_emu_ents<<<nblk(nc, 256), 256, 0, s>>>(nc, p->Dk, p->run_start, p->run_len, p->kval,
+                                               p->s_ab, p->s_bb, E.a_doff, E.b_doff, E.ebeg,
+                                               E.ents);
+      BST_CHECK_LAUNCH();
+    }
   }
-  // warps per (m,n) class: one per 16-row x 16-column tile of each C block (3xTF32),
-  // one per 16-row x 8-column tile (BF16 slices)
+  // 3xTF32 warps per (m,n) class: one per 16-row x 16-column tile of each C block
   const int32_t ncls = p->Dm * p->Dn;
-  std::vector<int64_t> ws((size_t)ncls + 1, 0), wb((size_t)ncls + 1, 0);
+  std::vector<int64_t> ws((size_t)ncls + 1, 0);
   for (int32_t c = 0; c < ncls; ++c) {
     const int64_t cnt = (int64_t)p->h_class_ptr[c + 1] - p->h_class_ptr[c];
     const int m = p->m_vals.empty() ? 0 : p->m_vals[c / p->Dn];
     const int n = p->n_vals.empty() ? 0 : p->n_vals[c % p->Dn];
     const int64_t mt = (m + 15) / 16, nt = (n + 7) / 8;
     ws[c + 1] = ws[c] + cnt * mt * ((nt + 1) / 2);
-    wb[c + 1] = wb[c] + cnt * mt * nt;
   }
   E.ncls = ncls;
   E.nwarps = ws.back();
-  E.nwarps_b = wb.back();
   E.wstart = ar.alloc_n<int64_t>(ws.size());
-  E.wstart_b = ar.alloc_n<int64_t>(wb.size());
   BST_CUDA(cudaMemcpyAsync(E.wstart, ws.data(), 8 * ws.size(), cudaMemcpyHostToDevice, s));
-  BST_CUDA(cudaMemcpyAsync(E.wstart_b, wb.data(), 8 * wb.size(), cudaMemcpyHostToDevice, s));
   // global element starts of op(A) row blocks and op(B) column blocks
   auto starts = [&](const std::vector<int32_t> &sz, int64_t *&out, int64_t &total) {
     std::vector<int64_t> h(sz.size() + 1, 0);
@@ -877,21 +997,7 @@ void emu_index(bst_plan *p, EmuState &E, cudaStream_t s) {
   };
   starts(p->oa.h_rs, E.a_rowstart, E.nrows);
   starts(p->ob.h_cs, E.b_colstart, E.ncols);
-  // guard bits: the int64 accumulator of a C element holds up to K_tot * 2^(49 - G)
-  unsigned long long *mk = scratch.alloc_n<unsigned long long>(1);
-  BST_CUDA(cudaMemsetAsync(mk, 0, 8, s));
-  const int64_t nc = p->C->nblocks;
-  if (nc > 0) {
-    k_max_ktot<<<nblk(nc, 256), 256, 0, s>>>(nc, p->Dk, p->run_len, p->kval, mk);
-    BST_CHECK_LAUNCH();
-  }
-  unsigned long long hk = 0;
-  BST_CUDA(cudaMemcpyAsync(&hk, mk, 8, cudaMemcpyDeviceToHost, s));
   BST_CUDA(cudaStreamSynchronize(s));
-  int lg = 0;
-  while ((1ull << lg) <= hk) ++lg;
-  // per inner element |a'b'| <= 1, i.e. 2^((S+1) beta) units; keep K_tot * that < 2^62
-  E.guard = std::max(0, lg - (62 - (kSlices + 1) * kBeta));
   scratch.release_all();
   E.index_ready = true;
 }
@@ -916,7 +1022,6 @@ EmuParams emu_params(bst_plan *p, const EmuState &E, const NumArgs &a) {
   P.beta = a.beta;
   P.Dk = p->Dk;
   P.ncls = E.ncls;
-  P.guard = E.guard;
   P.wstart = E.wstart;
   P.tiles_n = 2;
   P.a_rowstart = E.a_rowstart;
@@ -938,8 +1043,8 @@ EmuParams emu_params(bst_plan *p, const EmuState &E, const NumArgs &a) {
   P.run_len = p->run_len;
   P.s_ab = p->s_ab;
   P.s_bb = p->s_bb;
-  P.e_adoff = E.e_adoff;
-  P.e_bdoff = E.e_bdoff;
+  P.desc = E.desc;
+  P.ents = E.ents;
   P.a_eoff = E.a_eoff;
   P.b_eoff = E.b_eoff;
   P.a_dig = E.a_dig;
@@ -972,9 +1077,6 @@ static void emu_alloc_digits(EmuState &E) {
 
 // slices and exponents of the current operand data (launches only)
 static void emu_prepare(bst_plan *p, EmuState &E, const NumArgs &a, cudaStream_t s) {
-  // padding must read as zero
-  BST_CUDA(cudaMemsetAsync(E.a_dig, 0, 2 * (size_t)std::max<int64_t>(E.a_dsize, 1), s));
-  BST_CUDA(cudaMemsetAsync(E.b_dig, 0, 2 * (size_t)std::max<int64_t>(E.b_dsize, 1), s));
   fill_i32(E.a_exp, kExpNone, E.a_esize, s);
   fill_i32(E.b_exp, kExpNone, E.b_esize, s);
   fill_i32(E.row_exp, kExpNone, E.nrows, s);
@@ -1003,10 +1105,8 @@ static EmuParams bf16_params(bst_plan *p, const EmuState &E, const NumArgs &a) {
   EmuParams P = emu_params(p, E, a);
   P.a_doff = E.a_doff;
   P.b_doff = E.b_doff;
-  P.wstart = E.wstart_b;
   P.tiles_n = 1;
   P.row_scale = p->ctx->tune_emu_row_scale;
-  P.cls_swap = E.cls_swap;
   return P;
 }
 
@@ -1024,33 +1124,38 @@ static int class_swap(const bst_ctx *ctx, int m, int n) {
   return swapped < plain ? 1 : 0;
 }
 
-// (Re)build the BF16 work list when the tuning state changed since the last build.
+// (Re)build the BF16 C block descriptors when the tuning state changed since the last
+// build (they carry each class's tile orientation).  Launches only, no synchronisation.
 static void emu_schedule(bst_plan *p, EmuState &E, cudaStream_t s) {
   const bst_ctx *ctx = p->ctx;
-  if (E.items && E.sched_version == ctx->tune_version && E.sched_rows == ctx->tune_emu_row_scale)
+  if (E.desc && E.sched_version == ctx->tune_version && E.sched_rows == ctx->tune_emu_row_scale)
     return;
   const int32_t ncls = p->Dm * p->Dn;
-  std::vector<int32_t> sw((size_t)ncls, 0);
-  int64_t total = 0;
+  std::vector<int32_t> sw((size_t)std::max(ncls, 1), 0);
   for (int32_t c = 0; c < ncls; ++c) {
     const int m = p->m_vals.empty() ? 0 : p->m_vals[c / p->Dn];
     const int n = p->n_vals.empty() ? 0 : p->n_vals[c % p->Dn];
     const int64_t cnt = (int64_t)p->h_class_ptr[c + 1] - p->h_class_ptr[c];
+    // the descriptor holds m and n in 12 bits each
+    BST_REQUIRE(cnt == 0 || (m < 4096 && n < 4096), BST_ERR_UNSUPPORTED,
+                "emulated FP64 takes C blocks of at most 4095 x 4095 elements");
     if (cnt > 0 && m > 0 && n > 0) sw[(size_t)c] = class_swap(ctx, m, n);
-    const int rm = sw[(size_t)c] ? n : m, rn = sw[(size_t)c] ? m : n;
-    total += cnt * (int64_t)((rm + 15) / 16) * ((rn + 7) / 8);
   }
-  if (!E.cls_swap) E.cls_swap = E.ar.alloc_n<int32_t>((size_t)ncls);
-  BST_CUDA(cudaMemcpyAsync(E.cls_swap, sw.data(), 4 * (size_t)ncls, cudaMemcpyHostToDevice, s));
-  if (total > E.items_cap) {
-    E.items = E.ar.alloc_n<int64_t>((size_t)total);
-    E.items_cap = total;
-  }
+  const int64_t nc = p->C->nblocks;
+  if (!E.cls_swap) E.cls_swap = E.ar.alloc_n<int32_t>(sw.size());
+  if (!E.desc) E.desc = E.ar.alloc_n<int32_t>((size_t)std::max<int64_t>(nc, 1) * kDescWords);
   if (!E.counter) E.counter = E.ar.alloc_n<unsigned long long>(1);
-  E.nwarps_b = total;
+  BST_CUDA(cudaMemcpyAsync(E.cls_swap, sw.data(), 4 * sw.size(), cudaMemcpyHostToDevice, s));
+  if (nc > 0) {
+    k_emu_desc<<<nblk(nc, 256), 256, 0, s>>>(nc, p->Dk, p->run_len, p->kval, E.ebeg, p->C->off,
+                                             p->C->row, p->C->col, p->c_cls, p->cls_m, p->cls_n,
+                                             E.cls_swap, p->c_cin, E.a_rowstart, E.b_colstart,
+                                             E.desc);
+    BST_CHECK_LAUNCH();
+  }
+  E.nitems_b = nc;
   E.sched_version = ctx->tune_version;
   E.sched_rows = ctx->tune_emu_row_scale;
-  emu_build_items(p, 0, E.items, s);  // synchronises: the host vector ends here
 }
 
 int64_t emu_item_count(bst_plan *p, cudaStream_t s) {
@@ -1058,26 +1163,15 @@ int64_t emu_item_count(bst_plan *p, cudaStream_t s) {
   EmuState &E = emu_state(p, s);
   emu_alloc_digits(E);
   emu_schedule(p, E, s);
-  return E.nwarps_b;
+  return E.nitems_b;
 }
 
-// the BF16 warp tiles of a plan in C block order; item = base | c << 16 | mt << 8 | nt
+// the BF16 work items of a plan in a batch: base | C block, in C block order
 void emu_build_items(bst_plan *p, int64_t base, int64_t *items, cudaStream_t s) {
   const int64_t nc = p->C->nblocks;
   if (nc == 0) return;
-  const int32_t *cls_swap = p->emu->cls_swap;
-  Arena scratch;
-  scratch.ctx = static_cast<Ctx *>(p->ctx);
-  scratch.stream = s;
-  int32_t *cnt = scratch.alloc_n<int32_t>((size_t)nc);
-  int64_t *start = scratch.alloc_n<int64_t>((size_t)nc + 1);
-  k_emu_tile_counts<<<nblk(nc, 256), 256, 0, s>>>(nc, p->c_cls, p->cls_m, p->cls_n, cls_swap, cnt);
+  k_emu_items<<<nblk(nc, 256), 256, 0, s>>>(nc, base, items);
   BST_CHECK_LAUNCH();
-  exscan_i32_i64(cnt, start, nc, scratch, s);
-  k_emu_tile_fill<<<nblk(nc, 256), 256, 0, s>>>(nc, p->c_cls, p->cls_m, p->cls_n, cls_swap, start,
-                                                base, items);
-  BST_CHECK_LAUNCH();
-  BST_CUDA(cudaStreamSynchronize(s));
 }
 
 void emu_prepare_and_fill(bst_plan *p, const NumArgs &a, void *out, cudaStream_t s) {
@@ -1087,18 +1181,26 @@ void emu_prepare_and_fill(bst_plan *p, const NumArgs &a, void *out, cudaStream_t
   std::memcpy(out, &P, sizeof(P));
 }
 
-int emu_persist_grid(int num_sms) {
+// resident CTAs of 256 threads per SM for the BF16 kernels (both scaling modes)
+static int emu_ctas_per_sm(bool batch) {
   int nb0 = 0, nb1 = 0;
-  BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, k_num_emu_bf16_persist<0>, 256, 0));
-  BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_num_emu_bf16_persist<1>, 256, 0));
-  return std::max(1, std::min(nb0, nb1)) * num_sms;
+  if (batch) {
+    BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, k_num_emu_bf16_persist<0>, 256, 0));
+    BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_num_emu_bf16_persist<1>, 256, 0));
+  } else {
+    BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, k_num_emu_bf16_persist1<0>, 256, 0));
+    BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_num_emu_bf16_persist1<1>, 256, 0));
+  }
+  return std::max(1, std::min(nb0, nb1));
 }
+
+int emu_persist_grid(int num_sms) { return emu_ctas_per_sm(true) * num_sms; }
 
 void launch_emu_persist(const void *params, const int64_t *items, int64_t nitems,
                         unsigned long long *counter, int grid, int row_scale, cudaStream_t s) {
   if (nitems == 0) return;
   BST_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
-  const int g = (int)std::min<int64_t>(grid, (nitems + 7) / 8);
+  const int g = (int)std::min<int64_t>(grid, (nitems + 8 * kChunk - 1) / (8 * kChunk));
   const EmuParams *P = static_cast<const EmuParams *>(params);
   if (row_scale)
     k_num_emu_bf16_persist<1><<<g, 256, 0, s>>>(P, items, nitems, counter);
@@ -1111,22 +1213,17 @@ void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
   if (p->C->nblocks == 0) return;
   EmuState &E = emu_state(p, s);
   emu_alloc_digits(E);
-  emu_schedule(p, E, s);  // warp tiles in C block order, rebuilt when tuning changed
+  emu_schedule(p, E, s);  // C block descriptors, rebuilt when tuning changed
   emu_prepare(p, E, a, s);
   const EmuParams P = bf16_params(p, E, a);
-  if (E.nwarps_b > 0) {
-    int nb = 0;
-    if (P.row_scale)
-      BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_emu_bf16_persist1<1>, 256, 0));
-    else
-      BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_emu_bf16_persist1<0>, 256, 0));
-    const int g = (int)std::min<int64_t>((int64_t)std::max(1, nb) * p->ctx->num_sms,
-                                         (E.nwarps_b + 7) / 8);
+  if (E.nitems_b > 0) {
+    const int g = (int)std::min<int64_t>((int64_t)emu_ctas_per_sm(false) * p->ctx->num_sms,
+                                         (E.nitems_b + 8 * kChunk - 1) / (8 * kChunk));
     BST_CUDA(cudaMemsetAsync(E.counter, 0, sizeof(unsigned long long), s));
     if (P.row_scale)
-      k_num_emu_bf16_persist1<1><<<g, 256, 0, s>>>(P, E.items, E.nwarps_b, E.counter);
+      k_num_emu_bf16_persist1<1><<<g, 256, 0, s>>>(P, E.nitems_b, E.counter);
     else
-      k_num_emu_bf16_persist1<0><<<g, 256, 0, s>>>(P, E.items, E.nwarps_b, E.counter);
+      k_num_emu_bf16_persist1<0><<<g, 256, 0, s>>>(P, E.nitems_b, E.counter);
     BST_CHECK_LAUNCH();
   }
 }

@@ -45,6 +45,8 @@ struct NumParams {
   const int32_t *run_start, *run_len;
   const int32_t *s_a, *s_b, *s_k;
   const int32_t *cls_m, *cls_n, *kval;
+  const int32_t *fdesc;  // staged kernel: C block descriptors (kF64Desc words each)
+  const int4 *fents;     // staged kernel: C-major entries
 };
 
 // first entry in [lo, hi) whose k block index is >= kb (entries ascend in k)
@@ -266,6 +268,300 @@ __global__ void __launch_bounds__(256, 2)
   persist_loop(items, nitems, counter, [&](int64_t pl) -> const NumParams & { return plans[pl]; });
 }
 
+// ---- staged persistent kernel ---------------------------------------------------------
+//
+// For plans whose products fit a shared-memory slot (m k + k n <= kStageMax doubles) and
+// whose C blocks have at most 32 * kMaxR elements.  A warp walks a stream of jobs (the
+// stack entries of its C blocks, C block by C block) and keeps two slots: while it
+// multiplies the op(A) and op(B) blocks of job j from one slot, the blocks of job j + 1
+// -- possibly the first product of its next C block -- arrive in the other through
+// cp.async, so the FP64 pipe never waits on an L2 round trip inside a product.  The
+// operands are then read from shared memory (broadcast for A, consecutive for B).
+// C blocks come from the cost-ordered item list in a fixed stride (item w, w + W, ...
+// for warp w of W); the descriptor of the next block is loaded one block ahead and its
+// first entries while the current block runs.
+
+constexpr int kMaxR = 17;         // accumulators per lane: C blocks up to 544 elements
+constexpr int kStageMax = 1536;   // doubles per slot (two slots per warp)
+constexpr int kStageWarps = 4;    // warps per CTA
+constexpr int kF64Desc = 8;       // descriptor words per C block
+
+// descriptor: 0 element offset of C block, 1 first entry, 2 entry count,
+// 3 m | n << 12, 4 C_in block (-1: none), 5 C block
+struct F64Blk {
+  int off, eb, ne, m, n, cin;
+};
+
+__device__ __forceinline__ F64Blk f64_blk(int dw) {
+  F64Blk b;
+  b.off = __shfl_sync(0xffffffffu, dw, 0);
+  b.eb = __shfl_sync(0xffffffffu, dw, 1);
+  b.ne = __shfl_sync(0xffffffffu, dw, 2);
+  const int mn = __shfl_sync(0xffffffffu, dw, 3);
+  b.cin = __shfl_sync(0xffffffffu, dw, 4);
+  b.m = mn & 0xfff;
+  b.n = (mn >> 12) & 0xfff;
+  return b;
+}
+
+__device__ __forceinline__ void cp_async8(double *smem, const double *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// one product's op(A) and op(B) blocks (stored layouts, na and nb doubles) into a slot
+__device__ __forceinline__ void stage_product(double *slot, const double *a, const double *b,
+                                              int na, int nb) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < na; i += 32) cp_async8(slot + i, a + i);
+  for (int i = lane; i < nb; i += 32) cp_async8(slot + na + i, b + i);
+}
+
+// acc[r] += op(A)(p_r, :) . op(B)(:, q_r) from a slot, o = lane + 32 r = p_r N + q_r
+template <int M, int N, int KC>
+__device__ __forceinline__ void slot_product(const NumParams &P, const double *__restrict__ As,
+                                             int kk, double (&acc)[kMaxR]) {
+  constexpr int MN = M * N, R = (MN + 31) / 32;
+  static_assert(R <= kMaxR, "C block too large for the staged kernel");
+  const int lane = threadIdx.x & 31;
+  const int k = KC ? KC : kk;
+  const double *__restrict__ Bs = As + M * k;
+  const int a_sp = P.ta ? 1 : k, a_sl = P.ta ? M : 1;
+  const int b_sl = P.tb ? 1 : N, b_sq = P.tb ? k : 1;
+#pragma unroll 1
+  for (int l = 0; l < k; ++l) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int o = lane + 32 * r;
+      if (r < R - 1 || o < MN)
+        acc[r] = fma(As[(o / N) * a_sp + l * a_sl], Bs[(o % N) * b_sq + l * b_sl], acc[r]);
+    }
+  }
+}
+
+// any (m, n) with m n <= 32 R: runtime sizes, R accumulators
+template <int R>
+__device__ __forceinline__ void slot_product_rt(const NumParams &P, const double *__restrict__ As,
+                                                int m, int n, int k, double (&acc)[kMaxR]) {
+  const int lane = threadIdx.x & 31, mn = m * n;
+  const double *__restrict__ Bs = As + m * k;
+  const int a_sp = P.ta ? 1 : k, a_sl = P.ta ? m : 1;
+  const int b_sl = P.tb ? 1 : n, b_sq = P.tb ? k : 1;
+#pragma unroll 1
+  for (int l = 0; l < k; ++l) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int o = lane + 32 * r;
+      if (o < mn) acc[r] = fma(As[(o / n) * a_sp + l * a_sl], Bs[(o % n) * b_sq + l * b_sl], acc[r]);
+    }
+  }
+}
+
+template <int M, int N>
+__device__ __forceinline__ void slot_product_k(const NumParams &P, const double *As, int k,
+                                               double (&acc)[kMaxR]) {
+  switch (k) {
+    case 5: slot_product<M, N, 5>(P, As, k, acc); break;
+    case 13: slot_product<M, N, 13>(P, As, k, acc); break;
+    case 23: slot_product<M, N, 23>(P, As, k, acc); break;
+    default: slot_product<M, N, 0>(P, As, k, acc); break;
+  }
+}
+
+__device__ __forceinline__ void slot_dispatch(const NumParams &P, const double *As, int m, int n,
+                                              int k, double (&acc)[kMaxR]) {
+#define BST_MN(MM, NN) \
+  if (m == MM && n == NN) { slot_product_k<MM, NN>(P, As, k, acc); return; }
+  BST_MN(5, 5)
+  BST_MN(5, 13)
+  BST_MN(5, 23)
+  BST_MN(13, 5)
+  BST_MN(13, 13)
+  BST_MN(13, 23)
+  BST_MN(23, 5)
+  BST_MN(23, 13)
+  BST_MN(23, 23)
+#undef BST_MN
+  switch ((m * n + 31) >> 5) {
+#define BST_R(RR) case RR: slot_product_rt<RR>(P, As, m, n, k, acc); return;
+    BST_R(1) BST_R(2) BST_R(3) BST_R(4) BST_R(5) BST_R(6) BST_R(7) BST_R(8) BST_R(9)
+    BST_R(10) BST_R(11) BST_R(12) BST_R(13) BST_R(14) BST_R(15) BST_R(16) BST_R(17)
+#undef BST_R
+    default: return;  // excluded on the host
+  }
+}
+
+// C = alpha * acc + beta * C_in for one C block (C_in unread when beta == 0)
+__device__ __forceinline__ void store_block(const NumParams &P, const F64Blk &b,
+                                            const double (&acc)[kMaxR]) {
+  const int lane = threadIdx.x & 31, mn = b.m * b.n;
+  const double *ci = (P.has_beta && b.cin >= 0) ? P.Cin + P.cin_off[b.cin] : nullptr;
+  double *C = P.C + b.off;
+  if (!P.alpha_one || ci) {
+#pragma unroll
+    for (int r = 0; r < kMaxR; ++r) {
+      const int o = lane + 32 * r;
+      if (o < mn) {
+        double v = P.alpha * acc[r];
+        if (ci) v = fma(P.beta, ci[o], v);
+        C[o] = v;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < kMaxR; ++r)
+      if (lane + 32 * r < mn) C[lane + 32 * r] = acc[r];
+  }
+}
+
+template <class GetP>
+__device__ __forceinline__ void staged_loop(const int64_t *__restrict__ items, int64_t nitems,
+                                            int slot_elems, GetP get) {
+  extern __shared__ double smem_stage[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double *slots = smem_stage + (size_t)wid * 2 * slot_elems;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
+  auto item = [&](int64_t i) -> int64_t { return i < nitems ? items[i] : -1; };
+  auto word = [&](int64_t v) -> int {
+    return (v >= 0 && lane < kF64Desc)
+               ? get(v >> 32).fdesc[(v & 0xffffffffll) * kF64Desc + lane]
+               : 0;
+  };
+  // entries g0 .. g0 + 31 of a block, one per lane
+  auto group = [&](int64_t v, const F64Blk &b, int g0) -> int4 {
+    return (v >= 0 && g0 + lane < b.ne) ? get(v >> 32).fents[(int64_t)b.eb + g0 + lane]
+                                        : make_int4(0, 0, 0, 0);
+  };
+  int64_t v = item(it), vn = item(it + nw);
+  if (v < 0) return;
+  int dw = word(v), dwn = word(vn);
+  F64Blk b = f64_blk(dw);
+  int4 ent = group(v, b, 0);
+  int slot = 0;
+  bool staged = false;  // slot holds the first product of the current block
+  for (;;) {
+    const NumParams &P = get(v >> 32);
+    const F64Blk bn = f64_blk(dwn);
+    const int4 entn = group(vn, bn, 0);
+    const int64_t vnn = item(it + 2 * nw);
+    const int dwnn = word(vnn);
+    if (!staged && b.ne > 0) {
+      const int k = __shfl_sync(0xffffffffu, ent.z, 0);
+      stage_product(slots + slot * slot_elems, P.A + __shfl_sync(0xffffffffu, ent.x, 0),
+                    P.B + __shfl_sync(0xffffffffu, ent.y, 0), b.m * k, k * b.n);
+      cp_commit();
+    }
+    double acc[kMaxR];
+#pragma unroll
+    for (int r = 0; r < kMaxR; ++r) acc[r] = 0.0;
+    int g0 = 0;
+    for (int e = 0; e < b.ne; ++e) {
+      if (e - g0 == 32) {
+        g0 += 32;
+        ent = group(v, b, g0);
+      }
+      const int k = __shfl_sync(0xffffffffu, ent.z, e - g0);
+      // the next job into the other slot: this block's next product, else the first
+      // product of the next block
+      double *nxt = slots + (slot ^ 1) * slot_elems;
+      if (e + 1 < b.ne) {
+        int j = e + 1 - g0;
+        int4 src = ent;
+        if (j == 32) {
+          src = group(v, b, g0 + 32);
+          j = 0;
+        }
+        const int k1 = __shfl_sync(0xffffffffu, src.z, j);
+        stage_product(nxt, P.A + __shfl_sync(0xffffffffu, src.x, j),
+                      P.B + __shfl_sync(0xffffffffu, src.y, j), b.m * k1, k1 * b.n);
+      } else if (vn >= 0 && bn.ne > 0) {
+        const NumParams &Pn = get(vn >> 32);
+        const int k1 = __shfl_sync(0xffffffffu, entn.z, 0);
+        stage_product(nxt, Pn.A + __shfl_sync(0xffffffffu, entn.x, 0),
+                      Pn.B + __shfl_sync(0xffffffffu, entn.y, 0), bn.m * k1, k1 * bn.n);
+      }
+      cp_commit();
+      cp_wait_prev();
+      __syncwarp();
+      slot_dispatch(P, slots + slot * slot_elems, b.m, b.n, k, acc);
+      __syncwarp();
+      slot ^= 1;
+    }
+    staged = b.ne > 0 && vn >= 0 && bn.ne > 0;
+    store_block(P, b, acc);
+    if (vn < 0) break;
+    it += nw;
+    v = vn;
+    vn = vnn;
+    dw = dwn;
+    dwn = dwnn;
+    b = bn;
+    ent = entn;
+  }
+  cp_wait_all();
+}
+
+__global__ void __launch_bounds__(32 * kStageWarps, 3)
+    k_num_fp64_staged1(NumParams P, const int64_t *__restrict__ items, int64_t nitems,
+                       int slot_elems) {
+  staged_loop(items, nitems, slot_elems, [&](int64_t) -> const NumParams & { return P; });
+}
+
+__global__ void __launch_bounds__(32 * kStageWarps, 3)
+    k_num_fp64_staged(const NumParams *__restrict__ plans, const int64_t *__restrict__ items,
+                      int64_t nitems, int slot_elems) {
+  staged_loop(items, nitems, slot_elems,
+              [&](int64_t pl) -> const NumParams & { return plans[pl]; });
+}
+
+// ---- schedule of the staged kernel (built with the plan) ----------------------------
+
+__global__ void k_f64_ent_count(int64_t nc, int32_t Dk, const int32_t *__restrict__ run_len,
+                                int32_t *__restrict__ cnt) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  int s = 0;
+  for (int kc = 0; kc < Dk; ++kc) s += run_len[c * Dk + kc];
+  cnt[c] = s;
+}
+
+// C-major entries {a_off, b_off, k, stack entry}: C block c owns [ebeg[c], ebeg[c+1])
+__global__ void k_f64_ents(int64_t nc, int32_t Dk, const int32_t *__restrict__ run_start,
+                           const int32_t *__restrict__ run_len, const int32_t *__restrict__ kval,
+                           const int32_t *__restrict__ s_a, const int32_t *__restrict__ s_b,
+                           const int64_t *__restrict__ ebeg, int4 *__restrict__ ents) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  int64_t q = ebeg[c];
+  for (int kc = 0; kc < Dk; ++kc) {
+    const int len = run_len[c * Dk + kc];
+    const int e0 = run_start[c * Dk + kc];
+    for (int e = e0; e < e0 + len; ++e) ents[q++] = make_int4(s_a[e], s_b[e], kval[kc], e);
+  }
+}
+
+__global__ void k_f64_desc(int64_t nc, const int64_t *__restrict__ ebeg,
+                           const int64_t *__restrict__ c_off, const int32_t *__restrict__ c_cls,
+                           const int32_t *__restrict__ cls_m, const int32_t *__restrict__ cls_n,
+                           const int32_t *__restrict__ c_cin, int32_t *__restrict__ desc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int cls = c_cls[c];
+  int32_t *d = desc + c * kF64Desc;
+  d[0] = (int32_t)c_off[c];
+  d[1] = (int32_t)ebeg[c];
+  d[2] = (int32_t)(ebeg[c + 1] - ebeg[c]);
+  d[3] = cls_m[cls] | (cls_n[cls] << 12);
+  d[4] = c_cin[c];
+  d[5] = (int32_t)c;
+  d[6] = 0;
+  d[7] = 0;
+}
+
 __global__ void k_plan_items(int64_t nc, int64_t base, int64_t *__restrict__ item) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c < nc) item[c] = base | c;
@@ -342,6 +638,8 @@ NumParams make_params(bst_plan *p, const NumArgs &a, int split) {
   P.cls_m = p->cls_m;
   P.cls_n = p->cls_n;
   P.kval = p->kval;
+  P.fdesc = p->fdesc;
+  P.fents = p->fents;
   return P;
 }
 
@@ -376,6 +674,84 @@ void sort_items(const int64_t *items, const int32_t *keys, int64_t n, int64_t *o
   int32_t *kp = scratch.alloc_n<int32_t>(65);
   stable_partition(keys, n, 64, perm, kp, scratch, s);
   k_gather_items<<<nblk(n, 256), 256, 0, s>>>(items, perm, n, out);
+  BST_CHECK_LAUNCH();
+}
+
+// Entries, descriptors and slot size of the staged kernel; the plan keeps
+// stage_elems = 0 (and runs the direct-load kernel) when a product does not fit a slot,
+// a C block has more than 32 * kMaxR elements or a block size does not fit 12 bits.
+void build_f64_schedule(bst_plan *p, cudaStream_t s) {
+  p->stage_elems = 0;
+  const int64_t nc = p->C->nblocks;
+  if (nc == 0 || p->T == 0) return;
+  int64_t slot = 0;
+  for (int32_t b = 0; b < p->nb_all; ++b) {
+    if (p->h_bucket_ptr[b + 1] == p->h_bucket_ptr[b]) continue;
+    const int32_t kc = b % p->Dk, ncl = (b / p->Dk) % p->Dn, mc = b / (p->Dk * p->Dn);
+    const int64_t m = p->m_vals[mc], n = p->n_vals[ncl], k = p->k_vals[kc];
+    slot = std::max(slot, m * k + k * n);
+  }
+  for (int32_t c = 0; c < p->Dm * p->Dn; ++c) {
+    if (p->h_class_ptr[c + 1] == p->h_class_ptr[c]) continue;
+    const int64_t m = p->m_vals[c / p->Dn], n = p->n_vals[c % p->Dn];
+    if (m * n > 32 * kMaxR || m >= 4096 || n >= 4096) return;
+  }
+  if (slot > kStageMax) return;
+  Arena &ar = p->arena;
+  Arena scratch;
+  scratch.ctx = static_cast<Ctx *>(p->ctx);
+  scratch.stream = s;
+  int32_t *cnt = scratch.alloc_n<int32_t>((size_t)nc);
+  int64_t *ebeg = scratch.alloc_n<int64_t>((size_t)nc + 1);
+  p->fents = ar.alloc_n<int4>((size_t)p->T);
+  p->fdesc = ar.alloc_n<int32_t>((size_t)nc * kF64Desc);
+  k_f64_ent_count<<<nblk(nc, 256), 256, 0, s>>>(nc, p->Dk, p->run_len, cnt);
+  BST_CHECK_LAUNCH();
+  exscan_i32_i64(cnt, ebeg, nc, scratch, s);
+  k_f64_ents<<<nblk(nc, 256), 256, 0, s>>>(nc, p->Dk, p->run_start, p->run_len, p->kval, p->s_a,
+                                           p->s_b, ebeg, p->fents);
+  BST_CHECK_LAUNCH();
+  k_f64_desc<<<nblk(nc, 256), 256, 0, s>>>(nc, ebeg, p->C->off, p->c_cls, p->cls_m, p->cls_n,
+                                           p->c_cin, p->fdesc);
+  BST_CHECK_LAUNCH();
+  BST_CUDA(cudaStreamSynchronize(s));
+  scratch.release_all();
+  p->stage_elems = (int32_t)slot;
+}
+
+// resident CTAs per SM of the staged kernel for a slot size; raises the kernel's
+// dynamic shared-memory limit on first use
+static int staged_ctas_per_sm(bool batch, int slot_elems, size_t &smem) {
+  static bool attr_set[2] = {false, false};
+  const size_t max_smem = sizeof(double) * 2 * kStageMax * kStageWarps;
+  if (!attr_set[batch]) {
+    if (batch)
+      BST_CUDA(cudaFuncSetAttribute(k_num_fp64_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)max_smem));
+    else
+      BST_CUDA(cudaFuncSetAttribute(k_num_fp64_staged1,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
+    attr_set[batch] = true;
+  }
+  smem = sizeof(double) * 2 * (size_t)slot_elems * kStageWarps;
+  int nb = 0;
+  if (batch)
+    BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_fp64_staged,
+                                                           32 * kStageWarps, smem));
+  else
+    BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_fp64_staged1,
+                                                           32 * kStageWarps, smem));
+  return std::max(1, nb);
+}
+
+void launch_fp64_staged(const void *params, const int64_t *items, int64_t nitems,
+                        int slot_elems, int num_sms, cudaStream_t s) {
+  if (nitems == 0) return;
+  size_t smem = 0;
+  const int per = staged_ctas_per_sm(true, slot_elems, smem);
+  const int g = (int)std::min<int64_t>((int64_t)per * num_sms, (nitems + kStageWarps - 1) / kStageWarps);
+  k_num_fp64_staged<<<g, 32 * kStageWarps, smem, s>>>(static_cast<const NumParams *>(params),
+                                                       items, nitems, slot_elems);
   BST_CHECK_LAUNCH();
 }
 
@@ -417,6 +793,16 @@ int choose_split(const bst_plan *p, int num_sms) {
 void execute_fp64(bst_plan *p, const NumArgs &a, int split, cudaStream_t s) {
   const int64_t nc = p->C->nblocks;
   if (nc == 0) return;
+  if (split <= 1 && p->items && p->stage_elems > 0) {
+    size_t smem = 0;
+    const int per = staged_ctas_per_sm(false, p->stage_elems, smem);
+    const int g = (int)std::min<int64_t>((int64_t)per * p->ctx->num_sms,
+                                         (nc + kStageWarps - 1) / kStageWarps);
+    k_num_fp64_staged1<<<g, 32 * kStageWarps, smem, s>>>(make_params(p, a, 1), p->items, nc,
+                                                         p->stage_elems);
+    BST_CHECK_LAUNCH();
+    return;
+  }
   if (split <= 1 && p->items) {
     BST_CUDA(cudaMemsetAsync(p->items_counter, 0, sizeof(unsigned long long), s));
     const int64_t need = (nc + 7) / 8;

@@ -677,6 +677,7 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
   // entry, 8 bytes per norm (C_in read is added at execute time when beta != 0)
   st.bytes = 8.0 * ((double)hrefel[0] + (double)hrefel[1] + (double)nelemC) + 12.0 * (double)T +
              8.0 * (double)(A->nblocks + B->nblocks);
+  build_f64_schedule(p, s);
 }
 
 }  // namespace bst

@@ -102,3 +102,31 @@ def test_integer_data_exact():
     ref = oracle.multiply(p.A, p.B)
     got = run_multiply(p, precision=bst.BST_FP64_EMU_BF16, stacks=False)
     assert (got["data"] == ref["data"]).all()
+
+
+@pytest.mark.parametrize("case", ["transposed", "wide_range", "large_blocks", "tall_skinny"])
+def test_emulated_block_scaled(case):
+    """The block-scaled digit mode (exponents per block row / column instead of per whole
+    op row / column) meets the same bound."""
+    ctx = bst.context()
+    old = bst.bst_tune_get(ctx, bst.BST_TUNE_EMU_ROW_SCALE)
+    bst.bst_tune_set(ctx, bst.BST_TUNE_EMU_ROW_SCALE, 0)
+    try:
+        p = {"transposed": lambda: _mixed(11, ta="T", tb="T", alpha=-0.5, beta=2.0),
+             "wide_range": lambda: _mixed(12, scale_decades=8.0, dist="normal", cin=False),
+             "large_blocks": lambda: _mixed(13, nb=(9, 7, 8), occ=0.4, sizes=(1, 7, 31, 40, 170)),
+             "tall_skinny": lambda: tall_skinny(seed=14, nk=3000, nmn=48, window=10, p=0.3)}[case]()
+        check(p, bst.BST_FP64_EMU_BF16)
+    finally:
+        bst.bst_tune_set(ctx, bst.BST_TUNE_EMU_ROW_SCALE, old)
+
+
+def test_emulated_many_products_per_block():
+    """C blocks with far more than 32 products (the entry list is walked 32 at a time)."""
+    p = tall_skinny(seed=15, nk=4000, nmn=8, window=8, p=0.5)
+    ref = oracle.multiply(p.A, p.B, None, 1.0, 0.0, p.eps, p.transa, p.transb)
+    st = run_multiply(p, precision=bst.BST_FP64, stacks=True)
+    _, per_block = np.unique(st["c_off"], return_counts=True)
+    assert per_block.max() > 64
+    got = run_multiply(p, precision=bst.BST_FP64_EMU_BF16, stacks=False)
+    assert rel_fro(got["data"], ref["data"]) <= 1e-11
