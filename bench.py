@@ -34,10 +34,22 @@ WORKLOAD = ("banded 4000x4000 blocks, sizes {5:.4,13:.4,23:.2}, ~1% occupancy "
 # FP64 FMA peak of one GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM
 # x 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def _measured_bf16():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d.get("bf16_tflops") or 0.0) or None
+    except (OSError, ValueError, TypeError):
+        return None
+
+
+BF16_PEAK_TFLOPS = _measured_bf16()
 CPU_SAMPLE_ROWS = (1000, 3000)     # cpu_baseline: block rows of A in the sample
 REF_SAMPLE_ROWS = (1800, 2200)     # --impl reference: block rows per step
 # timed-step precision -> (library constant name, numeric kernel launched by execute)
-PRECISIONS = {"fp64": ("BST_FP64", "k_num_fp64_persist1"),
+PRECISIONS = {"fp64": ("BST_FP64", "k_num_fp64_staged1"),
               "emu": ("BST_FP64_EMU_BF16", "k_num_emu_bf16_persist1"),
               "tf32x3": ("BST_TF32X3", "k_num_tf32x3")}
 
@@ -182,6 +194,30 @@ def run_reference(args):
     return 0
 
 
+# measured BF16 mma.sync throughput of one GB300 (a throughput probe with 8 independent
+# chains per thread); the emulated kernel is built on mma.sync m16n8k16
+MMA_SYNC_BF16_TFLOPS = 604.0
+
+
+def emu_tensor_ops(plan, ctx):
+    """BF16 tensor flops the emulated kernel executes for a plan: per product 21 slice
+    products on 16 x 8 tiles covering the C block (rows over the block's rows, or over
+    its columns for a swapped class) and the inner size padded to 16."""
+    from paper_1910_13555_gb300 import bst
+    st = bst.bst_plan_get_stacks(plan.handle)
+    cnt = (st["bucket_ptr"][1:] - st["bucket_ptr"][:-1]).astype(float)
+    total = 0.0
+    for (m, n, k), c in zip(st["mnk"].tolist(), cnt):
+        sw = bst.bst_tune_get(ctx, bst.BST_TUNE_EMU_SWAP, m, n)
+        plain = -(-m // 16) * -(-n // 8)
+        swapped = -(-n // 16) * -(-m // 8)
+        if sw < 0:
+            sw = 1 if swapped < plain else 0
+        tiles = swapped if sw else plain
+        total += c * 21 * 2 * tiles * 16 * 8 * 16 * -(-k // 16)
+    return total
+
+
 def keep_plan_index(A, B, p, device):
     """C block index of the workload's product (rows, cols, offsets) from one plan."""
     from paper_1910_13555_gb300 import bst
@@ -320,7 +356,7 @@ def run_ours(args):
                       "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                       "frac": achieved / FP64_PEAK_TFLOPS,
                       "peak_note": "FP64 FMA pipe: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz",
-                      "traffic": load_traffic("k_num_fp64_persist1_banded") if args.nb == 4000 else None}
+                      "traffic": load_traffic(f"{kernel}_banded") if args.nb == 4000 else None}
                      if args.precision == "fp64" else None),
         "gpu_launches": launches,
         "clocks": clk,
@@ -367,6 +403,18 @@ def run_ours(args):
                                 "first_execute_ms": min(first),
                                 "note": "repeat executes of one plan; first_execute_ms adds "
                                         "the per-plan slicing index"}
+                if prec == bst.BST_FP64_EMU_BF16:
+                    ops = emu_tensor_ops(pl2, bst.context(local_rank))
+                    achieved_t = ops / (t * 1e-3) / 1e12
+                    extras[name]["tensor_roofline"] = {
+                        "bound": "tensor", "executed_bf16_tflop_per_execute": ops / 1e12,
+                        "achieved": achieved_t, "unit": "TFLOP/s",
+                        "peak_mma_sync_bf16": MMA_SYNC_BF16_TFLOPS,
+                        "frac": achieved_t / MMA_SYNC_BF16_TFLOPS,
+                        "peak_measured_bf16": BF16_PEAK_TFLOPS,
+                        "frac_of_measured": achieved_t / BF16_PEAK_TFLOPS if BF16_PEAK_TFLOPS else None,
+                        "note": "whole execute (slicing + products) against the BF16 mma.sync "
+                                "rate and the measured cuBLAS BF16 rate"}
                 if sample is not None:
                     extras[name]["rel_err_vs_oracle_sample"] = sample.error(pl2)
                 del pl, pl2
