@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the precision-variant legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (tiny, tall-skinny, batched, rank-3)")
     ap.add_argument("--nb", type=int, default=4000,
                     help="block rows/columns of the banded workload (smaller for profiler captures)")
     ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS),
@@ -363,7 +365,7 @@ def run_ours(args):
     }
 
     if not args.no_e2e:
-        line["e2e"] = e2e_leg(p, local_rank, min(args.steps, 3), stream, barrier, world, dev)
+        line["e2e"] = e2e_leg(p, local_rank, min(args.steps, 6), stream, barrier, world, dev)
 
     if not args.no_extras:
         from paper_1910_13555_gb300 import tune
@@ -423,6 +425,9 @@ def run_ours(args):
         if sample is not None:
             extras["error_sample"] = sample.describe()
         line["precision_variants"] = extras
+        line["fp64_stacks_13_23"] = single_stacks(local_rank, stream)
+        if rank == 0 and not args.no_configs:
+            line["other_configs"] = other_configs(local_rank, stream)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         rows = CPU_SAMPLE_ROWS if args.nb == 4000 else (args.nb // 4, 3 * args.nb // 4)
@@ -438,11 +443,201 @@ def run_ours(args):
     return 0
 
 
-def e2e_leg(p, local_rank, steps, stream, barrier, world, dev):
-    """The same metric through the public API from host buffers: each step creates
-    the matrices from host index arrays and pinned host data (H2D inside), plans,
-    executes and reads C_out back into pinned host memory (D2H inside)."""
+def single_stacks(local_rank, stream, nb=1000):
+    """Native FP64 numeric throughput and roofline fraction on single-stack versions of
+    the banded workload: every (m, n, k) in {13, 23}^3, same band and filter."""
+    import torch
+
+    from paper_1910_13555_gb300 import bst
+    from paper_1910_13555_gb300.workloads import banded
+    out = []
+    for m in (13, 23):
+        for n in (13, 23):
+            for k in (13, 23):
+                p = banded(seed=1102, nb=nb, block_mkn=(m, k, n))
+                mk = lambda x: bst.Matrix.from_host(x.row_sizes, x.col_sizes, x.rows, x.cols,
+                                                    x.data, device=local_rank)
+                A, B = mk(p.A), mk(p.B)
+                plan = bst.multiply_plan(A, B, None, p.eps, device=local_rank)
+                plan.alloc_result(local_rank)
+                plan.execute(1.0, 0.0, bst.BST_FP64, 1)
+                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                times = []
+                for _ in range(3):
+                    ev[0].record(stream)
+                    plan.execute(1.0, 0.0, bst.BST_FP64, 1)
+                    ev[1].record(stream)
+                    torch.cuda.synchronize()
+                    times.append(ev[0].elapsed_time(ev[1]))
+                t = statistics.median(times)
+                f = plan.stats()["flops"]
+                out.append({"mnk": [m, n, k], "flop": f, "ms": t,
+                            "gflops": f / (t * 1e-3) / 1e9,
+                            "frac": f / (t * 1e-3) / 1e12 / FP64_PEAK_TFLOPS})
+                del plan, A, B
+    tot_f = sum(o["flop"] for o in out)
+    tot_t = sum(o["ms"] for o in out)
+    return {"workload": f"banded {nb}x{nb} blocks, one (m, n, k) per run", "stacks": out,
+            "aggregate_frac": tot_f / (tot_t * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+
+
+def _median_ms(fn, stream, reps=3):
+    import torch
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        ev[0].record(stream)
+        fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        times.append(ev[0].elapsed_time(ev[1]))
+    return statistics.median(times)
+
+
+def _rel(got, ref):
     import numpy as np
+    return float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def _gather(data, offs, lens):
+    import numpy as np
+    import torch
+    idx = np.concatenate([np.arange(o, o + n) for o, n in zip(offs, lens)])
+    return data[torch.as_tensor(idx, device=data.device)].cpu().numpy()
+
+
+def _sample_err_matrix(p, plan, row_sizes, col_sizes, nsample=32, seed=0):
+    """Relative error of a product on sampled C blocks (the oracle computes exactly those)."""
+    import numpy as np
+
+    import oracle
+    rows, cols, offs = plan.result.index()
+    if len(rows) == 0:
+        return 0.0
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(len(rows), min(nsample, len(rows)), replace=False))
+    ref, _ = oracle.multiply_sample(p.A, p.B, p.C_in, p.alpha, p.beta, p.eps, rows[sel], cols[sel],
+                                    transa=p.transa, transb=p.transb, row_sizes=row_sizes,
+                                    col_sizes=col_sizes)
+    lens = row_sizes[rows[sel]].astype(np.int64) * col_sizes[cols[sel]]
+    return _rel(_gather(plan.result.data, offs[sel], lens), ref)
+
+
+def other_configs(local_rank, stream):
+    """The other workloads of the method, measured like the headline: numeric GFLOP/s
+    (CUDA events, median of 3), fraction of the FP64 unit-count peak, and error against
+    the CPU oracle on sampled output blocks."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1910_13555_gb300 import bst
+    from paper_1910_13555_gb300.workloads import batched, plain, rank3, tall_skinny
+
+    def mk(m):
+        return bst.Matrix.from_host(m.row_sizes, m.col_sizes, m.rows, m.cols, m.data,
+                                    device=local_rank)
+
+    def rate(f, ms):
+        return {"gflops": f / (ms * 1e-3) / 1e9, "ms": ms,
+                "frac": f / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+
+    out = {}
+    # 40 x 40 blocks of size 5, 10 % occupancy, no filter
+    p = plain()
+    A, B = mk(p.A), mk(p.B)
+    plan = bst.multiply_plan(A, B, None, 0.0, device=local_rank)
+    plan.alloc_result(local_rank)
+    ms = _median_ms(lambda: plan.execute(1.0, 0.0, bst.BST_FP64, 1), stream)
+    ref = oracle.multiply(p.A, p.B)
+    n = plan.result.info[3]
+    out["plain_40x40_size5"] = dict(rate(plan.stats()["flops"], ms),
+                                    rel_err_vs_oracle=_rel(plan.result.data[:n].cpu().numpy(),
+                                                           ref["data"]))
+    del plan, A, B
+    # tall-skinny C = A^T B (100000 x 400 blocks), split-K
+    p = tall_skinny()
+    A, B = mk(p.A), mk(p.B)
+    plan = bst.multiply_plan(A, B, None, p.eps, "T", "N", device=local_rank)
+    plan.alloc_result(local_rank)
+    f = plan.stats()["flops"]
+    ts = {}
+    for split in (1, 0):
+        ms = _median_ms(lambda: plan.execute(1.0, 0.0, bst.BST_FP64, split), stream)
+        ts[f"split_{split or 'auto'}"] = dict(rate(f, ms), split_k=plan.stats()["split_k"],
+                                              rel_err_vs_oracle_sample=_sample_err_matrix(
+                                                  p, plan, p.A.col_sizes, p.B.col_sizes))
+    ms = _median_ms(lambda: plan.execute(1.0, 0.0, bst.BST_FP64_EMU_BF16, 1), stream)
+    ts["emu_bf16"] = dict(rate(f, ms), rel_err_vs_oracle_sample=_sample_err_matrix(
+        p, plan, p.A.col_sizes, p.B.col_sizes))
+    out["tall_skinny_AtB"] = ts
+    del plan, A, B
+    # 64 independent products in one persistent launch, replayed from a CUDA graph
+    probs = batched()
+    mats, plans = [], []
+    for q in probs:
+        A, B = mk(q.A), mk(q.B)
+        pl = bst.multiply_plan(A, B, None, q.eps, device=local_rank)
+        pl.alloc_result(local_rank)
+        mats.append((A, B))
+        plans.append(pl)
+    f = sum(pl.stats()["flops"] for pl in plans)
+    batch = bst.bst_batch_create(bst.context(local_rank), [pl.handle for pl in plans])
+    ones, zeros = np.ones(len(plans)), np.zeros(len(plans))
+    bt = {}
+    for name, prec in (("fp64", bst.BST_FP64), ("emu_bf16", bst.BST_FP64_EMU_BF16)):
+        bst.bst_batch_execute(batch, ones, zeros, prec)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream()
+        with torch.cuda.graph(g, stream=cs):
+            bst.bst_batch_execute(batch, ones, zeros, prec, stream=cs)
+        ms = _median_ms(g.replay, stream)
+        errs = [_sample_err_matrix(probs[q], plans[q], probs[q].A.row_sizes,
+                                   probs[q].B.col_sizes, nsample=8, seed=q) for q in (0, 7, 31, 63)]
+        bt[name] = dict(rate(f, ms), rel_err_vs_oracle_sample=max(errs),
+                        launch="one persistent kernel per replay (CUDA graph)")
+        del g
+    bst.bst_batch_destroy(batch)
+    out["batched_64"] = dict(bt, flop=f)
+    del plans, mats
+    # rank-3 contraction R(mu,lam) = sum_{P,nu} T(P,mu,nu) U(P,nu,lam), forward + adjoint
+    w = rank3()
+    t1 = bst.Tensor.from_host(w.T1.block_sizes, w.T1.index, w.T1.data, device=local_rank)
+    t2 = bst.Tensor.from_host(w.T2.block_sizes, w.T2.index, w.T2.data, device=local_rank)
+    cplan = bst.contract(t1, t2, w.c1, w.c2, w.f1, w.f2, w.result_order, device=local_rank)
+    torch.cuda.synchronize()
+    f = cplan.stats()["flops"]
+    R = cplan.result
+    ms = _median_ms(lambda: cplan.execute(1.0, 0.0, bst.BST_FP64, 1), stream)
+    idx, offs = R.index()
+    rs = [w.T1.block_sizes[1], w.T2.block_sizes[2]]
+    rng = np.random.default_rng(1)
+    sel = np.sort(rng.choice(len(idx), min(32, len(idx)), replace=False))
+    ref, _ = oracle.contract_sample(w.T1, w.T2, w.c1, w.c2, w.f1, w.f2, w.result_order, None,
+                                    1.0, 0.0, 0.0, idx[sel], rs)
+    lens = rs[0][idx[sel, 0]].astype(np.int64) * rs[1][idx[sel, 1]]
+    fwd = dict(rate(f, ms), rel_err_vs_oracle_sample=_rel(_gather(R.data, offs[sel], lens), ref))
+    ne = R.info[2]
+    dR = R.data[:ne].clone()
+    dT = torch.empty_like(t1.data)
+    dU = torch.empty_like(t2.data)
+    ms_adj = _median_ms(lambda: bst.bst_plan_adjoint(cplan.handle, dR, dT, dU, None, 1.0, 0.0),
+                        stream)
+    out["rank3_contraction"] = {"forward": fwd,
+                                "adjoint": dict(rate(2.0 * f, ms_adj),
+                                                note="dT and dU, 2x the forward flop")}
+    return out
+
+
+def e2e_leg(p, local_rank, steps, stream, barrier, world, dev):
+    """The same metric through the public API from host buffers: each step copies A's
+    and B's data from pinned host memory (H2D), creates the matrices from the host index
+    arrays, plans, executes and reads all of C_out back into pinned host memory (D2H).
+    Steps alternate between two CUDA streams, so one step's D2H overlaps the next
+    step's work, as a caller streaming independent products would run them."""
     import torch
 
     from paper_1910_13555_gb300 import bst
@@ -450,33 +645,43 @@ def e2e_leg(p, local_rank, steps, stream, barrier, world, dev):
     ha = torch.from_numpy(p.A.data).pin_memory()
     hb = torch.from_numpy(p.B.data).pin_memory()
     ctx = bst.context(local_rank)
-    hc = None
-    flops = 0.0
+    streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+    hcs = [None, None]
+    alive = [None, None]  # objects of the step in flight on each stream
+    info = {"flops": 0.0, "n": 0}
 
-    def one():
-        nonlocal hc, flops
-        da = ha.to(dev, non_blocking=True)
-        db = hb.to(dev, non_blocking=True)
-        A = bst.Matrix(bst.bst_matrix_create(ctx, p.A.row_sizes, p.A.col_sizes, p.A.rows,
-                                             p.A.cols, da), da)
-        B = bst.Matrix(bst.bst_matrix_create(ctx, p.B.row_sizes, p.B.col_sizes, p.B.rows,
-                                             p.B.cols, db), db)
-        plan = bst.multiply(A, B, None, 1.0, 0.0, p.eps, device=local_rank)
-        n = plan.result.info[3]
-        if hc is None or hc.numel() < n:
-            hc = torch.empty(n, dtype=torch.float64).pin_memory()
-        hc[:n].copy_(plan.result.data[:n], non_blocking=True)
-        torch.cuda.synchronize()
-        flops = plan.stats()["flops"]
-        return n
+    def one(i):
+        slot = i % 2
+        s = streams[slot]
+        with torch.cuda.stream(s):
+            sh = s.cuda_stream
+            da = ha.to(dev, non_blocking=True)
+            db = hb.to(dev, non_blocking=True)
+            A = bst.Matrix(bst.bst_matrix_create(ctx, p.A.row_sizes, p.A.col_sizes, p.A.rows,
+                                                 p.A.cols, da, stream=sh), da)
+            B = bst.Matrix(bst.bst_matrix_create(ctx, p.B.row_sizes, p.B.col_sizes, p.B.rows,
+                                                 p.B.cols, db, stream=sh), db)
+            plan = bst.multiply(A, B, None, 1.0, 0.0, p.eps, device=local_rank, stream=sh)
+            n = plan.result.info[3]
+            if hcs[slot] is None or hcs[slot].numel() < n:
+                hcs[slot] = torch.empty(n, dtype=torch.float64).pin_memory()
+            hcs[slot][:n].copy_(plan.result.data[:n], non_blocking=True)
+        alive[slot] = (plan, A, B, da, db)
+        info["flops"] = plan.stats()["flops"]
+        info["n"] = n
 
-    n = one()
+    one(0)
+    one(1)
+    torch.cuda.synchronize()
     barrier()
     t = time.perf_counter()
-    for _ in range(steps):
-        n = one()
+    for i in range(steps):
+        one(i)
+    torch.cuda.synchronize()
     barrier()
     dt = (time.perf_counter() - t) / steps
+    alive[0] = alive[1] = None
+    flops = info["flops"]
     if world > 1:
         tt = torch.tensor([dt], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -487,7 +692,8 @@ def e2e_leg(p, local_rank, steps, stream, barrier, world, dev):
     h2d = (p.A.data.nbytes + p.B.data.nbytes + 8 * (p.A.nblocks + p.B.nblocks) +
            4 * (len(p.A.row_sizes) + len(p.A.col_sizes) + len(p.B.row_sizes) + len(p.B.col_sizes)))
     return {"value": flops / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(8 * n), "ms_per_step": dt * 1e3}
+            "d2h_bytes_per_step": int(8 * info["n"]), "ms_per_step": dt * 1e3,
+            "streams": 2}
 
 
 def main():

@@ -92,7 +92,9 @@ typedef void *(*bst_alloc_fn)(size_t bytes, void *user, void *stream);
 typedef void (*bst_free_fn)(void *ptr, void *user, void *stream);
 
 /* Create a context on CUDA device `device`.  alloc/free may both be NULL, in which
- * case the library uses cudaMallocAsync/cudaFreeAsync on the call's stream. */
+ * case the library allocates stream-ordered (cudaMallocFromPoolAsync / cudaFreeAsync on
+ * the call's stream) from a memory pool of its own that keeps freed memory for reuse
+ * until bst_context_destroy (which synchronises the device and destroys the pool). */
 bst_status bst_context_create(bst_ctx **out, int32_t device, bst_alloc_fn alloc,
                               bst_free_fn free_fn, void *user);
 bst_status bst_context_destroy(bst_ctx *ctx);

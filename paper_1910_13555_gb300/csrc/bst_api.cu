@@ -30,7 +30,8 @@ void *Arena::alloc(size_t bytes) {
     p = ctx->alloc(bytes, ctx->user, stream);
     if (!p) throw Error{BST_ERR_ALLOC, "allocator callback returned NULL"};
   } else {
-    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    cudaError_t e = ctx && ctx->pool ? cudaMallocFromPoolAsync(&p, bytes, ctx->pool, stream)
+                                     : cudaMallocAsync(&p, bytes, stream);
     if (e != cudaSuccess || !p) {
       (void)cudaGetLastError();
       throw Error{BST_ERR_ALLOC, std::string("cudaMallocAsync: ") + cudaGetErrorString(e)};
@@ -136,12 +137,32 @@ bst_status bst_context_create(bst_ctx **out, int32_t device, bst_alloc_fn alloc,
   c->num_sms = v;
   cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   c->max_smem_optin = (size_t)v;
+  if (!alloc) {
+    // the context's own stream-ordered pool, keeping freed memory for the next plan
+    // (the device's default pool returns it to the driver at every synchronisation)
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      c->pool = pool;
+    } else {
+      (void)cudaGetLastError();
+    }
+  }
   *out = c;
   API_END
 }
 
 bst_status bst_context_destroy(bst_ctx *ctx) {
   API_BEGIN
+  if (ctx && ctx->pool) {
+    BST_CUDA(cudaDeviceSynchronize());
+    cudaMemPoolDestroy(ctx->pool);
+  }
   delete static_cast<bst::Ctx *>(ctx);
   API_END
 }

@@ -77,6 +77,7 @@ struct bst_ctx {
   void *user = nullptr;
   int num_sms = 0;
   size_t max_smem_optin = 0;
+  cudaMemPool_t pool = nullptr;  // own allocations when no callbacks are given
   // kernel choices (bst_tune_set): emulated-FP64 digit scaling per whole op row /
   // column (1) or per block row / column (0); per (m, n) C block class, the tile
   // orientation of the emulated kernel (1 = MMA rows run over the C block's columns);

@@ -18,9 +18,8 @@
 // element share ref = E_row + F_col, in block-scaled mode each product's I is first
 // shifted (with rounding) from its own scale ea + eb to the element's ref = the largest
 // E_row + F_col; G guard bits keep K_tot * 2^56 below 2^62.  The int64 sum becomes FP64
-// through an integer-only, round-to-nearest-even conversion written from the IEEE 754
-// binary64 encoding, so no FP64 multiply-add is issued -- GB300's FP64 pipe runs at
-// 1/64 of the FP32 rate.
+// through the hardware conversion and an exponent-field add; no FP64 multiply-add is
+// issued -- GB300's FP64 pipe runs at 1/64 of the FP32 rate.
 //
 // 3xTF32 (BST_TF32X3), after Ootomo and Yokota (IJHPCA 2022): x = hi + lo with hi, lo
 // TF32; per block product hi*hi + hi*lo + lo*hi on the TF32 tensor cores with FP32
@@ -95,12 +94,6 @@ __device__ __forceinline__ int exp_of(double x) {
   return ex == 0 ? kExpNone : ex - 1022;
 }
 
-// position of inner index l inside its 16-chunk after the fragment permutation
-// (thread t of an m16n8k16 fragment holds k = 2t, 2t+1, 2t+8, 2t+9 -> positions 4t..4t+3)
-__device__ __forceinline__ int perm16(int l) {
-  const int j = l & 15;
-  return (l & ~15) + 4 * ((j & 7) >> 1) + 2 * (j >> 3) + (j & 1);
-}
 // same for m16n8k8 TF32 (thread t holds k = t, t+4 -> positions 2t, 2t+1)
 __device__ __forceinline__ int perm8(int l) {
   const int j = l & 7;
@@ -172,7 +165,8 @@ __device__ __forceinline__ double side_value(const SideBlock &B, int outer, int 
   return B.x[B.outer_major ? outer * B.Cc + inner : inner * B.Cc + outer];
 }
 
-// inner index (within its chunk) of digit position 4t + u
+// inner index (within its 16-chunk) stored at digit position 4t + u: thread t of an
+// m16n8k16 fragment holds k = 2t, 2t+1, 2t+8, 2t+9, stored next to each other
 __device__ __forceinline__ int chunk_inner(int t, int u) { return 2 * t + (u & 1) + 8 * (u >> 1); }
 
 // largest exponent of every op row (column) of a block and of the whole op row (column):
@@ -209,8 +203,6 @@ __global__ void k_emu_digits(SideArgs S) {
   const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (b >= S.nblocks) return;
   const SideBlock B = side_block(S, b);
-  const int kp = B.nch * 16;
-  const int64_t plane = (int64_t)B.nouter * kp;
   __nv_bfloat16 *d = S.dig + S.doff[b];
   const int total = B.nouter * B.nch;
   for (int q = lane >> 2; q < total; q += 8) {
@@ -240,10 +232,11 @@ __global__ void k_emu_digits(SideArgs S) {
         w[s][u >> 1] |= h << (16 * (u & 1));
       }
     }
-    __nv_bfloat16 *p = d + (int64_t)outer * kp + ch * 16 + 4 * t;
+    // chunk q = outer * nch + ch holds its six digit slices side by side
+    __nv_bfloat16 *p = d + (int64_t)q * (kSlices * 16) + 4 * t;
 #pragma unroll
     for (int s = 0; s < kSlices; ++s)
-      *reinterpret_cast<uint2 *>(p + s * plane) = make_uint2(w[s][0], w[s][1]);
+      *reinterpret_cast<uint2 *>(p + s * 16) = make_uint2(w[s][0], w[s][1]);
   }
 }
 
@@ -360,39 +353,21 @@ __global__ void k_emu_items(int64_t nc, int64_t base, int64_t *__restrict__ item
 
 // ---- integer -> FP64 ---------------------------------------------------------------
 
-// results outside the normal binary64 range (not met by the test workloads); kept out
-// of line so that the common path issues no FP64 instruction
-__device__ __noinline__ double i64_ldexp_slow(long long v, int e2) { return ldexp((double)v, e2); }
+// results outside the normal binary64 range (not met by the test workloads)
+__device__ __noinline__ double i64_ldexp_slow(double d, int e2) { return ldexp(d, e2); }
 
-// v * 2^e2 rounded to nearest-even binary64, from the IEEE 754 encoding (sign, biased
-// exponent, 52-bit fraction); integer operations only.  Results outside the normal
-// range take the library conversion.
+// v * 2^e2 rounded to nearest-even binary64: the hardware int64 -> FP64 conversion
+// (correctly rounded; it runs on the FP64 unit, which the emulated kernel otherwise
+// leaves idle) and the scale added to the exponent field, exact while the result stays
+// normal.  This keeps the epilogue's integer work, which competes with the MMA loop for
+// issue slots, to a handful of instructions per element.
 __device__ __forceinline__ double i64_ldexp(long long v, int e2) {
   if (v == 0) return 0.0;
-  const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
-  unsigned long long u = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-  const int nb = 64 - __clzll(u);  // significant bits
-  int e = e2;
-  if (nb > 53) {
-    const int r = nb - 53;
-    const unsigned long long rem = u & ((1ull << r) - 1ull), half = 1ull << (r - 1);
-    u >>= r;
-    e += r;
-    if (rem > half || (rem == half && (u & 1ull))) {
-      ++u;
-      if (u == (1ull << 53)) {
-        u >>= 1;
-        ++e;
-      }
-    }
-  } else {
-    u <<= (53 - nb);
-    e -= (53 - nb);
-  }
-  const int be = e + 52 + 1023;  // value = u 2^e with u in [2^52, 2^53)
-  if (be <= 0 || be >= 2047) return i64_ldexp_slow(v, e2);
-  return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) |
-                                          (u & ((1ull << 52) - 1ull))));
+  const double d = __ll2double_rn(v);
+  const long long bits = __double_as_longlong(d);
+  const int be = (int)((bits >> 52) & 0x7ff) + e2;
+  if (be <= 0 || be >= 2047) return i64_ldexp_slow(d, e2);
+  return __longlong_as_double(bits + ((long long)e2 << 52));
 }
 
 // FP32 -> FP64 from the binary32 / binary64 encodings (normal numbers and zero; FP32
@@ -406,17 +381,6 @@ __device__ __forceinline__ double f32_to_f64(float f) {
                                   ((unsigned long long)(ex - 127 + 1023) << 52) |
                                   ((unsigned long long)(b & 0x7fffffu) << 29);
   return __longlong_as_double((long long)bits);
-}
-
-// an integer-valued binary32 x with |x| < 2^24 as an int, read from its encoding
-// (value = significand * 2^(exponent - 150)); integer operations only
-__device__ __forceinline__ int f32_exact_int(float x) {
-  const unsigned b = __float_as_uint(x);
-  const int e = (int)((b >> 23) & 0xffu);
-  const unsigned m = (b & 0x7fffffu) | 0x800000u;
-  const int sh = 150 - e;
-  const int v = (e < 127) ? 0 : (int)(m >> sh);
-  return (b >> 31) ? -v : v;
 }
 
 __device__ __forceinline__ long long round_shift(long long v, int sh) {
@@ -639,7 +603,6 @@ __device__ __forceinline__ void emu_tile_rs(const EmuParams &P, const EmuBlk &b,
                                             const int4 &ent0) {
   const int lane = threadIdx.x & 31, t = lane & 3;
   const TileLane L = tile_lane(P, b, mt, ng);
-  const int RM = b.sw ? b.n : b.m, RN = b.sw ? b.m : b.n;
   const __nv_bfloat16 *Xa = b.sw ? P.b_dig : P.a_dig, *Xb = b.sw ? P.a_dig : P.b_dig;
   long long acc[4] = {0, 0, 0, 0};
   float lv[kSlices][4];
@@ -670,19 +633,21 @@ __device__ __forceinline__ void emu_tile_rs(const EmuParams &P, const EmuBlk &b,
       const int nch = __shfl_sync(kFull, ent.z, j);
       const __nv_bfloat16 *Ad = Xa + 16 * (size_t)(b.sw ? eb : ea);
       const __nv_bfloat16 *Bd = Xb + 16 * (size_t)(b.sw ? ea : eb);
-      // per-thread element offsets inside one digit plane of the row / column operand
-      const int kp = nch * 16, pa = RM * kp, pb = RN * kp;
-      const int oa0 = L.r0 * kp + 4 * t, oa1 = L.r1 * kp + 4 * t, ob = L.colB * kp + 4 * t;
+      // per-thread digit pointers of the row / column operand: chunk ch of outer row r
+      // starts at (r * nch + ch) * 96, slice s of it 16 elements further per s
+      const int rs = nch * (kSlices * 16);
+      const __nv_bfloat16 *a0 = Ad + (L.r0 * rs + 4 * t), *a1 = Ad + (L.r1 * rs + 4 * t);
+      const __nv_bfloat16 *b0 = Bd + (L.colB * rs + 4 * t);
       for (int ch = 0; ch < nch; ++ch) {
         if (used == kSegChunks) fold();
-        const int cofs = ch * 16;
+        const int cofs = ch * (kSlices * 16);
         uint2 bf[kSlices];
 #pragma unroll
-        for (int tt = 0; tt < kSlices; ++tt) bf[tt] = L.vB ? ld8(Bd + (tt * pb + ob + cofs)) : zero;
+        for (int tt = 0; tt < kSlices; ++tt) bf[tt] = L.vB ? ld8(b0 + cofs + tt * 16) : zero;
 #pragma unroll
         for (int s = 0; s < kSlices; ++s) {
-          const uint2 x0 = L.v0 ? ld8(Ad + (s * pa + oa0 + cofs)) : zero;
-          const uint2 x1 = L.v1 ? ld8(Ad + (s * pa + oa1 + cofs)) : zero;
+          const uint2 x0 = L.v0 ? ld8(a0 + cofs + s * 16) : zero;
+          const uint2 x1 = L.v1 ? ld8(a1 + cofs + s * 16) : zero;
           const uint32_t af[4] = {x0.x, x1.x, x0.y, x1.y};
 #pragma unroll
           for (int tt = 0; s + tt < kSlices; ++tt) mma_bf16(lv[s + tt], af, bf[tt].x, bf[tt].y);
@@ -714,8 +679,9 @@ __device__ __forceinline__ void emu_tile_bs(const EmuParams &P, const EmuBlk &b,
       const int e = __shfl_sync(kFull, ent.w, j);
       const __nv_bfloat16 *Ad = P.a_dig + 16 * (size_t)ea;
       const __nv_bfloat16 *Bd = P.b_dig + 16 * (size_t)eb;
-      const int kp = nch * 16, pa = b.m * kp, pb = b.n * kp;
-      const int oa0 = L.r0 * kp + 4 * t, oa1 = L.r1 * kp + 4 * t, ob = L.colB * kp + 4 * t;
+      const int rs = nch * (kSlices * 16);
+      const __nv_bfloat16 *a0 = Ad + (L.r0 * rs + 4 * t), *a1 = Ad + (L.r1 * rs + 4 * t);
+      const __nv_bfloat16 *b0 = Bd + (L.colB * rs + 4 * t);
       const int64_t aeo = P.a_eoff[P.s_ab[e]], beo = P.b_eoff[P.s_bb[e]];
       const bool vc0 = L.valid[0] || L.valid[2], vc1 = L.valid[1] || L.valid[3];
       const int ea0 = L.v0 ? P.a_exp[aeo + L.r0] : kExpNone, ea1 = L.v1 ? P.a_exp[aeo + L.r1] : kExpNone;
@@ -729,14 +695,14 @@ __device__ __forceinline__ void emu_tile_bs(const EmuParams &P, const EmuBlk &b,
           for (int h = 0; h < 4; ++h) lv[s][h] = 0.f;
         const int ce = min(nch, cs + kSegChunks);
         for (int ch = cs; ch < ce; ++ch) {
-          const int cofs = ch * 16;
+          const int cofs = ch * (kSlices * 16);
           uint2 bf[kSlices];
 #pragma unroll
-          for (int tt = 0; tt < kSlices; ++tt) bf[tt] = L.vB ? ld8(Bd + (tt * pb + ob + cofs)) : zero;
+          for (int tt = 0; tt < kSlices; ++tt) bf[tt] = L.vB ? ld8(b0 + cofs + tt * 16) : zero;
 #pragma unroll
           for (int s = 0; s < kSlices; ++s) {
-            const uint2 x0 = L.v0 ? ld8(Ad + (s * pa + oa0 + cofs)) : zero;
-            const uint2 x1 = L.v1 ? ld8(Ad + (s * pa + oa1 + cofs)) : zero;
+            const uint2 x0 = L.v0 ? ld8(a0 + cofs + s * 16) : zero;
+            const uint2 x1 = L.v1 ? ld8(a1 + cofs + s * 16) : zero;
             const uint32_t af[4] = {x0.x, x1.x, x0.y, x1.y};
 #pragma unroll
             for (int tt = 0; s + tt < kSlices; ++tt) mma_bf16(lv[s + tt], af, bf[tt].x, bf[tt].y);

@@ -261,18 +261,24 @@ def banded_pattern(rng, nb, occ=0.01, decay=200.0):
 
 
 def banded(seed=1002, nb=4000, occ=0.01, decay=200.0, value_decay=50.0, eps=1e-8,
-           sizes=SIZES_5_13_23) -> Problem:
-    """Banded block-sparse product with mixed 5/13/23 blocks and a norm filter."""
+           sizes=SIZES_5_13_23, block_mkn=None) -> Problem:
+    """Banded block-sparse product with mixed 5/13/23 blocks and a norm filter.
+    block_mkn = (m, k, n) gives every block row of A the size m, every inner block k and
+    every block column of B the size n instead (a single (m, n, k) stack)."""
     rng = np.random.default_rng(seed)
     sz = draw_sizes(rng, nb, sizes)
+    if block_mkn is None:
+        sm = sk = sn = sz
+    else:
+        sm, sk, sn = (np.full(nb, v, np.int32) for v in block_mkn)
 
     def vscale(r, c):
         return np.exp(-np.abs(r.astype(np.float64) - c) / value_decay)
 
     ra, ca, c = banded_pattern(rng, nb, occ, decay)
-    A = make_matrix(rng, sz, sz, ra, ca, dist="normal", scale=vscale)
+    A = make_matrix(rng, sm, sk, ra, ca, dist="normal", scale=vscale)
     rb, cb, _ = banded_pattern(rng, nb, occ, decay)
-    B = make_matrix(rng, sz, sz, rb, cb, dist="normal", scale=vscale)
+    B = make_matrix(rng, sk, sn, rb, cb, dist="normal", scale=vscale)
     n = eps_guard(A, B, eps)
     return Problem(A, B, None, 1.0, 0.0, eps, name=f"banded nb={nb}",
                    meta=dict(keep_scale=c, guard_rescaled=n))
