@@ -148,6 +148,10 @@ bst_status bst_context_create(bst_ctx **out, int32_t device, bst_alloc_fn alloc,
     if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
       uint64_t keep = UINT64_MAX;
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      // no reuse of memory freed on another stream behind an inserted wait: that would
+      // chain independent streams (a plan built on one stream behind another's copies)
+      int no = 0;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
       c->pool = pool;
     } else {
       (void)cudaGetLastError();
@@ -163,6 +167,7 @@ bst_status bst_context_destroy(bst_ctx *ctx) {
     BST_CUDA(cudaDeviceSynchronize());
     cudaMemPoolDestroy(ctx->pool);
   }
+  if (ctx && ctx->rb_host) cudaFreeHost(ctx->rb_host);
   delete static_cast<bst::Ctx *>(ctx);
   API_END
 }

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -78,6 +79,10 @@ struct bst_ctx {
   int num_sms = 0;
   size_t max_smem_optin = 0;
   cudaMemPool_t pool = nullptr;  // own allocations when no callbacks are given
+  // mapped pinned staging for ReadBack (grown on demand), held for one ReadBack at a time
+  void *rb_host = nullptr;
+  size_t rb_cap = 0;
+  std::mutex rb_mutex;
   // kernel choices (bst_tune_set): emulated-FP64 digit scaling per whole op row /
   // column (1) or per block row / column (0); per (m, n) C block class, the tile
   // orientation of the emulated kernel (1 = MMA rows run over the C block's columns);
@@ -151,6 +156,27 @@ void radix_sort_perm(const uint64_t *keys, int64_t n, int bits, int32_t *perm, A
 
 void iota_i32(int32_t *p, int64_t n, cudaStream_t s);
 void fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s);
+
+// Device -> host reads of a few values (sizes, bucket and class pointers) during plan
+// construction.  A kernel writes them into the context's mapped pinned buffer, so they
+// do not queue on the copy engine behind a large transfer of another stream; finish()
+// synchronises the stream and copies them to their host destinations.
+struct ReadBack {
+  bst_ctx *ctx;
+  cudaStream_t s;
+  struct Item {
+    void *dst;
+    size_t off, bytes;
+  };
+  std::vector<Item> items;
+  size_t used = 0;
+  bool locked = false;
+  ReadBack(bst_ctx *c, cudaStream_t st);
+  ~ReadBack();
+  void add(void *host_dst, const void *dev_src, size_t bytes);
+  void finish();  // values are in place afterwards
+  void done();    // finish() and release the staging buffer to other threads
+};
 void gather_i32(const int32_t *src, const int32_t *idx, int32_t *dst, int64_t n, cudaStream_t s);
 
 template <class T>

@@ -907,10 +907,11 @@ void emu_index(bst_plan *p, EmuState &E, cudaStream_t s) {
     exscan_i64(tsz, toff, n, scratch, s);
     exscan_i64(esz, eoff, n, scratch, s);
     int64_t tot[3];
-    BST_CUDA(cudaMemcpyAsync(&tot[0], doff + n, 8, cudaMemcpyDeviceToHost, s));
-    BST_CUDA(cudaMemcpyAsync(&tot[1], toff + n, 8, cudaMemcpyDeviceToHost, s));
-    BST_CUDA(cudaMemcpyAsync(&tot[2], eoff + n, 8, cudaMemcpyDeviceToHost, s));
-    BST_CUDA(cudaStreamSynchronize(s));
+    ReadBack rb(p->ctx, s);
+    rb.add(&tot[0], doff + n, 8);
+    rb.add(&tot[1], toff + n, 8);
+    rb.add(&tot[2], eoff + n, 8);
+    rb.done();
     dsize = tot[0];
     tsize = tot[1];
     esize = tot[2];

@@ -4,6 +4,8 @@
 // All of them are deterministic: the counting sort is stable because every warp
 // owns one contiguous segment of the input and emits it in order, with the ranks of
 // equal keys inside a 32-element batch taken from __match_any_sync.
+#include <cstring>
+
 #include "bst_internal.h"
 
 namespace bst {
@@ -208,6 +210,68 @@ void iota_i32(int32_t *p, int64_t n, cudaStream_t s) {
   k_iota<<<nblk(n, 256), 256, 0, s>>>(p, n);
   BST_CHECK_LAUNCH();
 }
+__global__ void k_copy_bytes(unsigned char *__restrict__ dst, const unsigned char *__restrict__ src,
+                             int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+ReadBack::ReadBack(bst_ctx *c, cudaStream_t st) : ctx(c), s(st) {
+  ctx->rb_mutex.lock();
+  locked = true;
+}
+
+ReadBack::~ReadBack() {
+  if (locked) {
+    // an exception left copies in flight: let them land before the buffer is reused
+    if (!items.empty()) (void)cudaStreamSynchronize(s);
+    ctx->rb_mutex.unlock();
+  }
+}
+
+void ReadBack::done() {
+  finish();
+  if (locked) {
+    locked = false;
+    ctx->rb_mutex.unlock();
+  }
+}
+
+void ReadBack::add(void *host_dst, const void *dev_src, size_t bytes) {
+  if (bytes == 0) return;
+  const size_t off = (used + 15) & ~(size_t)15;
+  if (off + bytes > ctx->rb_cap) {
+    // grow: earlier items of this ReadBack are still pending, so finish them first
+    if (!items.empty()) finish();
+    const size_t cap = std::max<size_t>(1 << 16, 2 * (bytes + 16));
+    BST_CUDA(cudaStreamSynchronize(s));
+    if (ctx->rb_host) BST_CUDA(cudaFreeHost(ctx->rb_host));
+    ctx->rb_host = nullptr;
+    ctx->rb_cap = 0;
+    BST_CUDA(cudaHostAlloc(&ctx->rb_host, cap, cudaHostAllocMapped));
+    ctx->rb_cap = cap;
+    return add(host_dst, dev_src, bytes);
+  }
+  void *dev_view = nullptr;
+  BST_CUDA(cudaHostGetDevicePointer(&dev_view, ctx->rb_host, 0));
+  const int64_t n = (int64_t)bytes;
+  const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);
+  k_copy_bytes<<<blocks, 256, 0, s>>>(static_cast<unsigned char *>(dev_view) + off,
+                                      static_cast<const unsigned char *>(dev_src), n);
+  BST_CHECK_LAUNCH();
+  items.push_back({host_dst, off, bytes});
+  used = off + bytes;
+}
+
+void ReadBack::finish() {
+  BST_CUDA(cudaStreamSynchronize(s));
+  for (const Item &it : items)
+    std::memcpy(it.dst, static_cast<const char *>(ctx->rb_host) + it.off, it.bytes);
+  items.clear();
+  used = 0;
+}
+
 void fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   k_fill<<<nblk(n, 256), 256, 0, s>>>(p, v, n);

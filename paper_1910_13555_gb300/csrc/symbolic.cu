@@ -494,10 +494,13 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
   exscan_i32_i64(t_rowcnt, t_rowptr, M, scratch, s);
   exscan_i32_i64(cand_rowcnt, cand_ptr, M, scratch, s);
   int64_t tot[3];
-  BST_CUDA(cudaMemcpyAsync(&tot[0], c_rowptr64 + M, 8, cudaMemcpyDeviceToHost, s));
-  BST_CUDA(cudaMemcpyAsync(&tot[1], t_rowptr + M, 8, cudaMemcpyDeviceToHost, s));
-  BST_CUDA(cudaMemcpyAsync(&tot[2], cand_ptr + M, 8, cudaMemcpyDeviceToHost, s));
-  BST_CUDA(cudaStreamSynchronize(s));
+  {
+    ReadBack rb(p->ctx, s);
+    rb.add(&tot[0], c_rowptr64 + M, 8);
+    rb.add(&tot[1], t_rowptr + M, 8);
+    rb.add(&tot[2], cand_ptr + M, 8);
+    rb.done();
+  }
   const int64_t nnzC = tot[0], T = tot[1], ncand = tot[2];
   BST_REQUIRE(nnzC < INT32_MAX && T < INT32_MAX, BST_ERR_OVERFLOW,
               "more than 2^31-1 C blocks or kept products");
@@ -557,8 +560,11 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
   }
   exscan_i64(csize, C->off, nnzC, scratch, s);
   int64_t nelemC = 0;
-  BST_CUDA(cudaMemcpyAsync(&nelemC, C->off + nnzC, 8, cudaMemcpyDeviceToHost, s));
-  BST_CUDA(cudaStreamSynchronize(s));
+  {
+    ReadBack rb(p->ctx, s);
+    rb.add(&nelemC, C->off + nnzC, 8);
+    rb.done();
+  }
   BST_REQUIRE(nelemC < INT32_MAX, BST_ERR_OVERFLOW, "C_out has more than 2^31-1 elements");
   C->nelem = nelemC;
 
@@ -568,8 +574,8 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
   p->class_ptr = ar.alloc_n<int32_t>((size_t)ncls + 1);
   stable_partition(p->c_cls, nnzC, ncls, p->task_c, p->class_ptr, scratch, s);
   p->h_class_ptr.assign((size_t)ncls + 1, 0);
-  BST_CUDA(cudaMemcpyAsync(p->h_class_ptr.data(), p->class_ptr, sizeof(int32_t) * (ncls + 1),
-                           cudaMemcpyDeviceToHost, s));
+  ReadBack rb_ptrs(p->ctx, s);  // class and bucket pointers, read together below
+  rb_ptrs.add(p->h_class_ptr.data(), p->class_ptr, sizeof(int32_t) * (ncls + 1));
 
   // bucketed stacks
   int32_t *key = scratch.alloc_n<int32_t>((size_t)T);
@@ -581,7 +587,7 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
   int32_t *bptr = scratch.alloc_n<int32_t>((size_t)p->nb_all + 1);
   stable_partition(key, T, p->nb_all, perm, bptr, scratch, s);
   std::vector<int32_t> hb((size_t)p->nb_all + 1);
-  BST_CUDA(cudaMemcpyAsync(hb.data(), bptr, sizeof(int32_t) * hb.size(), cudaMemcpyDeviceToHost, s));
+  rb_ptrs.add(hb.data(), bptr, sizeof(int32_t) * hb.size());
   p->s_a = ar.alloc_n<int32_t>((size_t)T);
   p->s_b = ar.alloc_n<int32_t>((size_t)T);
   p->s_c = ar.alloc_n<int32_t>((size_t)T);
@@ -649,8 +655,8 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
     BST_CHECK_LAUNCH();
   }
   unsigned long long hrefel[2];
-  BST_CUDA(cudaMemcpyAsync(hrefel, refel, 16, cudaMemcpyDeviceToHost, s));
-  BST_CUDA(cudaStreamSynchronize(s));
+  rb_ptrs.add(hrefel, refel, 16);
+  rb_ptrs.done();
   scratch.release_all();
 
   p->h_bucket_ptr.assign(hb.begin(), hb.end());
