@@ -296,8 +296,12 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    keep = None
     for _ in range(max(args.warmup, 0)):
         keep = step()
+    if keep is None:  # no warm-up asked for: the plan alone (symbolic phase) for the counts
+        keep = bst.multiply_plan(A, B, None, p.eps, device=local_rank)
+        keep.alloc_result(local_rank)
     barrier()
     flops = keep.stats()["flops"]
     stats = keep.stats()
@@ -534,7 +538,8 @@ def other_configs(local_rank, stream):
 
     import oracle
     from paper_1910_13555_gb300 import bst
-    from paper_1910_13555_gb300.workloads import batched, plain, rank3, tall_skinny
+    from paper_1910_13555_gb300.workloads import (batched, plain, rank3, rank4, rect_case2,
+                                                  tall_skinny)
 
     def mk(m):
         return bst.Matrix.from_host(m.row_sizes, m.col_sizes, m.rows, m.cols, m.data,
@@ -647,6 +652,39 @@ def other_configs(local_rank, stream):
     out["rank3_contraction"] = {"forward": fwd,
                                 "adjoint": dict(rate(2.0 * f, ms_adj),
                                                 note="dT and dU, 2x the forward flop")}
+    del cplan, t1, t2, R, dR, dT, dU
+    # rectangular case S_B << S_A, S_C: C = A B with a small B
+    p = rect_case2()
+    A, B = mk(p.A), mk(p.B)
+    plan = bst.multiply_plan(A, B, None, p.eps, device=local_rank)
+    plan.alloc_result(local_rank)
+    f = plan.stats()["flops"]
+    rc = {}
+    for name, prec in (("fp64", bst.BST_FP64), ("emu_bf16", bst.BST_FP64_EMU_BF16)):
+        ms = _median_ms(lambda: plan.execute(1.0, 0.0, prec, 1), stream)
+        rc[name] = dict(rate(f, ms), rel_err_vs_oracle_sample=_sample_err_matrix(
+            p, plan, p.A.row_sizes, p.B.col_sizes))
+    out["rect_case2_small_B"] = dict(rc, flop=f)
+    del plan, A, B
+    # rank-4 x rank-3 over two index pairs, permuted view, reordered result
+    w = rank4()
+    t1 = bst.Tensor.from_host(w.T1.block_sizes, w.T1.index, w.T1.data, device=local_rank)
+    t2 = bst.Tensor.from_host(w.T2.block_sizes, w.T2.index, w.T2.data, device=local_rank)
+    cplan = bst.contract(t1, t2, w.c1, w.c2, w.f1, w.f2, w.result_order, device=local_rank)
+    torch.cuda.synchronize()
+    f = cplan.stats()["flops"]
+    R = cplan.result
+    ms = _median_ms(lambda: cplan.execute(1.0, 0.0, bst.BST_FP64, 1), stream)
+    idx, offs = R.index()
+    rs = [w.T1.block_sizes[1], w.T2.block_sizes[2], w.T1.block_sizes[3]]
+    sel = np.sort(np.random.default_rng(2).choice(len(idx), min(32, len(idx)), replace=False))
+    ref, _ = oracle.contract_sample(w.T1, w.T2, w.c1, w.c2, w.f1, w.f2, w.result_order, None,
+                                    1.0, 0.0, 0.0, idx[sel], rs)
+    lens = np.ones(len(sel), np.int64)
+    for d in range(3):
+        lens *= rs[d][idx[sel, d]].astype(np.int64)
+    out["rank4_contraction"] = dict(rate(f, ms), rel_err_vs_oracle_sample=_rel(
+        _gather(R.data, offs[sel], lens), ref))
     return out
 
 

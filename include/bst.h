@@ -125,6 +125,20 @@ bst_status bst_matrix_get_index(const bst_matrix *m, int32_t *blk_row, int32_t *
 bst_status bst_matrix_bind_data(bst_matrix *m, double *data);
 bst_status bst_matrix_destroy(bst_matrix *m);
 
+/* Block post-filter (paper Sec. 2: chained products such as the sign-matrix iteration
+ * drop negligible blocks between multiplies).  bst_matrix_filter returns, in *out, a new
+ * matrix with X's block sizes holding the blocks of X whose Frobenius norm is >= eps
+ * (eps = 0 keeps every block), in canonical CSR order; its data is not bound.  It runs
+ * on `stream` and synchronises it twice (to learn the kept block and element counts).
+ * The caller binds nelem doubles (bst_matrix_info) to *out with bst_matrix_bind_data
+ * and calls bst_matrix_filter_copy(X, *out), which copies the kept blocks' elements
+ * (asynchronously on `stream`).  Errors: BST_ERR_INVALID_ARG (NULL, eps < 0),
+ * BST_ERR_STATE (data not bound), BST_ERR_SHAPE_MISMATCH (Y is not a filter result of
+ * X, or X's block count changed). */
+bst_status bst_matrix_filter(bst_ctx *ctx, const bst_matrix *X, double eps, void *stream,
+                             bst_matrix **out);
+bst_status bst_matrix_filter_copy(const bst_matrix *X, bst_matrix *Y, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Multiply (paper Sec. 2 local multiply; Sec. 3.1 for transa = 'T').
  *

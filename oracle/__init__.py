@@ -304,3 +304,46 @@ def contract_adjoint(T1, T2, c1, c2, f1, f2, result_order, R_in, alpha, beta, ep
     if st:
         raise OracleError(st, "contract_adjoint")
     return d1, d2, dri
+
+
+class _Blocks:
+    """A block-sparse matrix as plain arrays (the attribute names of the generators')."""
+
+    def __init__(self, row_sizes, col_sizes, rows, cols, data):
+        self.row_sizes = np.ascontiguousarray(row_sizes, np.int32)
+        self.col_sizes = np.ascontiguousarray(col_sizes, np.int32)
+        self.rows = np.ascontiguousarray(rows, np.int32)
+        self.cols = np.ascontiguousarray(cols, np.int32)
+        self.data = np.ascontiguousarray(data, np.float64)
+        self.nblocks = len(self.rows)
+
+
+def filter_blocks(m, eps):
+    """Post-filter (paper Sec. 2, products of a chain drop negligible blocks): the blocks
+    of m, in canonical order, whose Frobenius norm (the same norm as the product filter)
+    is >= eps; their data unchanged."""
+    norms = block_norms(m)
+    lens = (np.asarray(m.row_sizes, np.int64)[np.asarray(m.rows)] *
+            np.asarray(m.col_sizes, np.int64)[np.asarray(m.cols)])
+    starts = np.concatenate([[0], np.cumsum(lens)])
+    keep = norms >= eps
+    data = [np.asarray(m.data)[starts[b]:starts[b + 1]] for b in range(len(lens)) if keep[b]]
+    return _Blocks(m.row_sizes, m.col_sizes, np.asarray(m.rows)[keep], np.asarray(m.cols)[keep],
+                   np.concatenate(data) if data else np.zeros(0))
+
+
+def sign_iteration(X, iters, eps=0.0, eps_post=0.0):
+    """The matrix-sign Newton-Schulz iteration X <- (3 X - X^3) / 2 as a chain of filtered
+    block-sparse products: T = filter(X X), X <- filter(-1/2 T X + 3/2 X), each product
+    with the block-norm filter eps and each result with the post-filter eps_post.
+    Returns the list of iterates (X_1 .. X_iters)."""
+    out = []
+    for _ in range(iters):
+        t = multiply(X, X, None, 1.0, 0.0, eps)
+        T = filter_blocks(_Blocks(X.row_sizes, X.col_sizes, t["rows"], t["cols"], t["data"]),
+                          eps_post)
+        x = multiply(T, X, X, -0.5, 1.5, eps)
+        X = filter_blocks(_Blocks(X.row_sizes, X.col_sizes, x["rows"], x["cols"], x["data"]),
+                          eps_post)
+        out.append(X)
+    return out

@@ -63,6 +63,8 @@ _SIGS = {
     "bst_matrix_get_index": ([_VP, _VP, _VP, _VP], C.c_int32),
     "bst_matrix_bind_data": ([_VP, _VP], C.c_int32),
     "bst_matrix_destroy": ([_VP], C.c_int32),
+    "bst_matrix_filter": ([_VP, _VP, C.c_double, _VP, C.POINTER(_VP)], C.c_int32),
+    "bst_matrix_filter_copy": ([_VP, _VP, _VP], C.c_int32),
     "bst_multiply_plan": ([_VP, C.c_char, C.c_char, _VP, _VP, _VP, C.c_double, _VP,
                            C.POINTER(_VP)], C.c_int32),
     "bst_plan_result": ([_VP, C.POINTER(_VP)], C.c_int32),
@@ -193,6 +195,17 @@ def bst_matrix_bind_data(m, data):
 
 def bst_matrix_destroy(m):
     _check(load().bst_matrix_destroy(m), "bst_matrix_destroy")
+
+
+def bst_matrix_filter(ctx, X, eps, stream=None):
+    h = C.c_void_p()
+    _check(load().bst_matrix_filter(ctx, X, float(eps), _stream(stream), C.byref(h)),
+           "bst_matrix_filter")
+    return h
+
+
+def bst_matrix_filter_copy(X, Y, stream=None):
+    _check(load().bst_matrix_filter_copy(X, Y, _stream(stream)), "bst_matrix_filter_copy")
 
 
 def bst_multiply_plan(ctx, transa, transb, A, B, C_in=None, eps=0.0, stream=None):
@@ -473,6 +486,17 @@ def contract(T1: Tensor, T2: Tensor, c1, c2, f1, f2, result_order=None, R_in=Non
     p.alloc_result(device)
     p.execute(alpha, beta, precision, split_k, stream)
     return p
+
+
+def filter_blocks(X: Matrix, eps, device=0, stream=None) -> Matrix:
+    """The blocks of X with Frobenius norm >= eps, as a new matrix with its own data."""
+    import torch
+    h = bst_matrix_filter(context(device), X.handle, eps, stream)
+    _, _, _, ne = bst_matrix_info(h)
+    d = torch.empty(max(ne, 1), dtype=torch.float64, device=f"cuda:{device}")
+    bst_matrix_bind_data(h, d)
+    bst_matrix_filter_copy(X.handle, h, stream)
+    return Matrix(h, d)
 
 
 def multiply_plan(A: Matrix, B: Matrix, C_in: Matrix | None = None, eps=0.0, transa="N",

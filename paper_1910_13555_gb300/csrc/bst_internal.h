@@ -114,6 +114,10 @@ struct bst_matrix {
   double *data = nullptr;
   bst::Arena arena;
   bool owned_by_plan = false;
+  // a post-filter result (bst_matrix_filter): source block in X of every block, and X's
+  // block count when the filter ran
+  int32_t *src = nullptr;
+  int64_t src_nblocks = -1;
 };
 
 struct bst_tensor {

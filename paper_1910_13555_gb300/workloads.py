@@ -309,6 +309,28 @@ def tall_skinny(seed=1003, nk=100000, nmn=400, window=60, p=1.0 / 30, kmin=20, k
     return Problem(A, B, None, 1.0, 0.0, eps, transa="T", name=f"tall_skinny nk={nk} nmn={nmn}")
 
 
+def rect_case2(seed=1006, nm=20000, nk=400, window=60, p=1.0 / 30, bwin=20, bp=0.5, kmin=20,
+               kmax=50, eps=0.0) -> Problem:
+    """C(P lam, nu) = sum_mu A(P lam, mu) B(mu, nu): the rectangular case S_B << S_A, S_C
+    (a small B between a tall A and a tall C).
+
+    A: nm x nk blocks, row blocks of U{kmin..kmax}, columns {5, 13}; row block r keeps the
+    columns of the circular window [c_r, c_r + window) w.p. p (c_r ~ U[0, nk)).
+    B: nk x nk blocks {5, 13}; (mu, nu) kept w.p. bp when (nu - mu) mod nk < bwin."""
+    rng = np.random.default_rng(seed)
+    msz = rng.integers(kmin, kmax + 1, nm).astype(np.int32)
+    ksz = rng.choice(np.array([5, 13], np.int32), nk).astype(np.int32)
+    centre = rng.integers(0, nk, nm)
+    keep = rng.random((nm, window)) < p
+    r, w = np.nonzero(keep)
+    A = make_matrix(rng, msz, ksz, r, (centre[r] + w) % nk)
+    keep_b = rng.random((nk, bwin)) < bp
+    mu, d = np.nonzero(keep_b)
+    B = make_matrix(rng, ksz, ksz, mu, (mu + d) % nk)
+    eps_guard(A, B, eps)
+    return Problem(A, B, None, 1.0, 0.0, eps, name=f"rect_case2 nm={nm} nk={nk}")
+
+
 def batched(seed=1004, nprob=64, nmin=200, nmax=3000, occ_min=1e-3, occ_max=1e-1,
             eps=1e-10, sizes=SIZES_5_13_23):
     """Independent square problems of log-uniform size and occupancy."""
@@ -363,6 +385,64 @@ def rank3(seed=1005, nP=2000, sP=30, nao=1000, window=20, p=0.25, eps=0.0) -> Co
     U = _tensor(rng, [psz, aosz, aosz], pattern())
     return Contraction(T, U, c1=[0, 2], c2=[0, 1], f1=[1], f2=[2], result_order=None,
                        eps=eps, name=f"rank3 nP={nP} nao={nao}")
+
+
+def rank4(seed=1007, nP=400, sP=30, nao=400, window=8, p4=0.04, p3=0.25, eps=0.0) -> Contraction:
+    """R(mu, sig, lam) = sum_{P, nu} V(P, mu, nu, lam) U(P, nu, sig): a rank-4 tensor
+    contracted with a rank-3 one over two index pairs, the free modes of V not adjacent
+    (its matrix view needs a permuted copy) and the result modes reordered.
+
+    Each P has a centre c_P; V(P, mu, nu, lam) is kept w.p. p4 when mu, nu, lam all lie
+    in the circular window [c_P, c_P + window) of AO blocks, U(P, nu, sig) w.p. p3."""
+    rng = np.random.default_rng(seed)
+    psz = np.full(nP, sP, np.int32)
+    aosz = rng.choice(np.array([5, 13], np.int32), nao).astype(np.int32)
+    centre = rng.integers(0, nao, nP)
+    keep = rng.random((nP, window, window, window)) < p4
+    P, a, b, c = np.nonzero(keep)
+    V = _tensor(rng, [psz, aosz, aosz, aosz],
+                np.stack([P, (centre[P] + a) % nao, (centre[P] + b) % nao, (centre[P] + c) % nao], 1))
+    keep = rng.random((nP, window, window)) < p3
+    P, a, b = np.nonzero(keep)
+    U = _tensor(rng, [psz, aosz, aosz], np.stack([P, (centre[P] + a) % nao, (centre[P] + b) % nao], 1))
+    return Contraction(V, U, c1=[0, 2], c2=[0, 1], f1=[1, 3], f2=[2], result_order=[0, 2, 1],
+                       eps=eps, name=f"rank4 nP={nP} nao={nao}")
+
+
+def sign_matrix(seed=1008, nb=2000, width=6, p=0.5, coupling=0.1, gap=0.3,
+                sizes=SIZES_5_13_23) -> BSMatrix:
+    """A symmetric block-sparse matrix for the matrix-sign iteration (paper Sec. 2, the
+    linear-scaling DFT use of chained filtered multiplies), scaled so that its spectrum
+    lies in [-1, 1] away from 0.
+
+    Diagonal blocks Q diag(+-U[gap, 1]) Q^T (Q random orthogonal); off-diagonal blocks
+    (i, j), 0 < j - i <= width, kept w.p. p with N(0,1) entries times coupling/sqrt(n_i n_j),
+    mirrored to (j, i) transposed; the whole matrix divided by its largest absolute row
+    sum (a bound on the spectral radius)."""
+    rng = np.random.default_rng(seed)
+    sz = draw_sizes(rng, nb, sizes)
+    rows, cols, blocks = [], [], {}
+    for i in range(nb):
+        n = int(sz[i])
+        q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        lam = rng.uniform(gap, 1.0, n) * rng.choice([-1.0, 1.0], n)
+        blocks[(i, i)] = (q * lam) @ q.T
+        for j in range(i + 1, min(nb, i + width + 1)):
+            if rng.random() < p:
+                m = int(sz[j])
+                b = rng.standard_normal((n, m)) * coupling / np.sqrt(n * m)
+                blocks[(i, j)] = b
+                blocks[(j, i)] = b.T.copy()
+    keys = sorted(blocks)
+    rows = np.array([k[0] for k in keys], np.int32)
+    cols = np.array([k[1] for k in keys], np.int32)
+    rowsum = np.zeros(int(sz.sum()))
+    starts = np.concatenate([[0], np.cumsum(sz)])
+    for (i, j) in keys:
+        rowsum[starts[i]:starts[i + 1]] += np.abs(blocks[(i, j)]).sum(1)
+    scale = 1.0 / rowsum.max()
+    data = np.concatenate([blocks[k].ravel() * scale for k in keys])
+    return BSMatrix(sz, sz, rows, cols, data)
 
 
 def random_tensor(rng, nblk, sizes, occ, dist="uniform"):
