@@ -32,6 +32,9 @@ struct bst_batch {
   size_t pbytes = 0;
   int grid = 0;
   int stage_elems = 0;  // staged FP64 kernel slot size (0: some plan needs direct loads)
+  bool stage_strided = false;
+  int64_t n_titems = 0;
+  int64_t *titems = nullptr;  // staged kernel: every plan's tiles by decreasing cost
   // emulated FP64 schedule (item = plan << 32 | C block)
   int64_t n_items_e = 0;
   int64_t *items_e = nullptr;
@@ -131,6 +134,19 @@ bst_status bst_batch_create(bst_ctx *ctx, int32_t n, bst_plan *const *plans, bst
           mx = std::max(mx, (int)p->stage_elems);
         }
         if (all) b->stage_elems = std::max(mx, 1);
+        for (auto *p : b->plans) b->stage_strided = b->stage_strided || p->stage_strided;
+      }
+      if (b->stage_elems > 0) {
+        for (auto *p : b->plans) b->n_titems += p->n_tiles;
+        int64_t *t0 = scratch.alloc_n<int64_t>((size_t)b->n_titems);
+        int32_t *tk = scratch.alloc_n<int32_t>((size_t)b->n_titems);
+        int64_t toff = 0;
+        for (int32_t q : order) {
+          bst::build_plan_tile_items(b->plans[q], (int64_t)q << 32, t0 + toff, tk + toff, s);
+          toff += b->plans[q]->n_tiles;
+        }
+        b->titems = b->ar.alloc_n<int64_t>((size_t)b->n_titems);
+        bst::sort_items(t0, tk, b->n_titems, b->titems, scratch, s);
       }
       // emulated FP64: every C block (slicing state built per plan here)
       std::vector<int64_t> cnt(n);
@@ -147,7 +163,7 @@ bst_status bst_batch_create(bst_ctx *ctx, int32_t n, bst_plan *const *plans, bst
       b->epbytes = bst::emu_params_bytes();
       b->d_eparams = b->ar.alloc(b->epbytes * n);
       BST_CUDA(cudaMallocHost(&b->h_eparams, b->epbytes * n));
-      b->grid_e = bst::emu_persist_grid(ctx->num_sms);
+      b->grid_e = bst::emu_persist_grid(ctx->num_sms, ctx->tune_emu_row_scale);
       b->tune_version = ctx->tune_version;
       BST_CUDA(cudaStreamSynchronize(s));
       scratch.release_all();
@@ -187,8 +203,8 @@ bst_status bst_batch_execute(bst_batch *b, const double *alpha, const double *be
       }
       BST_CUDA(cudaMemcpyAsync(b->d_params, b->h_params, b->pbytes * n, cudaMemcpyHostToDevice, s));
       if (b->stage_elems > 0)
-        bst::launch_fp64_staged(b->d_params, b->items, b->n_items, b->stage_elems,
-                                b->ctx->num_sms, s);
+        bst::launch_fp64_staged(b->d_params, b->titems, b->n_titems, b->stage_elems,
+                                b->stage_strided, b->ctx->num_sms, s);
       else
         bst::launch_fp64_persist(b->d_params, b->items, b->n_items, b->counter, b->grid, s);
     } else {

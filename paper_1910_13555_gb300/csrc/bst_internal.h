@@ -259,6 +259,10 @@ struct bst_plan {
   int4 *fents = nullptr;
   int32_t *fdesc = nullptr;
   int32_t stage_elems = 0;
+  int64_t n_tiles = 0;         // row tiles of C blocks (the staged kernel's work units)
+  bool stage_strided = false;  // some tile or panel is a strided part of a block
+  int64_t *titems = nullptr;   // tiles by decreasing cost
+  int32_t *tkeys = nullptr;    // each tile's cost key
   // stats
   bst_stats stats{};
   // emulated-precision state (numeric_emu.cu), built on first use
@@ -309,14 +313,16 @@ int persist_grid(int num_sms);
 void launch_fp64_persist(const void *params, const int64_t *items, int64_t nitems,
                          unsigned long long *counter, int grid, cudaStream_t s);
 void build_f64_schedule(bst_plan *p, cudaStream_t s);
+void build_plan_tile_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys,
+                           cudaStream_t s);
 void launch_fp64_staged(const void *params, const int64_t *items, int64_t nitems,
-                        int slot_elems, int num_sms, cudaStream_t s);
+                        int slot_elems, bool strided, int num_sms, cudaStream_t s);
 // persistent emulated-FP64 numeric (numeric_emu.cu)
 size_t emu_params_bytes();
 int64_t emu_item_count(bst_plan *p, cudaStream_t s);
 void emu_build_items(bst_plan *p, int64_t base, int64_t *items, cudaStream_t s);
 void emu_prepare_and_fill(bst_plan *p, const NumArgs &a, void *out, cudaStream_t s);
-int emu_persist_grid(int num_sms);
+int emu_persist_grid(int num_sms, int row_scale);
 void launch_emu_persist(const void *params, const int64_t *items, int64_t nitems,
                         unsigned long long *counter, int grid, int row_scale, cudaStream_t s);
 

@@ -1149,19 +1149,23 @@ void emu_prepare_and_fill(bst_plan *p, const NumArgs &a, void *out, cudaStream_t
 }
 
 // resident CTAs of 256 threads per SM for the BF16 kernels (both scaling modes)
-static int emu_ctas_per_sm(bool batch) {
-  int nb0 = 0, nb1 = 0;
+static int emu_ctas_per_sm(bool batch, int row_scale) {
+  int nb = 0;
   if (batch) {
-    BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, k_num_emu_bf16_persist<0>, 256, 0));
-    BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_num_emu_bf16_persist<1>, 256, 0));
+    if (row_scale)
+      BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_emu_bf16_persist<1>, 256, 0));
+    else
+      BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_emu_bf16_persist<0>, 256, 0));
   } else {
-    BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, k_num_emu_bf16_persist1<0>, 256, 0));
-    BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_num_emu_bf16_persist1<1>, 256, 0));
+    if (row_scale)
+      BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_emu_bf16_persist1<1>, 256, 0));
+    else
+      BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_emu_bf16_persist1<0>, 256, 0));
   }
-  return std::max(1, std::min(nb0, nb1));
+  return std::max(1, nb);
 }
 
-int emu_persist_grid(int num_sms) { return emu_ctas_per_sm(true) * num_sms; }
+int emu_persist_grid(int num_sms, int row_scale) { return emu_ctas_per_sm(true, row_scale) * num_sms; }
 
 void launch_emu_persist(const void *params, const int64_t *items, int64_t nitems,
                         unsigned long long *counter, int grid, int row_scale, cudaStream_t s) {
@@ -1184,7 +1188,7 @@ void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
   emu_prepare(p, E, a, s);
   const EmuParams P = bf16_params(p, E, a);
   if (E.nitems_b > 0) {
-    const int g = (int)std::min<int64_t>((int64_t)emu_ctas_per_sm(false) * p->ctx->num_sms,
+    const int g = (int)std::min<int64_t>((int64_t)emu_ctas_per_sm(false, P.row_scale) * p->ctx->num_sms,
                                          (E.nitems_b + 8 * kChunk - 1) / (8 * kChunk));
     BST_CUDA(cudaMemsetAsync(E.counter, 0, sizeof(unsigned long long), s));
     if (P.row_scale)

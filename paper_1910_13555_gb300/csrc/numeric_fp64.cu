@@ -270,26 +270,30 @@ __global__ void __launch_bounds__(256, 2)
 
 // ---- staged persistent kernel ---------------------------------------------------------
 //
-// For plans whose products fit a shared-memory slot (m k + k n <= kStageMax doubles) and
-// whose C blocks have at most 32 * kMaxR elements.  A warp walks a stream of jobs (the
-// stack entries of its C blocks, C block by C block) and keeps two slots: while it
-// multiplies the op(A) and op(B) blocks of job j from one slot, the blocks of job j + 1
-// -- possibly the first product of its next C block -- arrive in the other through
-// cp.async, so the FP64 pipe never waits on an L2 round trip inside a product.  The
-// operands are then read from shared memory (broadcast for A, consecutive for B).
-// C blocks come from the cost-ordered item list in a fixed stride (item w, w + W, ...
-// for warp w of W); the descriptor of the next block is loaded one block ahead and its
-// first entries while the current block runs.
+// The work units are row tiles of C blocks (whole blocks up to 32 * kMaxR elements) and
+// their entries are (product, inner panel) pairs, both cut on the host so that one
+// entry's operands always fit a shared-memory slot (kStageMax doubles).  A warp walks a
+// stream of jobs (the entries of its tiles, tile by tile) and keeps two slots: while it
+// multiplies the op(A) and op(B) panels of job j from one slot, those of job j + 1 --
+// possibly the first job of its next tile -- arrive in the other through cp.async, so
+// the FP64 pipe never waits on an L2 round trip inside a product.  The operands are then
+// read from shared memory (broadcast for A, consecutive for B).  Tiles come from the
+// cost-ordered list in a fixed stride (item w, w + W, ... for warp w of W); the
+// descriptor of the next tile is loaded one tile ahead and its first entries while the
+// current tile runs.
 
-constexpr int kMaxR = 17;         // accumulators per lane: C blocks up to 544 elements
+constexpr int kMaxR = 17;         // accumulators per lane: tiles up to 544 elements
+constexpr int kTile = 32 * kMaxR;
 constexpr int kStageMax = 1536;   // doubles per slot (two slots per warp)
 constexpr int kStageWarps = 4;    // warps per CTA
 constexpr int kF64Desc = 8;       // descriptor words per C block
 
-// descriptor: 0 element offset of C block, 1 first entry, 2 entry count,
-// 3 m | n << 12, 4 C_in block (-1: none), 5 C block
+// Work unit: a row tile of a C block (the whole block when it has at most 32 * kMaxR
+// elements).  Descriptor: 0 element offset of the tile in C, 1 first entry, 2 entry
+// count, 3 tile rows m | n << 12, 4 C_in block (-1: none), 5 element offset of the tile
+// inside the C_in block, 6 C block.
 struct F64Blk {
-  int off, eb, ne, m, n, cin;
+  int off, eb, ne, m, n, cin, cio;
 };
 
 __device__ __forceinline__ F64Blk f64_blk(int dw) {
@@ -299,6 +303,7 @@ __device__ __forceinline__ F64Blk f64_blk(int dw) {
   b.ne = __shfl_sync(0xffffffffu, dw, 2);
   const int mn = __shfl_sync(0xffffffffu, dw, 3);
   b.cin = __shfl_sync(0xffffffffu, dw, 4);
+  b.cio = __shfl_sync(0xffffffffu, dw, 5);
   b.m = mn & 0xfff;
   b.n = (mn >> 12) & 0xfff;
   return b;
@@ -312,12 +317,43 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// one product's op(A) and op(B) blocks (stored layouts, na and nb doubles) into a slot
-__device__ __forceinline__ void stage_product(double *slot, const double *a, const double *b,
-                                              int na, int nb) {
+// `rows` segments of `len` doubles, `stride` apart, packed into dst (out of line: only
+// panels and tiles of large products take it)
+__device__ __noinline__ void stage_strided(double *dst, const double *src, int rows, int len,
+                                           int stride) {
   const int lane = threadIdx.x & 31;
-  for (int i = lane; i < na; i += 32) cp_async8(slot + i, a + i);
-  for (int i = lane; i < nb; i += 32) cp_async8(slot + na + i, b + i);
+  for (int r = 0; r < rows; ++r)
+    for (int c = lane; c < len; c += 32) cp_async8(dst + r * len + c, src + (int64_t)r * stride + c);
+}
+
+template <bool STRIDED>
+__device__ __forceinline__ void stage_2d(double *dst, const double *src, int rows, int len,
+                                         int stride) {
+  const int lane = threadIdx.x & 31;
+  if (!STRIDED || len == stride) {
+    for (int i = lane; i < rows * len; i += 32) cp_async8(dst + i, src + i);
+  } else {
+    stage_strided(dst, src, rows, len, stride);
+  }
+}
+
+// One job's operands into a slot in their stored layouts, restricted to the job's tile
+// rows and inner panel: op(A) is m x w (stored as m rows of w, or w rows of m when
+// transposed), op(B) is w x n (w rows of n, or n rows of w).  The entry gives the first
+// element of each and the stored row strides (sa | sb << 16); contiguous when a stride
+// equals the row length.
+template <bool STRIDED>
+__device__ __forceinline__ void stage_product(double *slot, const double *a, const double *b,
+                                              int m, int n, int w, int strides, int ta, int tb) {
+  const int sa = strides & 0xffff, sb = strides >> 16;
+  if (ta)
+    stage_2d<STRIDED>(slot, a, w, m, sa);
+  else
+    stage_2d<STRIDED>(slot, a, m, w, sa);
+  if (tb)
+    stage_2d<STRIDED>(slot + m * w, b, n, w, sb);
+  else
+    stage_2d<STRIDED>(slot + m * w, b, w, n, sb);
 }
 
 // acc[r] += op(A)(p_r, :) . op(B)(:, q_r) from a slot, o = lane + 32 r = p_r N + q_r
@@ -343,17 +379,20 @@ __device__ __forceinline__ void slot_product(const NumParams &P, const double *_
 }
 
 // any (m, n) with m n <= 32 R: runtime sizes, R accumulators
-template <int R>
+// any (m, n) with m n <= 32 kMaxR: runtime sizes, one body for every size (a body per
+// accumulator count thrashed the instruction cache on plans with many block sizes)
 __device__ __forceinline__ void slot_product_rt(const NumParams &P, const double *__restrict__ As,
                                                 int m, int n, int k, double (&acc)[kMaxR]) {
   const int lane = threadIdx.x & 31, mn = m * n;
   const double *__restrict__ Bs = As + m * k;
   const int a_sp = P.ta ? 1 : k, a_sl = P.ta ? m : 1;
   const int b_sl = P.tb ? 1 : n, b_sq = P.tb ? k : 1;
+  const int R = (mn + 31) >> 5;
 #pragma unroll 1
   for (int l = 0; l < k; ++l) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < kMaxR; ++r) {
+      if (r >= R) break;
       const int o = lane + 32 * r;
       if (o < mn) acc[r] = fma(As[(o / n) * a_sp + l * a_sl], Bs[(o % n) * b_sq + l * b_sl], acc[r]);
     }
@@ -385,20 +424,14 @@ __device__ __forceinline__ void slot_dispatch(const NumParams &P, const double *
   BST_MN(23, 13)
   BST_MN(23, 23)
 #undef BST_MN
-  switch ((m * n + 31) >> 5) {
-#define BST_R(RR) case RR: slot_product_rt<RR>(P, As, m, n, k, acc); return;
-    BST_R(1) BST_R(2) BST_R(3) BST_R(4) BST_R(5) BST_R(6) BST_R(7) BST_R(8) BST_R(9)
-    BST_R(10) BST_R(11) BST_R(12) BST_R(13) BST_R(14) BST_R(15) BST_R(16) BST_R(17)
-#undef BST_R
-    default: return;  // excluded on the host
-  }
+  slot_product_rt(P, As, m, n, k, acc);
 }
 
 // C = alpha * acc + beta * C_in for one C block (C_in unread when beta == 0)
 __device__ __forceinline__ void store_block(const NumParams &P, const F64Blk &b,
                                             const double (&acc)[kMaxR]) {
   const int lane = threadIdx.x & 31, mn = b.m * b.n;
-  const double *ci = (P.has_beta && b.cin >= 0) ? P.Cin + P.cin_off[b.cin] : nullptr;
+  const double *ci = (P.has_beta && b.cin >= 0) ? P.Cin + P.cin_off[b.cin] + b.cio : nullptr;
   double *C = P.C + b.off;
   if (!P.alpha_one || ci) {
 #pragma unroll
@@ -417,7 +450,7 @@ __device__ __forceinline__ void store_block(const NumParams &P, const F64Blk &b,
   }
 }
 
-template <class GetP>
+template <bool STRIDED, class GetP>
 __device__ __forceinline__ void staged_loop(const int64_t *__restrict__ items, int64_t nitems,
                                             int slot_elems, GetP get) {
   extern __shared__ double smem_stage[];
@@ -450,9 +483,10 @@ __device__ __forceinline__ void staged_loop(const int64_t *__restrict__ items, i
     const int64_t vnn = item(it + 2 * nw);
     const int dwnn = word(vnn);
     if (!staged && b.ne > 0) {
-      const int k = __shfl_sync(0xffffffffu, ent.z, 0);
-      stage_product(slots + slot * slot_elems, P.A + __shfl_sync(0xffffffffu, ent.x, 0),
-                    P.B + __shfl_sync(0xffffffffu, ent.y, 0), b.m * k, k * b.n);
+      stage_product<STRIDED>(slots + slot * slot_elems, P.A + __shfl_sync(0xffffffffu, ent.x, 0),
+                    P.B + __shfl_sync(0xffffffffu, ent.y, 0), b.m, b.n,
+                    __shfl_sync(0xffffffffu, ent.z, 0), __shfl_sync(0xffffffffu, ent.w, 0), P.ta,
+                    P.tb);
       cp_commit();
     }
     double acc[kMaxR];
@@ -475,14 +509,16 @@ __device__ __forceinline__ void staged_loop(const int64_t *__restrict__ items, i
           src = group(v, b, g0 + 32);
           j = 0;
         }
-        const int k1 = __shfl_sync(0xffffffffu, src.z, j);
-        stage_product(nxt, P.A + __shfl_sync(0xffffffffu, src.x, j),
-                      P.B + __shfl_sync(0xffffffffu, src.y, j), b.m * k1, k1 * b.n);
+        stage_product<STRIDED>(nxt, P.A + __shfl_sync(0xffffffffu, src.x, j),
+                      P.B + __shfl_sync(0xffffffffu, src.y, j), b.m, b.n,
+                      __shfl_sync(0xffffffffu, src.z, j), __shfl_sync(0xffffffffu, src.w, j), P.ta,
+                      P.tb);
       } else if (vn >= 0 && bn.ne > 0) {
         const NumParams &Pn = get(vn >> 32);
-        const int k1 = __shfl_sync(0xffffffffu, entn.z, 0);
-        stage_product(nxt, Pn.A + __shfl_sync(0xffffffffu, entn.x, 0),
-                      Pn.B + __shfl_sync(0xffffffffu, entn.y, 0), bn.m * k1, k1 * bn.n);
+        stage_product<STRIDED>(nxt, Pn.A + __shfl_sync(0xffffffffu, entn.x, 0),
+                      Pn.B + __shfl_sync(0xffffffffu, entn.y, 0), bn.m, bn.n,
+                      __shfl_sync(0xffffffffu, entn.z, 0), __shfl_sync(0xffffffffu, entn.w, 0),
+                      Pn.ta, Pn.tb);
       }
       cp_commit();
       cp_wait_prev();
@@ -505,61 +541,114 @@ __device__ __forceinline__ void staged_loop(const int64_t *__restrict__ items, i
   cp_wait_all();
 }
 
+// STRIDED: the plan has row tiles or inner panels (staging copies strided rows)
+template <bool STRIDED>
 __global__ void __launch_bounds__(32 * kStageWarps, 3)
     k_num_fp64_staged1(NumParams P, const int64_t *__restrict__ items, int64_t nitems,
                        int slot_elems) {
-  staged_loop(items, nitems, slot_elems, [&](int64_t) -> const NumParams & { return P; });
+  staged_loop<STRIDED>(items, nitems, slot_elems,
+                       [&](int64_t) -> const NumParams & { return P; });
 }
 
+template <bool STRIDED>
 __global__ void __launch_bounds__(32 * kStageWarps, 3)
     k_num_fp64_staged(const NumParams *__restrict__ plans, const int64_t *__restrict__ items,
                       int64_t nitems, int slot_elems) {
-  staged_loop(items, nitems, slot_elems,
-              [&](int64_t pl) -> const NumParams & { return plans[pl]; });
+  staged_loop<STRIDED>(items, nitems, slot_elems,
+                       [&](int64_t pl) -> const NumParams & { return plans[pl]; });
 }
 
 // ---- schedule of the staged kernel (built with the plan) ----------------------------
+//
+// Work units ("tiles") are row ranges of C blocks: a block of m x n elements with
+// m n > 32 * kMaxR is cut into tiles of floor(32 kMaxR / n) rows.  A product whose
+// tile operands exceed a slot ((tile rows + n) k > kStageMax) is cut into panels of the
+// inner dimension of width floor(kStageMax / (tile rows + n)).  Each tile lists its
+// (product, panel) entries {first A element, first B element, panel width w, row
+// strides}, in the product order of the stacks; per (m, n) class the host passes the
+// tile rows, and per (class, k class) the panel width.
 
-__global__ void k_f64_ent_count(int64_t nc, int32_t Dk, const int32_t *__restrict__ run_len,
-                                int32_t *__restrict__ cnt) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
-  int s = 0;
-  for (int kc = 0; kc < Dk; ++kc) s += run_len[c * Dk + kc];
-  cnt[c] = s;
+struct SchedTabs {
+  const int32_t *cls_m, *cls_n, *tile_rows;  // per (m, n) class
+  const int32_t *wpanel;                     // per (class, k class): panel width
+  const int32_t *kval;
+  int32_t Dk, ta, tb;
+};
+
+__device__ __forceinline__ int ntiles_of(const SchedTabs &S, int cls) {
+  const int tr = S.tile_rows[cls];
+  return (S.cls_m[cls] + tr - 1) / tr;
 }
 
-// C-major entries {a_off, b_off, k, stack entry}: C block c owns [ebeg[c], ebeg[c+1])
-__global__ void k_f64_ents(int64_t nc, int32_t Dk, const int32_t *__restrict__ run_start,
-                           const int32_t *__restrict__ run_len, const int32_t *__restrict__ kval,
-                           const int32_t *__restrict__ s_a, const int32_t *__restrict__ s_b,
-                           const int64_t *__restrict__ ebeg, int4 *__restrict__ ents) {
+__global__ void k_f64_tile_count(int64_t nc, const int32_t *__restrict__ c_cls, SchedTabs S,
+                                 int32_t *__restrict__ cnt) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
-  int64_t q = ebeg[c];
-  for (int kc = 0; kc < Dk; ++kc) {
-    const int len = run_len[c * Dk + kc];
-    const int e0 = run_start[c * Dk + kc];
-    for (int e = e0; e < e0 + len; ++e) ents[q++] = make_int4(s_a[e], s_b[e], kval[kc], e);
-  }
+  if (c < nc) cnt[c] = ntiles_of(S, c_cls[c]);
 }
 
-__global__ void k_f64_desc(int64_t nc, const int64_t *__restrict__ ebeg,
-                           const int64_t *__restrict__ c_off, const int32_t *__restrict__ c_cls,
-                           const int32_t *__restrict__ cls_m, const int32_t *__restrict__ cls_n,
-                           const int32_t *__restrict__ c_cin, int32_t *__restrict__ desc) {
+// entries of every tile of block c: sum over its products of the panel count
+__global__ void k_f64_ent_count(int64_t nc, const int32_t *__restrict__ c_cls,
+                                const int32_t *__restrict__ run_len, const int64_t *__restrict__ tbeg,
+                                SchedTabs S, int32_t *__restrict__ cnt) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const int cls = c_cls[c];
-  int32_t *d = desc + c * kF64Desc;
-  d[0] = (int32_t)c_off[c];
-  d[1] = (int32_t)ebeg[c];
-  d[2] = (int32_t)(ebeg[c + 1] - ebeg[c]);
-  d[3] = cls_m[cls] | (cls_n[cls] << 12);
-  d[4] = c_cin[c];
-  d[5] = (int32_t)c;
-  d[6] = 0;
-  d[7] = 0;
+  int s = 0;
+  for (int kc = 0; kc < S.Dk; ++kc) {
+    const int w = S.wpanel[cls * S.Dk + kc], k = S.kval[kc];
+    s += run_len[c * S.Dk + kc] * ((k + w - 1) / w);
+  }
+  const int nt = ntiles_of(S, cls);
+  for (int t = 0; t < nt; ++t) cnt[tbeg[c] + t] = s;
+}
+
+// descriptors and entries of every tile of block c, and each tile's cost key
+// (63 - floor(log2(flops)): a stable partition on it lists costly tiles first)
+__global__ void k_f64_tiles(int64_t nc, const int32_t *__restrict__ c_cls,
+                            const int32_t *__restrict__ run_start, const int32_t *__restrict__ run_len,
+                            const int32_t *__restrict__ s_a, const int32_t *__restrict__ s_b,
+                            const int64_t *__restrict__ c_off, const int32_t *__restrict__ c_cin,
+                            const int64_t *__restrict__ tbeg, const int64_t *__restrict__ ebeg,
+                            SchedTabs S, int32_t *__restrict__ desc, int4 *__restrict__ ents,
+                            int32_t *__restrict__ key) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int cls = c_cls[c];
+  const int m = S.cls_m[cls], n = S.cls_n[cls], tr = S.tile_rows[cls];
+  const int nt = (m + tr - 1) / tr;
+  for (int t = 0; t < nt; ++t) {
+    const int64_t tile = tbeg[c] + t;
+    const int p0 = t * tr, mt = min(tr, m - p0);
+    int64_t q = ebeg[tile];
+    unsigned long long flops = 0;
+    for (int kc = 0; kc < S.Dk; ++kc) {
+      const int len = run_len[c * S.Dk + kc];
+      if (len == 0) continue;
+      const int e0 = run_start[c * S.Dk + kc];
+      const int k = S.kval[kc], w = S.wpanel[cls * S.Dk + kc];
+      // stored row strides of the panels: A is m x k (k x m when transposed), B is k x n
+      // (n x k when transposed)
+      const int strides = (S.ta ? m : k) | ((S.tb ? k : n) << 16);
+      for (int e = e0; e < e0 + len; ++e)
+        for (int l0 = 0; l0 < k; l0 += w) {
+          const int wl = min(w, k - l0);
+          const int a = s_a[e] + (S.ta ? l0 * m + p0 : p0 * k + l0);
+          const int b = s_b[e] + (S.tb ? l0 : l0 * n);
+          ents[q++] = make_int4(a, b, wl, strides);
+        }
+      flops += (unsigned long long)len * mt * n * k;
+    }
+    int32_t *d = desc + tile * kF64Desc;
+    d[0] = (int32_t)(c_off[c] + (int64_t)p0 * n);
+    d[1] = (int32_t)ebeg[tile];
+    d[2] = (int32_t)(q - ebeg[tile]);
+    d[3] = mt | (n << 12);
+    d[4] = c_cin[c];
+    d[5] = p0 * n;
+    d[6] = (int32_t)c;
+    d[7] = 0;
+    key[tile] = __clzll(flops + 1ull);
+  }
 }
 
 __global__ void k_plan_items(int64_t nc, int64_t base, int64_t *__restrict__ item) {
@@ -677,81 +766,141 @@ void sort_items(const int64_t *items, const int32_t *keys, int64_t n, int64_t *o
   BST_CHECK_LAUNCH();
 }
 
-// Entries, descriptors and slot size of the staged kernel; the plan keeps
-// stage_elems = 0 (and runs the direct-load kernel) when a product does not fit a slot,
-// a C block has more than 32 * kMaxR elements or a block size does not fit 12 bits.
+// Tiles, entries, descriptors and slot size of the staged kernel.  The plan keeps
+// stage_elems = 0 (and runs the direct-load kernel) only when a block size does not fit
+// the descriptor's 12 bits or a row of C (n elements) exceeds one output tile.
 void build_f64_schedule(bst_plan *p, cudaStream_t s) {
   p->stage_elems = 0;
+  p->n_tiles = 0;
   const int64_t nc = p->C->nblocks;
   if (nc == 0 || p->T == 0) return;
-  int64_t slot = 0;
-  for (int32_t b = 0; b < p->nb_all; ++b) {
-    if (p->h_bucket_ptr[b + 1] == p->h_bucket_ptr[b]) continue;
-    const int32_t kc = b % p->Dk, ncl = (b / p->Dk) % p->Dn, mc = b / (p->Dk * p->Dn);
-    const int64_t m = p->m_vals[mc], n = p->n_vals[ncl], k = p->k_vals[kc];
-    slot = std::max(slot, m * k + k * n);
-  }
-  for (int32_t c = 0; c < p->Dm * p->Dn; ++c) {
+  const int32_t ncls = p->Dm * p->Dn, Dk = p->Dk;
+  std::vector<int32_t> tile_rows((size_t)ncls, 1), wpanel((size_t)ncls * Dk, 1);
+  for (int32_t c = 0; c < ncls; ++c) {
     if (p->h_class_ptr[c + 1] == p->h_class_ptr[c]) continue;
     const int64_t m = p->m_vals[c / p->Dn], n = p->n_vals[c % p->Dn];
-    if (m * n > 32 * kMaxR || m >= 4096 || n >= 4096) return;
+    if (m >= 4096 || n >= 4096 || n > kTile) return;
+    const int64_t tr = m * n <= kTile ? m : kTile / n;
+    if (tr + n > kStageMax) return;
+    tile_rows[(size_t)c] = (int32_t)tr;
   }
-  if (slot > kStageMax) return;
+  bool strided = false;
+  for (int32_t c = 0; c < ncls; ++c)
+    if (p->h_class_ptr[c + 1] > p->h_class_ptr[c] && tile_rows[(size_t)c] < p->m_vals[c / p->Dn])
+      strided = true;
+  int64_t slot = 1;
+  for (int32_t b = 0; b < p->nb_all; ++b) {
+    if (p->h_bucket_ptr[b + 1] == p->h_bucket_ptr[b]) continue;
+    const int32_t kc = b % Dk, ncl = (b / Dk) % p->Dn, mc = b / (Dk * p->Dn);
+    const int32_t cls = mc * p->Dn + ncl;
+    const int64_t n = p->n_vals[ncl], k = p->k_vals[kc], tr = tile_rows[(size_t)cls];
+    const int64_t w = (tr + n) * k <= kStageMax ? k : kStageMax / (tr + n);
+    wpanel[(size_t)cls * Dk + kc] = (int32_t)w;
+    if (w < k) strided = true;
+    slot = std::max(slot, (tr + n) * w);
+  }
   Arena &ar = p->arena;
   Arena scratch;
   scratch.ctx = static_cast<Ctx *>(p->ctx);
   scratch.stream = s;
-  int32_t *cnt = scratch.alloc_n<int32_t>((size_t)nc);
-  int64_t *ebeg = scratch.alloc_n<int64_t>((size_t)nc + 1);
-  p->fents = ar.alloc_n<int4>((size_t)p->T);
-  p->fdesc = ar.alloc_n<int32_t>((size_t)nc * kF64Desc);
-  k_f64_ent_count<<<nblk(nc, 256), 256, 0, s>>>(nc, p->Dk, p->run_len, cnt);
+  int32_t *d_tr = scratch.alloc_n<int32_t>(tile_rows.size());
+  int32_t *d_wp = scratch.alloc_n<int32_t>(wpanel.size());
+  BST_CUDA(cudaMemcpyAsync(d_tr, tile_rows.data(), 4 * tile_rows.size(), cudaMemcpyHostToDevice, s));
+  BST_CUDA(cudaMemcpyAsync(d_wp, wpanel.data(), 4 * wpanel.size(), cudaMemcpyHostToDevice, s));
+  SchedTabs S;
+  S.cls_m = p->cls_m;
+  S.cls_n = p->cls_n;
+  S.tile_rows = d_tr;
+  S.wpanel = d_wp;
+  S.kval = p->kval;
+  S.Dk = Dk;
+  S.ta = p->ta;
+  S.tb = p->tb;
+  int32_t *tcnt = scratch.alloc_n<int32_t>((size_t)nc);
+  int64_t *tbeg = scratch.alloc_n<int64_t>((size_t)nc + 1);
+  k_f64_tile_count<<<nblk(nc, 256), 256, 0, s>>>(nc, p->c_cls, S, tcnt);
   BST_CHECK_LAUNCH();
-  exscan_i32_i64(cnt, ebeg, nc, scratch, s);
-  k_f64_ents<<<nblk(nc, 256), 256, 0, s>>>(nc, p->Dk, p->run_start, p->run_len, p->kval, p->s_a,
-                                           p->s_b, ebeg, p->fents);
+  exscan_i32_i64(tcnt, tbeg, nc, scratch, s);
+  int64_t ntiles = 0;
+  {
+    ReadBack rb(p->ctx, s);
+    rb.add(&ntiles, tbeg + nc, 8);
+    rb.done();
+  }
+  int32_t *ecnt = scratch.alloc_n<int32_t>((size_t)ntiles);
+  int64_t *ebeg = scratch.alloc_n<int64_t>((size_t)ntiles + 1);
+  k_f64_ent_count<<<nblk(nc, 256), 256, 0, s>>>(nc, p->c_cls, p->run_len, tbeg, S, ecnt);
   BST_CHECK_LAUNCH();
-  k_f64_desc<<<nblk(nc, 256), 256, 0, s>>>(nc, ebeg, p->C->off, p->c_cls, p->cls_m, p->cls_n,
-                                           p->c_cin, p->fdesc);
+  exscan_i32_i64(ecnt, ebeg, ntiles, scratch, s);
+  int64_t nents = 0;
+  {
+    ReadBack rb(p->ctx, s);
+    rb.add(&nents, ebeg + ntiles, 8);
+    rb.done();
+  }
+  BST_REQUIRE(nents < INT32_MAX && ntiles < INT32_MAX, BST_ERR_OVERFLOW,
+              "more than 2^31-1 staged tiles or entries");
+  p->fents = ar.alloc_n<int4>((size_t)nents);
+  p->fdesc = ar.alloc_n<int32_t>((size_t)ntiles * kF64Desc);
+  p->tkeys = ar.alloc_n<int32_t>((size_t)ntiles);
+  k_f64_tiles<<<nblk(nc, 256), 256, 0, s>>>(nc, p->c_cls, p->run_start, p->run_len, p->s_a,
+                                            p->s_b, p->C->off, p->c_cin, tbeg, ebeg, S, p->fdesc,
+                                            p->fents, p->tkeys);
   BST_CHECK_LAUNCH();
+  // tiles by decreasing cost
+  int64_t *it0 = scratch.alloc_n<int64_t>((size_t)ntiles);
+  p->titems = ar.alloc_n<int64_t>((size_t)ntiles);
+  k_plan_items<<<nblk(ntiles, 256), 256, 0, s>>>(ntiles, 0, it0);
+  BST_CHECK_LAUNCH();
+  sort_items(it0, p->tkeys, ntiles, p->titems, scratch, s);
   BST_CUDA(cudaStreamSynchronize(s));
   scratch.release_all();
+  p->n_tiles = ntiles;
   p->stage_elems = (int32_t)slot;
+  p->stage_strided = strided;
 }
 
-// resident CTAs per SM of the staged kernel for a slot size; raises the kernel's
-// dynamic shared-memory limit on first use
-static int staged_ctas_per_sm(bool batch, int slot_elems, size_t &smem) {
-  static bool attr_set[2] = {false, false};
+// the staged kernel's tiles of a plan for a batch (item = base | tile) and their keys
+void build_plan_tile_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys,
+                           cudaStream_t s) {
+  if (p->n_tiles == 0) return;
+  k_plan_items<<<nblk(p->n_tiles, 256), 256, 0, s>>>(p->n_tiles, base, items);
+  BST_CHECK_LAUNCH();
+  BST_CUDA(cudaMemcpyAsync(keys, p->tkeys, 4 * (size_t)p->n_tiles, cudaMemcpyDeviceToDevice, s));
+}
+
+// resident CTAs per SM of a staged kernel instance for a slot size; raises its dynamic
+// shared-memory limit on first use
+template <class K>
+static int staged_ctas_per_sm(K kernel, bool &attr_set, int slot_elems, size_t &smem) {
   const size_t max_smem = sizeof(double) * 2 * kStageMax * kStageWarps;
-  if (!attr_set[batch]) {
-    if (batch)
-      BST_CUDA(cudaFuncSetAttribute(k_num_fp64_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)max_smem));
-    else
-      BST_CUDA(cudaFuncSetAttribute(k_num_fp64_staged1,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
-    attr_set[batch] = true;
+  if (!attr_set) {
+    BST_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)max_smem));
+    attr_set = true;
   }
   smem = sizeof(double) * 2 * (size_t)slot_elems * kStageWarps;
   int nb = 0;
-  if (batch)
-    BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_fp64_staged,
-                                                           32 * kStageWarps, smem));
-  else
-    BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_num_fp64_staged1,
-                                                           32 * kStageWarps, smem));
+  BST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, 32 * kStageWarps, smem));
   return std::max(1, nb);
 }
 
+static bool g_attr[4] = {false, false, false, false};
+
 void launch_fp64_staged(const void *params, const int64_t *items, int64_t nitems,
-                        int slot_elems, int num_sms, cudaStream_t s) {
+                        int slot_elems, bool strided, int num_sms, cudaStream_t s) {
   if (nitems == 0) return;
   size_t smem = 0;
-  const int per = staged_ctas_per_sm(true, slot_elems, smem);
-  const int g = (int)std::min<int64_t>((int64_t)per * num_sms, (nitems + kStageWarps - 1) / kStageWarps);
-  k_num_fp64_staged<<<g, 32 * kStageWarps, smem, s>>>(static_cast<const NumParams *>(params),
-                                                       items, nitems, slot_elems);
+  const int per = strided
+                      ? staged_ctas_per_sm(k_num_fp64_staged<true>, g_attr[0], slot_elems, smem)
+                      : staged_ctas_per_sm(k_num_fp64_staged<false>, g_attr[1], slot_elems, smem);
+  const int g = (int)std::min<int64_t>((int64_t)per * num_sms,
+                                       (nitems + kStageWarps - 1) / kStageWarps);
+  const NumParams *P = static_cast<const NumParams *>(params);
+  if (strided)
+    k_num_fp64_staged<true><<<g, 32 * kStageWarps, smem, s>>>(P, items, nitems, slot_elems);
+  else
+    k_num_fp64_staged<false><<<g, 32 * kStageWarps, smem, s>>>(P, items, nitems, slot_elems);
   BST_CHECK_LAUNCH();
 }
 
@@ -793,13 +942,21 @@ int choose_split(const bst_plan *p, int num_sms) {
 void execute_fp64(bst_plan *p, const NumArgs &a, int split, cudaStream_t s) {
   const int64_t nc = p->C->nblocks;
   if (nc == 0) return;
-  if (split <= 1 && p->items && p->stage_elems > 0) {
+  if (split <= 1 && p->stage_elems > 0) {
     size_t smem = 0;
-    const int per = staged_ctas_per_sm(false, p->stage_elems, smem);
+    const bool st = p->stage_strided;
+    const int per =
+        st ? staged_ctas_per_sm(k_num_fp64_staged1<true>, g_attr[2], p->stage_elems, smem)
+           : staged_ctas_per_sm(k_num_fp64_staged1<false>, g_attr[3], p->stage_elems, smem);
     const int g = (int)std::min<int64_t>((int64_t)per * p->ctx->num_sms,
-                                         (nc + kStageWarps - 1) / kStageWarps);
-    k_num_fp64_staged1<<<g, 32 * kStageWarps, smem, s>>>(make_params(p, a, 1), p->items, nc,
-                                                         p->stage_elems);
+                                         (p->n_tiles + kStageWarps - 1) / kStageWarps);
+    const NumParams P = make_params(p, a, 1);
+    if (st)
+      k_num_fp64_staged1<true><<<g, 32 * kStageWarps, smem, s>>>(P, p->titems, p->n_tiles,
+                                                                 p->stage_elems);
+    else
+      k_num_fp64_staged1<false><<<g, 32 * kStageWarps, smem, s>>>(P, p->titems, p->n_tiles,
+                                                                  p->stage_elems);
     BST_CHECK_LAUNCH();
     return;
   }
