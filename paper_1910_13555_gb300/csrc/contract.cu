@@ -136,21 +136,23 @@ __global__ void k_permute(PermArgs P) {
   if (q >= P.nblocks) return;
   const int64_t tb = P.tblk ? P.tblk[q] : q;
   const int32_t *t = P.idx + tb * P.rank;
-  int32_t s[kMaxRank];
-  int64_t st[kMaxRank];
-  int64_t len = 1;
+  // block-local index arithmetic in 32 bits (a tensor block holds fewer than 2^31
+  // elements; 64-bit division costs several times more)
+  int32_t s[kMaxRank], st[kMaxRank];
+  int32_t len = 1;
   for (int d = P.rank - 1; d >= 0; --d) {
     s[d] = P.sz[P.szoff[d] + t[d]];
     st[d] = len;
     len *= s[d];
   }
   const int64_t to = P.toff[tb], vo = P.voff[q];
-  for (int64_t e = lane; e < len; e += 32) {
-    int64_t rem = e, src = 0;
+  for (int32_t e = lane; e < len; e += 32) {
+    int32_t rem = e, src = 0;
     for (int j = P.rank - 1; j >= 0; --j) {
       const int d = P.ord[j];
-      src += (rem % s[d]) * st[d];
-      rem /= s[d];
+      const int32_t qd = rem / s[d];
+      src += (rem - qd * s[d]) * st[d];
+      rem = qd;
     }
     if (P.to_view)
       P.dst[vo + e] = P.src[to + src];

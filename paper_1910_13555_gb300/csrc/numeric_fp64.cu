@@ -388,13 +388,25 @@ __device__ __forceinline__ void slot_product_rt(const NumParams &P, const double
   const int a_sp = P.ta ? 1 : k, a_sl = P.ta ? m : 1;
   const int b_sl = P.tb ? 1 : n, b_sq = P.tb ? k : 1;
   const int R = (mn + 31) >> 5;
-#pragma unroll 1
-  for (int l = 0; l < k; ++l) {
+  // output by output: the element's row and column are found once (incrementally from
+  // the previous accumulator's: o grows by 32), then its whole dot product runs
+  int p = lane / n, q = lane - p * n;
+  const int dp = 32 / n, dq = 32 - dp * n;
 #pragma unroll
-    for (int r = 0; r < kMaxR; ++r) {
-      if (r >= R) break;
-      const int o = lane + 32 * r;
-      if (o < mn) acc[r] = fma(As[(o / n) * a_sp + l * a_sl], Bs[(o % n) * b_sq + l * b_sl], acc[r]);
+  for (int r = 0; r < kMaxR; ++r) {
+    if (r >= R) break;
+    if (lane + 32 * r < mn) {
+      const double *a = As + p * a_sp, *b = Bs + q * b_sq;
+      double s = acc[r];
+#pragma unroll 4
+      for (int l = 0; l < k; ++l) s = fma(a[l * a_sl], b[l * b_sl], s);
+      acc[r] = s;
+    }
+    p += dp;
+    q += dq;
+    if (q >= n) {
+      q -= n;
+      ++p;
     }
   }
 }
