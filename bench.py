@@ -77,6 +77,26 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def rank_seed(rank):
+    """Each rank multiplies its own banded product (the path partitions into independent
+    problems: no data-path collective, weak scaling)."""
+    return 1002 + 1000 * rank
+
+
+def reduce_over_ranks(ms, flops, world, device):
+    """Whole-job timing: the slowest rank's time and the work of all ranks (the only
+    collectives of the benchmark, after the timed region)."""
+    if world <= 1:
+        return ms, flops
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    f = torch.tensor([flops], device=device, dtype=torch.float64)
+    dist.all_reduce(f)
+    return float(t.item()), float(f.item())
+
+
 # ---------------------------------------------------------------------------------------
 # clocks sampled during the timed region
 
@@ -271,7 +291,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     bst.load()
-    p = banded(seed=1002 + 1000 * rank, nb=args.nb)
+    p = banded(seed=rank_seed(rank), nb=args.nb)
     workload = WORKLOAD if args.nb == 4000 else WORKLOAD.replace("4000x4000", f"{args.nb}x{args.nb}")
     prec_name, kernel = PRECISIONS[args.precision]
     main_prec = getattr(bst, prec_name)
@@ -328,15 +348,7 @@ def run_ours(args):
     ms = t0.elapsed_time(t1)
     num_ms = [a.elapsed_time(b) for a, b in evs]
     ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-        f = torch.tensor([flops], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(f)
-        total_flops = float(f.item())
-    else:
-        total_flops = flops
+    ms_max, total_flops = reduce_over_ranks(ms, flops, world, dev)
     value = total_flops * args.steps / (ms_max * 1e-3) / 1e9
     num_avg = statistics.mean(num_ms)
     achieved = flops / (num_avg * 1e-3) / 1e12
@@ -738,13 +750,7 @@ def e2e_leg(p, local_rank, steps, stream, barrier, world, dev):
     dt = (time.perf_counter() - t) / steps
     alive[0] = alive[1] = None
     flops = info["flops"]
-    if world > 1:
-        tt = torch.tensor([dt], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        dt = float(tt.item())
-        f = torch.tensor([flops], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(f)
-        flops = float(f.item())
+    dt, flops = reduce_over_ranks(dt, flops, world, dev)
     h2d = (p.A.data.nbytes + p.B.data.nbytes + 8 * (p.A.nblocks + p.B.nblocks) +
            4 * (len(p.A.row_sizes) + len(p.A.col_sizes) + len(p.B.row_sizes) + len(p.B.col_sizes)))
     return {"value": flops / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
