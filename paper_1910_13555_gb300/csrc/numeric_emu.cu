@@ -26,13 +26,15 @@
 // accumulation, and the products summed as an unevaluated FP32 pair (TwoSum), then
 // converted to FP64 and combined with alpha, beta.
 //
-// Both use warp-level mma.sync tiles (m16n8k16 BF16, m16n8k8 TF32): one warp owns a
-// 16 x 8 (BF16) or 16 x 16 (TF32) tile of one C block (no two warps write the same
-// element); for the BF16 kernel the tile rows may run over the C block's columns instead
-// (C^T = op(B)^T op(A)^T on the same slices), chosen per (m, n) class by the autotuner.
-// The operand slices are staged once per execute in a padded, permuted layout that makes
-// every fragment a single 8-byte load (inner dimension padded with zeros to the MMA K
-// and permuted inside each chunk so a thread's four values are adjacent).
+// Both use warp-level mma.sync tiles (m16n8k16 BF16, m16n8k8 TF32).  The BF16 kernel
+// runs one warp per C block (its 16 x 8 tiles one after another; no two warps write the
+// same element), taking consecutive C blocks in chunks from a counter; the tile rows may
+// run over the C block's columns instead (C^T = op(B)^T op(A)^T on the same slices),
+// chosen per (m, n) class by the autotuner.  The 3xTF32 kernel runs one warp per 16 x 16
+// tile.  The operand slices are staged once per execute in a padded, permuted layout that
+// makes every fragment a single 8-byte load at a fixed offset (inner dimension padded
+// with zeros to the MMA K, a chunk's slices side by side, and permuted inside each chunk
+// so a thread's four values are adjacent).
 #include <cuda_bf16.h>
 
 #include <algorithm>
