@@ -778,22 +778,22 @@ void sort_items(const int64_t *items, const int32_t *keys, int64_t n, int64_t *o
   BST_CHECK_LAUNCH();
 }
 
-// Tiles, entries, descriptors and slot size of the staged kernel.  The plan keeps
-// stage_elems = 0 (and runs the direct-load kernel) only when a block size does not fit
-// the descriptor's 12 bits or a row of C (n elements) exceeds one output tile.
-void build_f64_schedule(bst_plan *p, cudaStream_t s) {
+// Tiles, entries, descriptors and slot size of the staged kernel; false (stage_elems
+// stays 0) when a block size does not fit the descriptor's 12 bits or a row of C (n
+// elements) exceeds one output tile.
+static bool build_staged(bst_plan *p, cudaStream_t s) {
   p->stage_elems = 0;
   p->n_tiles = 0;
   const int64_t nc = p->C->nblocks;
-  if (nc == 0 || p->T == 0) return;
+  if (nc == 0 || p->T == 0) return false;
   const int32_t ncls = p->Dm * p->Dn, Dk = p->Dk;
   std::vector<int32_t> tile_rows((size_t)ncls, 1), wpanel((size_t)ncls * Dk, 1);
   for (int32_t c = 0; c < ncls; ++c) {
     if (p->h_class_ptr[c + 1] == p->h_class_ptr[c]) continue;
     const int64_t m = p->m_vals[c / p->Dn], n = p->n_vals[c % p->Dn];
-    if (m >= 4096 || n >= 4096 || n > kTile) return;
+    if (m >= 4096 || n >= 4096 || n > kTile) return false;
     const int64_t tr = m * n <= kTile ? m : kTile / n;
-    if (tr + n > kStageMax) return;
+    if (tr + n > kStageMax) return false;
     tile_rows[(size_t)c] = (int32_t)tr;
   }
   bool strided = false;
@@ -870,6 +870,28 @@ void build_f64_schedule(bst_plan *p, cudaStream_t s) {
   p->n_tiles = ntiles;
   p->stage_elems = (int32_t)slot;
   p->stage_strided = strided;
+  return true;
+}
+
+// C blocks by decreasing cost, for the direct-load persistent kernel
+static void build_cost_items(bst_plan *p, cudaStream_t s) {
+  const int64_t nc = p->C->nblocks;
+  if (nc == 0) return;
+  Arena scratch;
+  scratch.ctx = static_cast<Ctx *>(p->ctx);
+  scratch.stream = s;
+  int64_t *it0 = scratch.alloc_n<int64_t>((size_t)nc);
+  int32_t *keys = scratch.alloc_n<int32_t>((size_t)nc);
+  p->items = p->arena.alloc_n<int64_t>((size_t)nc);
+  build_plan_items(p, 0, it0, keys, s);
+  sort_items(it0, keys, nc, p->items, scratch, s);
+  BST_CUDA(cudaStreamSynchronize(s));
+  scratch.release_all();
+}
+
+// The numeric schedule of a plan: the staged kernel's, else the direct-load kernel's
+void build_f64_schedule(bst_plan *p, cudaStream_t s) {
+  if (!build_staged(p, s)) build_cost_items(p, s);
 }
 
 // the staged kernel's tiles of a plan for a batch (item = base | tile) and their keys

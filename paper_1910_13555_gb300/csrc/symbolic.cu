@@ -632,16 +632,7 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
     k_emit_stacks<<<nblk(T, 256), 256, 0, s>>>(E);
     BST_CHECK_LAUNCH();
   }
-  // persistent numeric schedule: C blocks by decreasing cost (FP64 balances better
-  // this way than in CSR order)
-  {
-    int64_t *it0 = scratch.alloc_n<int64_t>((size_t)nnzC);
-    int32_t *keys = scratch.alloc_n<int32_t>((size_t)nnzC);
-    p->items = ar.alloc_n<int64_t>((size_t)nnzC);
-    p->items_counter = ar.alloc_n<unsigned long long>(1);
-    build_plan_items(p, 0, it0, keys, s);
-    sort_items(it0, keys, nnzC, p->items, scratch, s);
-  }
+  p->items_counter = ar.alloc_n<unsigned long long>(1);
   unsigned long long *refel = scratch.alloc_n<unsigned long long>(2);
   BST_CUDA(cudaMemsetAsync(refel, 0, 16, s));
   if (A->nblocks > 0) {
