@@ -123,6 +123,8 @@ bst_status bst_matrix_info(const bst_matrix *m, int32_t *nbr, int32_t *nbc, int6
 bst_status bst_matrix_get_index(const bst_matrix *m, int32_t *blk_row, int32_t *blk_col,
                                 int64_t *blk_off);
 bst_status bst_matrix_bind_data(bst_matrix *m, double *data);
+/* Number of doubles the matrix's data buffer holds (the packed block elements). */
+bst_status bst_matrix_data_size(const bst_matrix *m, int64_t *n_elements);
 bst_status bst_matrix_destroy(bst_matrix *m);
 
 /* Block post-filter (paper Sec. 2: chained products such as the sign-matrix iteration
@@ -221,6 +223,9 @@ size_t bst_static_scratch_doubles(void);
  * C_out.  For a contraction plan the buffers are the tensors' packings.  FP64. */
 bst_status bst_plan_adjoint(bst_plan *plan, const double *dC, double *dA, double *dB,
                             double *dC_in, double alpha, double beta, void *stream);
+/* The same without a C_in gradient: bst_plan_adjoint(plan, dC, dA, dB, NULL, alpha, 0). */
+bst_status bst_multiply_adjoint(bst_plan *plan, const double *dC, double *dA, double *dB,
+                                double alpha, void *stream);
 
 bst_status bst_plan_destroy(bst_plan *plan);
 

@@ -63,6 +63,8 @@ _SIGS = {
     "bst_matrix_get_index": ([_VP, _VP, _VP, _VP], C.c_int32),
     "bst_matrix_bind_data": ([_VP, _VP], C.c_int32),
     "bst_matrix_destroy": ([_VP], C.c_int32),
+    "bst_matrix_data_size": ([_VP, _VP], C.c_int32),
+    "bst_multiply_adjoint": ([_VP, _VP, _VP, _VP, C.c_double, _VP], C.c_int32),
     "bst_matrix_filter": ([_VP, _VP, C.c_double, _VP, C.POINTER(_VP)], C.c_int32),
     "bst_matrix_filter_copy": ([_VP, _VP, _VP], C.c_int32),
     "bst_multiply_plan": ([_VP, C.c_char, C.c_char, _VP, _VP, _VP, C.c_double, _VP,
@@ -195,6 +197,17 @@ def bst_matrix_bind_data(m, data):
 
 def bst_matrix_destroy(m):
     _check(load().bst_matrix_destroy(m), "bst_matrix_destroy")
+
+
+def bst_matrix_data_size(m) -> int:
+    v = C.c_int64()
+    _check(load().bst_matrix_data_size(m, C.byref(v)), "bst_matrix_data_size")
+    return v.value
+
+
+def bst_multiply_adjoint(plan, dC, dA, dB, alpha=1.0, stream=None):
+    _check(load().bst_multiply_adjoint(plan, _ptr(dC), _ptr(dA), _ptr(dB), float(alpha),
+                                       _stream(stream)), "bst_multiply_adjoint")
 
 
 def bst_matrix_filter(ctx, X, eps, stream=None):

@@ -253,6 +253,13 @@ bst_status bst_matrix_info(const bst_matrix *m, int32_t *nbr, int32_t *nbc, int6
   API_END
 }
 
+bst_status bst_matrix_data_size(const bst_matrix *m, int64_t *n_elements) {
+  API_BEGIN
+  BST_REQUIRE(m && n_elements, BST_ERR_INVALID_ARG, "NULL argument");
+  *n_elements = m->nelem;
+  API_END
+}
+
 bst_status bst_matrix_get_index(const bst_matrix *m, int32_t *blk_row, int32_t *blk_col,
                                 int64_t *blk_off) {
   API_BEGIN
@@ -447,6 +454,11 @@ bst_status bst_plan_adjoint(bst_plan *plan, const double *dC, double *dA, double
   bst::adjoint_fp64(plan, plan->A->data, plan->B->data, dC, dA, dB, alpha, s);
   bst::scale_cin_grad(plan, dC, dC_in, beta, s);
   API_END
+}
+
+bst_status bst_multiply_adjoint(bst_plan *plan, const double *dC, double *dA, double *dB,
+                                double alpha, void *stream) {
+  return bst_plan_adjoint(plan, dC, dA, dB, nullptr, alpha, 0.0, stream);
 }
 
 bst_status bst_tune_set(bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t value) {

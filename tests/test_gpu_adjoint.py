@@ -104,3 +104,19 @@ def test_autograd_matches_adjoint_and_fd():
                 fd = (lp - lm) / (2 * h)
                 gv = float(g[e])
                 assert abs(fd - gv) <= 1e-7 * max(1, abs(gv)) + 8 * 2.0 ** -52 * L / h
+
+
+def test_multiply_adjoint_equals_plan_adjoint_without_cin():
+    import torch
+    p = _mixed(41, cin=False)
+    A, B = to_lib(p.A), to_lib(p.B)
+    plan = bst.multiply(A, B, None, p.alpha, 0.0, p.eps, p.transa, p.transb)
+    assert bst.bst_matrix_data_size(plan.result.handle) == plan.result.info[3]
+    assert bst.bst_matrix_data_size(A.handle) == len(p.A.data)
+    g = torch.randn(plan.result.info[3], dtype=torch.float64, device="cuda")
+    dA1, dB1 = torch.empty_like(A.data), torch.empty_like(B.data)
+    dA2, dB2 = torch.empty_like(A.data), torch.empty_like(B.data)
+    bst.bst_plan_adjoint(plan.handle, g, dA1, dB1, None, p.alpha, 0.0)
+    bst.bst_multiply_adjoint(plan.handle, g, dA2, dB2, p.alpha)
+    torch.cuda.synchronize()
+    assert torch.equal(dA1, dA2) and torch.equal(dB1, dB2)
