@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the precision-variant legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-cpu-parallel", action="store_true",
+                    help="skip the multi-process leg of the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads (tiny, tall-skinny, batched, rank-3)")
@@ -189,6 +191,61 @@ def cpu_baseline(p, rows, steps=1):
         times.append(time.perf_counter() - t)
         flops = res["flops"]
     return flops, times
+
+
+def _oracle_rows_worker(seed, nb, r0, r1, barrier, queue):
+    """One process of the parallel CPU baseline: the oracle on block rows [r0, r1) of A
+    (its own copy of the workload, built before the common start)."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import oracle
+    from paper_1910_13555_gb300.workloads import BSMatrix, banded
+    p = banded(seed=seed, nb=nb)
+    sel = (p.A.rows >= r0) & (p.A.rows < r1)
+    offs, lens = p.A.offsets, p.A.block_lens
+    idx = np.concatenate([np.arange(offs[b], offs[b] + lens[b]) for b in np.nonzero(sel)[0]])
+    A2 = BSMatrix(p.A.row_sizes, p.A.col_sizes, p.A.rows[sel], p.A.cols[sel], p.A.data[idx])
+    barrier.wait(timeout=600)
+    t0 = time.time()
+    res = oracle.multiply(A2, p.B, None, 1.0, 0.0, p.eps)
+    queue.put((res["flops"], t0, time.time()))
+
+
+def cpu_baseline_parallel(seed, nb, rows, workers):
+    """The oracle, as it stands, in `workers` processes over disjoint ranges of block rows
+    of A (the parallel leg of the CPU baseline); wall time from the common start to the
+    last finish."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(workers), ctx.Queue()
+    bounds = np.linspace(rows[0], rows[1], workers + 1).astype(int)
+    procs = [ctx.Process(target=_oracle_rows_worker,
+                         args=(seed, nb, int(bounds[i]), int(bounds[i + 1]), barrier, queue))
+             for i in range(workers)]
+    for pr in procs:
+        pr.start()
+    out, deadline = [], time.time() + 900
+    try:
+        while len(out) < workers:
+            try:
+                out.append(queue.get(timeout=1.0))
+            except Exception:
+                bad = [pr.exitcode for pr in procs if pr.exitcode not in (None, 0)]
+                if bad or time.time() > deadline:
+                    raise RuntimeError(f"parallel oracle baseline failed (exit codes {bad})")
+    finally:
+        for pr in procs:
+            pr.join(timeout=5)
+            if pr.is_alive():
+                pr.terminate()
+    flops = sum(o[0] for o in out)
+    return flops, max(o[2] for o in out) - min(o[1] for o in out)
 
 
 def run_reference(args):
@@ -452,6 +509,13 @@ def run_ours(args):
             "value": fl / times[0] / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"block rows {rows[0]}..{rows[1]} of A times all of B "
                       f"({fl:.3e} flop, {times[0]:.1f} s, single thread)"}
+        if not args.no_cpu_parallel:
+            ncores = min(len(os.sched_getaffinity(0)), 64)
+            flp, tp = cpu_baseline_parallel(rank_seed(rank), args.nb, (0, args.nb), ncores)
+            line["cpu_baseline_parallel"] = {
+                "value": flp / tp / 1e9, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                "sample": f"all {args.nb} block rows of A times B, one process per core over "
+                          f"disjoint block rows ({flp:.3e} flop, {tp:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
