@@ -181,6 +181,13 @@ bst_status bst_plan_stats(const bst_plan *plan, bst_stats *out);
 bst_status bst_plan_get_stacks(const bst_plan *plan, int32_t *mnk, int64_t *bucket_ptr,
                                int32_t *a_off, int32_t *b_off, int32_t *c_off);
 
+/* Work units of the native-FP64 staged kernel: hist[s] (s = 1..16) = row tiles of C
+ * whose inner dimension is split over s lane groups (choice of BST_TUNE_F64_SPLIT and
+ * the built-in cost rule, as of the last execute or plan build); hist[0] = C blocks
+ * run by the direct-load kernel instead (plans whose blocks do not fit the staged
+ * tiles).  hist has 17 entries.  Synchronises. */
+bst_status bst_plan_split_histogram(const bst_plan *plan, int64_t *hist);
+
 /* Arithmetic used by execute. */
 enum {
   BST_FP64 = 0,          /* native FP64 FMA                                        */
@@ -240,10 +247,19 @@ bst_status bst_plan_destroy(bst_plan *plan);
  *     kernel; 0 = the 16-row MMA tiles run over the C block's rows, 1 = over its columns
  *     (C^T = op(B)^T op(A)^T on the same digit planes, fewer tiles when n > m);
  *     -1 = back to the built-in rule (fewer 16 x 8 tiles wins).  Row-scaled mode only.
+ *   BST_TUNE_F64_SPLIT (per (m, n) C block class): the largest number of lane groups
+ *     over which the native-FP64 staged kernel may split the inner dimension of one
+ *     C tile (1 = never split; 2..16); -1 = back to the built-in bound.  Within the
+ *     bound each tile takes the split that needs the fewest FP64 instructions, and
+ *     only when that saves at least 1/16 of them; the s partial sums of an output are
+ *     added in a fixed order, so results stay deterministic.
  * Changing a choice takes effect at the next execute of a plan; a batch built before
  * the change refuses emulated-FP64 execution (BST_ERR_STATE) and must be created again.
+ * A plan or batch whose native-FP64 tiles must be split again after a change returns
+ * BST_ERR_STATE when that execute is being captured into a CUDA graph: execute it once
+ * outside capture first.
  * Errors: INVALID_ARG for an unknown key or value. */
-enum { BST_TUNE_EMU_ROW_SCALE = 0, BST_TUNE_EMU_SWAP = 1 };
+enum { BST_TUNE_EMU_ROW_SCALE = 0, BST_TUNE_EMU_SWAP = 1, BST_TUNE_F64_SPLIT = 2 };
 bst_status bst_tune_set(bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t value);
 bst_status bst_tune_get(const bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t *value);
 

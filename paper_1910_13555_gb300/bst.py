@@ -72,6 +72,7 @@ _SIGS = {
     "bst_plan_result": ([_VP, C.POINTER(_VP)], C.c_int32),
     "bst_plan_stats": ([_VP, C.POINTER(bst_stats)], C.c_int32),
     "bst_plan_get_stacks": ([_VP, _VP, _VP, _VP, _VP, _VP], C.c_int32),
+    "bst_plan_split_histogram": ([_VP, _VP], C.c_int32),
     "bst_multiply_execute": ([_VP, C.c_double, C.c_double, C.c_int32, C.c_int32, _VP], C.c_int32),
     "bst_multiply_execute_static": ([_VP, C.c_double, C.c_double, C.c_int32, _VP], C.c_int32),
     "bst_static_scratch_doubles": ([], C.c_size_t),
@@ -240,6 +241,13 @@ def bst_plan_stats(plan) -> dict:
     return s.as_dict()
 
 
+def bst_plan_split_histogram(plan) -> np.ndarray:
+    """hist[s]: staged FP64 tiles split over s lane groups; hist[0]: direct-load blocks."""
+    h = np.zeros(17, np.int64)
+    _check(load().bst_plan_split_histogram(plan, _ptr(h)), "bst_plan_split_histogram")
+    return h
+
+
 def bst_plan_get_stacks(plan):
     st = bst_plan_stats(plan)
     nb, ns = st["n_buckets"], st["n_stack"]
@@ -280,6 +288,7 @@ def bst_plan_destroy(plan):
 
 BST_TUNE_EMU_ROW_SCALE = 0
 BST_TUNE_EMU_SWAP = 1
+BST_TUNE_F64_SPLIT = 2
 
 
 def bst_tune_set(ctx, key, value, m=0, n=0):
@@ -419,6 +428,9 @@ class Plan:
 
     def stacks(self):
         return bst_plan_get_stacks(self.handle)
+
+    def split_histogram(self):
+        return bst_plan_split_histogram(self.handle)
 
     def alloc_result(self, device=0):
         import torch

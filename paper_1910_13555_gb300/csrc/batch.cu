@@ -197,14 +197,19 @@ bst_status bst_batch_execute(bst_batch *b, const double *alpha, const double *be
     BST_REQUIRE(precision == BST_FP64 || b->tune_version == b->ctx->tune_version, BST_ERR_STATE,
                 "the context's tuning changed after the batch was created; create it again");
     if (precision == BST_FP64) {
+      bool split = false;
       for (int32_t q = 0; q < n; ++q) {
+        if (b->stage_elems > 0) {
+          bst::refresh_f64_split(b->plans[q], s);
+          split = split || b->plans[q]->stage_split;
+        }
         Args r = plan_args(b->plans[q], alpha[q], beta[q], s);
         bst::fill_num_params(b->plans[q], r.a, static_cast<char *>(b->h_params) + q * b->pbytes);
       }
       BST_CUDA(cudaMemcpyAsync(b->d_params, b->h_params, b->pbytes * n, cudaMemcpyHostToDevice, s));
       if (b->stage_elems > 0)
         bst::launch_fp64_staged(b->d_params, b->titems, b->n_titems, b->stage_elems,
-                                b->stage_strided, b->ctx->num_sms, s);
+                                b->stage_strided, split, b->ctx->num_sms, s);
       else
         bst::launch_fp64_persist(b->d_params, b->items, b->n_items, b->counter, b->grid, s);
     } else {

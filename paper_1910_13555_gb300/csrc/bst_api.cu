@@ -360,6 +360,22 @@ bst_status bst_plan_stats(const bst_plan *plan, bst_stats *out) {
   API_END
 }
 
+bst_status bst_plan_split_histogram(const bst_plan *plan, int64_t *hist) {
+  API_BEGIN
+  BST_REQUIRE(plan && hist, BST_ERR_INVALID_ARG, "NULL argument");
+  use_device(plan->ctx);
+  for (int s = 0; s <= 16; ++s) hist[s] = 0;
+  if (plan->n_tiles > 0) {
+    std::vector<int32_t> w((size_t)plan->n_tiles);
+    BST_CUDA(cudaMemcpy2D(w.data(), 4, plan->fdesc + 7, 4 * bst::kF64DescWords, 4,
+                          (size_t)plan->n_tiles, cudaMemcpyDeviceToHost));
+    for (int32_t v : w) ++hist[std::min(std::max(v, 1), 16)];
+  } else if (plan->C) {
+    hist[0] = plan->C->nblocks;
+  }
+  API_END
+}
+
 bst_status bst_plan_get_stacks(const bst_plan *plan, int32_t *mnk, int64_t *bucket_ptr,
                                int32_t *a_off, int32_t *b_off, int32_t *c_off) {
   API_BEGIN
@@ -477,6 +493,15 @@ bst_status bst_tune_set(bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t
       else
         ctx->tune_emu_swap[{m, n}] = value;
       break;
+    case BST_TUNE_F64_SPLIT:
+      BST_REQUIRE(value == -1 || (value >= 1 && value <= 16), BST_ERR_INVALID_ARG,
+                  "value must be -1 or 1..16");
+      BST_REQUIRE(m >= 1 && n >= 1, BST_ERR_INVALID_ARG, "m and n must be >= 1");
+      if (value < 0)
+        ctx->tune_f64_split.erase({m, n});
+      else
+        ctx->tune_f64_split[{m, n}] = value;
+      break;
     default:
       throw Error{BST_ERR_INVALID_ARG, "unknown tuning key"};
   }
@@ -494,6 +519,11 @@ bst_status bst_tune_get(const bst_ctx *ctx, int32_t key, int32_t m, int32_t n, i
     case BST_TUNE_EMU_SWAP: {
       auto it = ctx->tune_emu_swap.find({m, n});
       *value = it == ctx->tune_emu_swap.end() ? -1 : it->second;
+      break;
+    }
+    case BST_TUNE_F64_SPLIT: {
+      auto it = ctx->tune_f64_split.find({m, n});
+      *value = it == ctx->tune_f64_split.end() ? -1 : it->second;
       break;
     }
     default:

@@ -89,6 +89,9 @@ struct bst_ctx {
   // tune_version changes whenever a choice does
   int tune_emu_row_scale = 1;
   std::map<std::pair<int32_t, int32_t>, int32_t> tune_emu_swap;
+  // per (m, n) C block class, the largest inner split of the staged FP64 kernel's tiles
+  // (1 = none); classes without an entry use the built-in bound
+  std::map<std::pair<int32_t, int32_t>, int32_t> tune_f64_split;
   int64_t tune_version = 0;
 };
 
@@ -263,6 +266,8 @@ struct bst_plan {
   bool stage_strided = false;  // some tile or panel is a strided part of a block
   int64_t *titems = nullptr;   // tiles by decreasing cost
   int32_t *tkeys = nullptr;    // each tile's cost key
+  int64_t split_version = -1;  // tune_version the tiles' inner splits were chosen for
+  bool stage_split = false;    // some tile splits its inner dimension
   // stats
   bst_stats stats{};
   // emulated-precision state (numeric_emu.cu), built on first use
@@ -313,10 +318,12 @@ int persist_grid(int num_sms);
 void launch_fp64_persist(const void *params, const int64_t *items, int64_t nitems,
                          unsigned long long *counter, int grid, cudaStream_t s);
 void build_f64_schedule(bst_plan *p, cudaStream_t s);
+void refresh_f64_split(bst_plan *p, cudaStream_t s);
+constexpr int kF64DescWords = 8;  // descriptor words per staged tile
 void build_plan_tile_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys,
                            cudaStream_t s);
 void launch_fp64_staged(const void *params, const int64_t *items, int64_t nitems,
-                        int slot_elems, bool strided, int num_sms, cudaStream_t s);
+                        int slot_elems, bool strided, bool split, int num_sms, cudaStream_t s);
 // persistent emulated-FP64 numeric (numeric_emu.cu)
 size_t emu_params_bytes();
 int64_t emu_item_count(bst_plan *p, cudaStream_t s);

@@ -286,14 +286,14 @@ constexpr int kMaxR = 17;         // accumulators per lane: tiles up to 544 elem
 constexpr int kTile = 32 * kMaxR;
 constexpr int kStageMax = 1536;   // doubles per slot (two slots per warp)
 constexpr int kStageWarps = 4;    // warps per CTA
-constexpr int kF64Desc = 8;       // descriptor words per C block
+constexpr int kF64Desc = kF64DescWords;
 
 // Work unit: a row tile of a C block (the whole block when it has at most 32 * kMaxR
 // elements).  Descriptor: 0 element offset of the tile in C, 1 first entry, 2 entry
 // count, 3 tile rows m | n << 12, 4 C_in block (-1: none), 5 element offset of the tile
-// inside the C_in block, 6 C block.
+// inside the C_in block, 6 C block, 7 inner split s (>= 1).
 struct F64Blk {
-  int off, eb, ne, m, n, cin, cio;
+  int off, eb, ne, m, n, cin, cio, s;
 };
 
 __device__ __forceinline__ F64Blk f64_blk(int dw) {
@@ -304,6 +304,7 @@ __device__ __forceinline__ F64Blk f64_blk(int dw) {
   const int mn = __shfl_sync(0xffffffffu, dw, 3);
   b.cin = __shfl_sync(0xffffffffu, dw, 4);
   b.cio = __shfl_sync(0xffffffffu, dw, 5);
+  b.s = max(__shfl_sync(0xffffffffu, dw, 7), 1);
   b.m = mn & 0xfff;
   b.n = (mn >> 12) & 0xfff;
   return b;
@@ -411,6 +412,71 @@ __device__ __forceinline__ void slot_product_rt(const NumParams &P, const double
   }
 }
 
+// The inner dimension split s ways over the lanes, for tiles whose m n leaves lanes idle
+// (65 outputs on 3 x 32 lanes): virtual output v = lane + 32 r = g m n + o (o = p n + q)
+// accumulates op(A)(p, l) op(B)(l, q) over l = g, g + s, g + 2s, ... < k.  The s partial
+// sums of an output are added once, at the end of the tile (split_reduce).
+__device__ __forceinline__ void slot_product_split(const NumParams &P,
+                                                   const double *__restrict__ As, int m, int n,
+                                                   int k, int s, double (&acc)[kMaxR]) {
+  const int lane = threadIdx.x & 31, nv = s * m * n;
+  const double *__restrict__ Bs = As + m * k;
+  const int a_sp = P.ta ? 1 : k, a_sl = P.ta ? m : 1;
+  const int b_sl = P.tb ? 1 : n, b_sq = P.tb ? k : 1;
+  const int mn = m * n;
+  int g = lane / mn;
+  const int o = lane - g * mn;
+  int p = o / n, q = o - p * n;
+  const int dp = 32 / n, dq = 32 - dp * n;
+  const int da = s * a_sl, db = s * b_sl;
+#pragma unroll
+  for (int r = 0; r < kMaxR; ++r) {
+    if (32 * r >= nv) break;
+    if (lane + 32 * r < nv) {
+      const double *a = As + p * a_sp + g * a_sl, *b = Bs + q * b_sq + g * b_sl;
+      double t = acc[r];
+#pragma unroll 1
+      for (int l = g; l < k; l += s) {
+        t = fma(*a, *b, t);
+        a += da;
+        b += db;
+      }
+      acc[r] = t;
+    }
+    // the virtual output 32 further on
+    p += dp;
+    q += dq;
+    if (q >= n) {
+      q -= n;
+      ++p;
+    }
+    while (p >= m) {
+      p -= m;
+      ++g;
+    }
+  }
+}
+
+// acc[r] <- sum over g = 0 .. s - 1 (in that order) of the partial sums of output
+// o = lane + 32 r, through `red` (s m n doubles of a free slot)
+__device__ __forceinline__ void split_reduce(double *red, int mn, int s, double (&acc)[kMaxR]) {
+  const int lane = threadIdx.x & 31, nv = s * mn;
+#pragma unroll
+  for (int r = 0; r < kMaxR; ++r)
+    if (lane + 32 * r < nv) red[lane + 32 * r] = acc[r];
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < kMaxR; ++r) {
+    const int o = lane + 32 * r;
+    if (o < mn) {
+      double t = red[o];
+      for (int g = 1; g < s; ++g) t += red[g * mn + o];
+      acc[r] = t;
+    }
+  }
+  __syncwarp();
+}
+
 template <int M, int N>
 __device__ __forceinline__ void slot_product_k(const NumParams &P, const double *As, int k,
                                                double (&acc)[kMaxR]) {
@@ -462,7 +528,7 @@ __device__ __forceinline__ void store_block(const NumParams &P, const F64Blk &b,
   }
 }
 
-template <bool STRIDED, class GetP>
+template <bool STRIDED, bool SPLIT, class GetP>
 __device__ __forceinline__ void staged_loop(const int64_t *__restrict__ items, int64_t nitems,
                                             int slot_elems, GetP get) {
   extern __shared__ double smem_stage[];
@@ -535,11 +601,16 @@ __device__ __forceinline__ void staged_loop(const int64_t *__restrict__ items, i
       cp_commit();
       cp_wait_prev();
       __syncwarp();
-      slot_dispatch(P, slots + slot * slot_elems, b.m, b.n, k, acc);
+      if (SPLIT && b.s > 1)
+        slot_product_split(P, slots + slot * slot_elems, b.m, b.n, k, b.s, acc);
+      else
+        slot_dispatch(P, slots + slot * slot_elems, b.m, b.n, k, acc);
       __syncwarp();
       slot ^= 1;
     }
     staged = b.ne > 0 && vn >= 0 && bn.ne > 0;
+    // the slot of the tile's last job is free: the next tile's first job went to the other
+    if (SPLIT && b.s > 1 && b.ne > 0) split_reduce(slots + (slot ^ 1) * slot_elems, b.m * b.n, b.s, acc);
     store_block(P, b, acc);
     if (vn < 0) break;
     it += nw;
@@ -553,21 +624,24 @@ __device__ __forceinline__ void staged_loop(const int64_t *__restrict__ items, i
   cp_wait_all();
 }
 
-// STRIDED: the plan has row tiles or inner panels (staging copies strided rows)
-template <bool STRIDED>
+// STRIDED: the plan has row tiles or inner panels (staging copies strided rows);
+// SPLIT: some tile spreads its inner dimension over lane groups.  Each is a separate
+// instance so that plans without them run none of their code (a larger loop body costs
+// instruction-fetch stalls on every tile).
+template <bool STRIDED, bool SPLIT>
 __global__ void __launch_bounds__(32 * kStageWarps, 3)
     k_num_fp64_staged1(NumParams P, const int64_t *__restrict__ items, int64_t nitems,
                        int slot_elems) {
-  staged_loop<STRIDED>(items, nitems, slot_elems,
-                       [&](int64_t) -> const NumParams & { return P; });
+  staged_loop<STRIDED, SPLIT>(items, nitems, slot_elems,
+                              [&](int64_t) -> const NumParams & { return P; });
 }
 
-template <bool STRIDED>
+template <bool STRIDED, bool SPLIT>
 __global__ void __launch_bounds__(32 * kStageWarps, 3)
     k_num_fp64_staged(const NumParams *__restrict__ plans, const int64_t *__restrict__ items,
                       int64_t nitems, int slot_elems) {
-  staged_loop<STRIDED>(items, nitems, slot_elems,
-                       [&](int64_t pl) -> const NumParams & { return plans[pl]; });
+  staged_loop<STRIDED, SPLIT>(items, nitems, slot_elems,
+                              [&](int64_t pl) -> const NumParams & { return plans[pl]; });
 }
 
 // ---- schedule of the staged kernel (built with the plan) ----------------------------
@@ -661,6 +735,69 @@ __global__ void k_f64_tiles(int64_t nc, const int32_t *__restrict__ c_cls,
     d[7] = 0;
     key[tile] = __clzll(flops + 1ull);
   }
+}
+
+// Inner split of every tile (descriptor word 7): the s <= smax of the tile's class that
+// needs the fewest FP64 warp instructions -- ceil(s mt n / 32) for each of the
+// ceil(w / s) steps of a panel of width w, plus (s - 1) ceil(mt n / 32) adds for the
+// final sums -- when it saves at least 1/8 of the unsplit count on a tile with at least
+// kSplitMinInner inner elements in all (on shorter tiles the final sums cost more than
+// the idle lanes), else 1.  The plan-wide sums of the unsplit counts and of the savings
+// decide whether the plan splits at all (refresh_f64_split).
+constexpr int kMaxSplit = 16;
+constexpr int kSplitMinInner = 48;
+
+__device__ int f64_split_of(int32_t *__restrict__ d, const int4 *__restrict__ ents, int smax,
+                            long long &c1, long long &saved) {
+  const int mn = (d[3] & 0xfff) * ((d[3] >> 12) & 0xfff), ne = d[2];
+  smax = min(min(smax, kMaxSplit), kTile / max(mn, 1));
+  const long long v1 = (mn + 31) / 32;
+  int best = 1;
+  c1 = 0;
+  saved = 0;
+  long long W[kMaxSplit + 1];
+  for (int s = 1; s <= max(smax, 1); ++s) W[s] = 0;
+  for (int e = 0; e < ne; ++e) {
+    const int w = ents[(int64_t)d[1] + e].z;
+    for (int s = 1; s <= max(smax, 1); ++s) W[s] += (w + s - 1) / s;
+  }
+  c1 = v1 * W[1];
+  long long cb = c1;
+  for (int s = 2; s <= smax; ++s) {
+    const long long c = (long long)((s * mn + 31) / 32) * W[s] + (s - 1) * v1;
+    if (c < cb) {
+      cb = c;
+      best = s;
+    }
+  }
+  if (8 * cb > 7 * c1 || W[1] < kSplitMinInner) best = 1;
+  if (best > 1) saved = c1 - cb;
+  return best;
+}
+
+// sums[0] += unsplit FP64 instruction counts, sums[1] += savings of the chosen splits
+__global__ void k_f64_split(int64_t ntiles, const int4 *__restrict__ ents,
+                            const int32_t *__restrict__ c_cls, const int32_t *__restrict__ cls_smax,
+                            int32_t *__restrict__ desc, unsigned long long *__restrict__ sums) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  long long c1 = 0, saved = 0;
+  if (t < ntiles) {
+    int32_t *d = desc + t * kF64Desc;
+    d[7] = f64_split_of(d, ents, cls_smax[c_cls[d[6]]], c1, saved);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    c1 += __shfl_down_sync(0xffffffffu, c1, o);
+    saved += __shfl_down_sync(0xffffffffu, saved, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sums[0], (unsigned long long)c1);
+    atomicAdd(&sums[1], (unsigned long long)saved);
+  }
+}
+
+__global__ void k_f64_nosplit(int64_t ntiles, int32_t *__restrict__ desc) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < ntiles) desc[t * kF64Desc + 7] = 1;
 }
 
 __global__ void k_plan_items(int64_t nc, int64_t base, int64_t *__restrict__ item) {
@@ -870,7 +1007,51 @@ static bool build_staged(bst_plan *p, cudaStream_t s) {
   p->n_tiles = ntiles;
   p->stage_elems = (int32_t)slot;
   p->stage_strided = strided;
+  p->split_version = -1;
+  refresh_f64_split(p, s);
   return true;
+}
+
+// (Re)choose the inner split of every staged tile for the context's current tuning.
+void refresh_f64_split(bst_plan *p, cudaStream_t s) {
+  Ctx *ctx = static_cast<Ctx *>(p->ctx);
+  if (p->n_tiles == 0 || p->split_version == ctx->tune_version) return;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  BST_CUDA(cudaStreamIsCapturing(s, &cap));
+  BST_REQUIRE(cap == cudaStreamCaptureStatusNone, BST_ERR_STATE,
+              "the context's tuning changed since the plan's FP64 tiles were split; "
+              "execute once outside stream capture");
+  const int32_t ncls = p->Dm * p->Dn;
+  std::vector<int32_t> smax((size_t)ncls, kMaxSplit);
+  for (int32_t c = 0; c < ncls; ++c) {
+    auto it = ctx->tune_f64_split.find({(int32_t)p->m_vals[c / p->Dn], (int32_t)p->n_vals[c % p->Dn]});
+    if (it != ctx->tune_f64_split.end()) smax[(size_t)c] = it->second;
+  }
+  Arena scratch;
+  scratch.ctx = ctx;
+  scratch.stream = s;
+  int32_t *d_smax = scratch.alloc_n<int32_t>((size_t)ncls);
+  unsigned long long *d_sums = scratch.alloc_n<unsigned long long>(2);
+  BST_CUDA(cudaMemcpyAsync(d_smax, smax.data(), 4 * (size_t)ncls, cudaMemcpyHostToDevice, s));
+  BST_CUDA(cudaMemsetAsync(d_sums, 0, 2 * sizeof(unsigned long long), s));
+  k_f64_split<<<nblk(p->n_tiles, 128), 128, 0, s>>>(p->n_tiles, p->fents, p->c_cls, d_smax,
+                                                   p->fdesc, d_sums);
+  BST_CHECK_LAUNCH();
+  unsigned long long sums[2] = {0, 0};
+  {
+    ReadBack rb(p->ctx, s);
+    rb.add(sums, d_sums, sizeof(sums));
+    rb.done();
+  }
+  // The kernel instance with the split body runs every tile a few per cent slower
+  // (a longer loop body, more instruction-fetch stalls), so a plan splits only when the
+  // chosen splits save at least 1/25 of all its FP64 instructions.
+  p->stage_split = sums[1] > 0 && 25 * sums[1] >= sums[0];
+  if (!p->stage_split) {
+    k_f64_nosplit<<<nblk(p->n_tiles, 256), 256, 0, s>>>(p->n_tiles, p->fdesc);
+    BST_CHECK_LAUNCH();
+  }
+  p->split_version = ctx->tune_version;
 }
 
 // C blocks by decreasing cost, for the direct-load persistent kernel
@@ -919,23 +1100,32 @@ static int staged_ctas_per_sm(K kernel, bool &attr_set, int slot_elems, size_t &
   return std::max(1, nb);
 }
 
-static bool g_attr[4] = {false, false, false, false};
-
-void launch_fp64_staged(const void *params, const int64_t *items, int64_t nitems,
-                        int slot_elems, bool strided, int num_sms, cudaStream_t s) {
-  if (nitems == 0) return;
+// one launch of a staged kernel instance: as many CTAs as fit (all resident), at most
+// one warp per work item
+template <class K, class Arg>
+static void staged_launch(K kernel, bool &attr_set, Arg params, const int64_t *items,
+                          int64_t nitems, int slot_elems, int num_sms, cudaStream_t s) {
   size_t smem = 0;
-  const int per = strided
-                      ? staged_ctas_per_sm(k_num_fp64_staged<true>, g_attr[0], slot_elems, smem)
-                      : staged_ctas_per_sm(k_num_fp64_staged<false>, g_attr[1], slot_elems, smem);
+  const int per = staged_ctas_per_sm(kernel, attr_set, slot_elems, smem);
   const int g = (int)std::min<int64_t>((int64_t)per * num_sms,
                                        (nitems + kStageWarps - 1) / kStageWarps);
-  const NumParams *P = static_cast<const NumParams *>(params);
-  if (strided)
-    k_num_fp64_staged<true><<<g, 32 * kStageWarps, smem, s>>>(P, items, nitems, slot_elems);
-  else
-    k_num_fp64_staged<false><<<g, 32 * kStageWarps, smem, s>>>(P, items, nitems, slot_elems);
+  kernel<<<g, 32 * kStageWarps, smem, s>>>(params, items, nitems, slot_elems);
   BST_CHECK_LAUNCH();
+}
+
+static bool g_attr[2][4] = {};  // [batch, single plan][strided | split << 1]
+
+void launch_fp64_staged(const void *params, const int64_t *items, int64_t nitems,
+                        int slot_elems, bool strided, bool split, int num_sms, cudaStream_t s) {
+  if (nitems == 0) return;
+  const NumParams *P = static_cast<const NumParams *>(params);
+  const int v = (strided ? 1 : 0) | (split ? 2 : 0);
+  switch (v) {
+    case 0: staged_launch(k_num_fp64_staged<false, false>, g_attr[0][v], P, items, nitems, slot_elems, num_sms, s); break;
+    case 1: staged_launch(k_num_fp64_staged<true, false>, g_attr[0][v], P, items, nitems, slot_elems, num_sms, s); break;
+    case 2: staged_launch(k_num_fp64_staged<false, true>, g_attr[0][v], P, items, nitems, slot_elems, num_sms, s); break;
+    default: staged_launch(k_num_fp64_staged<true, true>, g_attr[0][v], P, items, nitems, slot_elems, num_sms, s); break;
+  }
 }
 
 int persist_grid(int num_sms) {
@@ -977,21 +1167,17 @@ void execute_fp64(bst_plan *p, const NumArgs &a, int split, cudaStream_t s) {
   const int64_t nc = p->C->nblocks;
   if (nc == 0) return;
   if (split <= 1 && p->stage_elems > 0) {
-    size_t smem = 0;
-    const bool st = p->stage_strided;
-    const int per =
-        st ? staged_ctas_per_sm(k_num_fp64_staged1<true>, g_attr[2], p->stage_elems, smem)
-           : staged_ctas_per_sm(k_num_fp64_staged1<false>, g_attr[3], p->stage_elems, smem);
-    const int g = (int)std::min<int64_t>((int64_t)per * p->ctx->num_sms,
-                                         (p->n_tiles + kStageWarps - 1) / kStageWarps);
+    refresh_f64_split(p, s);
     const NumParams P = make_params(p, a, 1);
-    if (st)
-      k_num_fp64_staged1<true><<<g, 32 * kStageWarps, smem, s>>>(P, p->titems, p->n_tiles,
-                                                                 p->stage_elems);
-    else
-      k_num_fp64_staged1<false><<<g, 32 * kStageWarps, smem, s>>>(P, p->titems, p->n_tiles,
-                                                                  p->stage_elems);
-    BST_CHECK_LAUNCH();
+    const int v = (p->stage_strided ? 1 : 0) | (p->stage_split ? 2 : 0);
+    const int ns = p->ctx->num_sms, se = p->stage_elems;
+    const int64_t nt = p->n_tiles;
+    switch (v) {
+      case 0: staged_launch(k_num_fp64_staged1<false, false>, g_attr[1][v], P, p->titems, nt, se, ns, s); break;
+      case 1: staged_launch(k_num_fp64_staged1<true, false>, g_attr[1][v], P, p->titems, nt, se, ns, s); break;
+      case 2: staged_launch(k_num_fp64_staged1<false, true>, g_attr[1][v], P, p->titems, nt, se, ns, s); break;
+      default: staged_launch(k_num_fp64_staged1<true, true>, g_attr[1][v], P, p->titems, nt, se, ns, s); break;
+    }
     return;
   }
   if (split <= 1 && p->items) {

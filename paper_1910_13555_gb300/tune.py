@@ -1,13 +1,18 @@
 """Autotuner of the library's kernel choices (bst_tune_set), written for this library.
 
-What it tunes: the thread mapping of the emulated-FP64 tensor-core kernel per (m, n) C
-block class -- whether the 16-row MMA tiles run over the C block's rows (0) or over its
-columns (1, computing C^T = op(B)^T op(A)^T on the same digit planes).  The two
-mappings use different numbers of 16 x 8 tiles and load the two operands' fragments in
-different proportions, so which one is faster depends on m, n and the inner sizes k of
-the products.  For every class present in a plan the tuner times the plan's execute with
-that class set to each mapping (the others unchanged), keeps the faster one, and returns
-a table that can be saved as JSON (keyed by GPU name) and applied to a context later.
+What it tunes, per (m, n) C block class:
+* the thread mapping of the emulated-FP64 tensor-core kernel -- whether the 16-row MMA
+  tiles run over the C block's rows (0) or over its columns (1, computing
+  C^T = op(B)^T op(A)^T on the same digit planes).  The two mappings use different
+  numbers of 16 x 8 tiles and load the two operands' fragments in different
+  proportions, so which one is faster depends on m, n and the inner sizes k;
+* the largest inner split of the native-FP64 staged kernel's tiles: a tile whose m n
+  outputs leave lanes idle (5 x 13 = 65 outputs on 3 x 32 lanes) can spread its inner
+  dimension over s lane groups and add the s partial sums at the end.  The library picks
+  s per tile by counting FP64 instructions; the tuner bounds it per class by timing.
+For every class present in a plan the tuner times the plan's execute with that class set
+to each choice (the others unchanged), keeps the fastest, and returns a table that can be
+saved as JSON (keyed by GPU name) and applied to a context later.
 
 Timing uses CUDA events on the current stream, after a warm-up, minimum over repeats.
 """
@@ -58,20 +63,59 @@ def tune_emulated(plan, device=0, reps=3) -> dict:
     return table
 
 
+SPLIT_CHOICES = (1, 2, 4, 16)  # largest split tried per class (16: the built-in bound)
+
+
+def tune_fp64_split(plan, device=0, reps=3, choices=SPLIT_CHOICES) -> dict:
+    """Choose the largest inner split of the native-FP64 staged kernel per (m, n) class
+    of `plan` (result bound) and leave the choices set in the context.  Returns
+    {(m, n): {"split": best, "ms": {choice: t}}}."""
+    ctx = bst.context(device)
+    table = {}
+    for (m, n) in plan_classes(plan):
+        times = {}
+        for v in choices:
+            bst.bst_tune_set(ctx, bst.BST_TUNE_F64_SPLIT, v, m, n)
+            times[v] = time_execute(plan, bst.BST_FP64, reps)
+        best = min(times, key=times.get)
+        bst.bst_tune_set(ctx, bst.BST_TUNE_F64_SPLIT, best, m, n)
+        table[(m, n)] = {"split": best, "ms": times}
+    return table
+
+
 def gpu_name(device=0) -> str:
     import torch
     return torch.cuda.get_device_name(device)
 
 
+_CHOICE_KEYS = ("swap", "split")
+
+
 def table_to_json(table: dict, gpu: str) -> dict:
-    return {"gpu": gpu, "precision": "fp64_emu_bf16", "key": "emu_swap",
-            "entries": [{"m": m, "n": n, "swap": v["swap"], "ms": v["ms"]}
-                        for (m, n), v in sorted(table.items())]}
+    """Entries carry "swap" (emulated-FP64 mapping) and/or "split" (native-FP64 bound)."""
+    return {"gpu": gpu, "entries": [
+        dict({"m": m, "n": n, "ms": v.get("ms", {})},
+             **{k: int(v[k]) for k in _CHOICE_KEYS if k in v})
+        for (m, n), v in sorted(table.items())]}
 
 
 def table_from_json(doc: dict) -> dict:
-    return {(int(e["m"]), int(e["n"])): {"swap": int(e["swap"]), "ms": e.get("ms", {})}
+    return {(int(e["m"]), int(e["n"])): dict({"ms": e.get("ms", {})},
+                                             **{k: int(e[k]) for k in _CHOICE_KEYS if k in e})
             for e in doc["entries"]}
+
+
+def merge_tables(*tables: dict) -> dict:
+    """One table from several (e.g. tune_emulated's and tune_fp64_split's)."""
+    out = {}
+    for t in tables:
+        for key, v in t.items():
+            e = out.setdefault(key, {"ms": {}})
+            for k in _CHOICE_KEYS:
+                if k in v:
+                    e[k] = v[k]
+                    e["ms"] = dict(e["ms"], **{f"{k}={c}": t_ for c, t_ in v["ms"].items()})
+    return out
 
 
 def save_table(table: dict, path: str, gpu: str) -> None:
@@ -88,7 +132,10 @@ def save_table(table: dict, path: str, gpu: str) -> None:
 def apply_table(table: dict, device=0) -> None:
     ctx = bst.context(device)
     for (m, n), v in table.items():
-        bst.bst_tune_set(ctx, bst.BST_TUNE_EMU_SWAP, int(v["swap"]), m, n)
+        if "swap" in v:
+            bst.bst_tune_set(ctx, bst.BST_TUNE_EMU_SWAP, int(v["swap"]), m, n)
+        if "split" in v:
+            bst.bst_tune_set(ctx, bst.BST_TUNE_F64_SPLIT, int(v["split"]), m, n)
 
 
 def load_table(path: str, gpu: str, device=0) -> dict:
