@@ -740,12 +740,14 @@ __global__ void k_f64_tiles(int64_t nc, const int32_t *__restrict__ c_cls,
 // Inner split of every tile (descriptor word 7): the s <= smax of the tile's class that
 // needs the fewest FP64 warp instructions -- ceil(s mt n / 32) for each of the
 // ceil(w / s) steps of a panel of width w, plus (s - 1) ceil(mt n / 32) adds for the
-// final sums -- when it saves at least 1/8 of the unsplit count on a tile with at least
-// kSplitMinInner inner elements in all (on shorter tiles the final sums cost more than
-// the idle lanes), else 1.  The plan-wide sums of the unsplit counts and of the savings
-// decide whether the plan splits at all (refresh_f64_split).
+// final sums -- when it saves anything on a tile with at least kSplitLongInner inner
+// elements in all, at least 1/8 of the unsplit count on one with kSplitMinInner or more,
+// else 1 (on short tiles the final sums cost more than the idle lanes).  The plan-wide
+// sums of the unsplit counts and of the savings decide whether the plan splits at all
+// (refresh_f64_split).
 constexpr int kMaxSplit = 16;
 constexpr int kSplitMinInner = 48;
+constexpr int kSplitLongInner = 128;
 
 __device__ int f64_split_of(int32_t *__restrict__ d, const int4 *__restrict__ ents, int smax,
                             long long &c1, long long &saved) {
@@ -770,7 +772,7 @@ __device__ int f64_split_of(int32_t *__restrict__ d, const int4 *__restrict__ en
       best = s;
     }
   }
-  if (8 * cb > 7 * c1 || W[1] < kSplitMinInner) best = 1;
+  if ((W[1] >= kSplitLongInner ? cb >= c1 : 8 * cb > 7 * c1) || W[1] < kSplitMinInner) best = 1;
   if (best > 1) saved = c1 - cb;
   return best;
 }
