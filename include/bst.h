@@ -188,6 +188,14 @@ bst_status bst_plan_get_stacks(const bst_plan *plan, int32_t *mnk, int64_t *buck
  * tiles).  hist has 17 entries.  Synchronises. */
 bst_status bst_plan_split_histogram(const bst_plan *plan, int64_t *hist);
 
+/* How the native-FP64 execute of a plan runs (for tests and tuning): info[0] = 1 when
+ * the staged kernel runs its tiles (0: the direct-load kernel), info[1] = 1 when its
+ * staging copies strided rows (row tiles, inner panels or slabs), info[2] = 1 when some
+ * tile splits its inner dimension (BST_TUNE_F64_SPLIT), info[3] = 1 when A is read in
+ * place as slabs of a contraction operand (BST_TUNE_CONTRACT_SLAB).  As of the last
+ * execute or plan build; split-K executes (split_k > 1) use none of this. */
+bst_status bst_plan_schedule_info(const bst_plan *plan, int32_t *info);
+
 /* Arithmetic used by execute. */
 enum {
   BST_FP64 = 0,          /* native FP64 FMA                                        */
@@ -253,13 +261,25 @@ bst_status bst_plan_destroy(bst_plan *plan);
  *     bound each tile takes the split that needs the fewest FP64 instructions, and
  *     only when that saves at least 1/16 of them; the s partial sums of an output are
  *     added in a fixed order, so results stay deterministic.
+ *   BST_TUNE_CONTRACT_SLAB (m, n ignored): 1 = when a contraction's first tensor is
+ *     stored as (outer contracted modes, free modes, inner contracted modes), e.g.
+ *     T(P, mu, nu) contracted over (P, nu), its matrix view is read in place as
+ *     consecutive contiguous slabs by native-FP64 executes that run the staged kernel
+ *     (no permuted copy is made before them); 0 = always through the permuted copy
+ *     (default).  Taken when a contraction plan is created; tune.tune_contract_slab
+ *     times both on a given contraction.
  * Changing a choice takes effect at the next execute of a plan; a batch built before
  * the change refuses emulated-FP64 execution (BST_ERR_STATE) and must be created again.
  * A plan or batch whose native-FP64 tiles must be split again after a change returns
  * BST_ERR_STATE when that execute is being captured into a CUDA graph: execute it once
  * outside capture first.
  * Errors: INVALID_ARG for an unknown key or value. */
-enum { BST_TUNE_EMU_ROW_SCALE = 0, BST_TUNE_EMU_SWAP = 1, BST_TUNE_F64_SPLIT = 2 };
+enum {
+  BST_TUNE_EMU_ROW_SCALE = 0,
+  BST_TUNE_EMU_SWAP = 1,
+  BST_TUNE_F64_SPLIT = 2,
+  BST_TUNE_CONTRACT_SLAB = 3
+};
 bst_status bst_tune_set(bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t value);
 bst_status bst_tune_get(const bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t *value);
 

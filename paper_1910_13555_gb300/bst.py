@@ -73,6 +73,7 @@ _SIGS = {
     "bst_plan_stats": ([_VP, C.POINTER(bst_stats)], C.c_int32),
     "bst_plan_get_stacks": ([_VP, _VP, _VP, _VP, _VP, _VP], C.c_int32),
     "bst_plan_split_histogram": ([_VP, _VP], C.c_int32),
+    "bst_plan_schedule_info": ([_VP, _VP], C.c_int32),
     "bst_multiply_execute": ([_VP, C.c_double, C.c_double, C.c_int32, C.c_int32, _VP], C.c_int32),
     "bst_multiply_execute_static": ([_VP, C.c_double, C.c_double, C.c_int32, _VP], C.c_int32),
     "bst_static_scratch_doubles": ([], C.c_size_t),
@@ -248,6 +249,14 @@ def bst_plan_split_histogram(plan) -> np.ndarray:
     return h
 
 
+def bst_plan_schedule_info(plan) -> dict:
+    """How the plan's native-FP64 execute runs: staged kernel, strided staging, inner
+    split, slab reading of A."""
+    v = np.zeros(4, np.int32)
+    _check(load().bst_plan_schedule_info(plan, _ptr(v)), "bst_plan_schedule_info")
+    return dict(staged=bool(v[0]), strided=bool(v[1]), split=bool(v[2]), slab=bool(v[3]))
+
+
 def bst_plan_get_stacks(plan):
     st = bst_plan_stats(plan)
     nb, ns = st["n_buckets"], st["n_stack"]
@@ -289,6 +298,7 @@ def bst_plan_destroy(plan):
 BST_TUNE_EMU_ROW_SCALE = 0
 BST_TUNE_EMU_SWAP = 1
 BST_TUNE_F64_SPLIT = 2
+BST_TUNE_CONTRACT_SLAB = 3
 
 
 def bst_tune_set(ctx, key, value, m=0, n=0):
@@ -431,6 +441,9 @@ class Plan:
 
     def split_histogram(self):
         return bst_plan_split_histogram(self.handle)
+
+    def schedule_info(self):
+        return bst_plan_schedule_info(self.handle)
 
     def alloc_result(self, device=0):
         import torch

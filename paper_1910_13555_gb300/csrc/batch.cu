@@ -55,9 +55,10 @@ struct Args {
   bool read_cin;
 };
 
-Args plan_args(bst_plan *p, double alpha, double beta, cudaStream_t s) {
+// a_copy: the execute reads A through the plan's permuted copy (not slab by slab in place)
+Args plan_args(bst_plan *p, double alpha, double beta, cudaStream_t s, bool a_copy = true) {
   if (p->contract)
-    bst::contract_prepare(p, beta != 0.0 && p->Cin && p->Cin->nblocks > 0, s);
+    bst::contract_prepare(p, beta != 0.0 && p->Cin && p->Cin->nblocks > 0, s, a_copy);
   const bst_matrix *C = p->C;
   BST_REQUIRE(std::isfinite(alpha) && std::isfinite(beta), BST_ERR_INVALID_ARG,
               "alpha and beta must be finite");
@@ -203,8 +204,10 @@ bst_status bst_batch_execute(bst_batch *b, const double *alpha, const double *be
           bst::refresh_f64_split(b->plans[q], s);
           split = split || b->plans[q]->stage_split;
         }
-        Args r = plan_args(b->plans[q], alpha[q], beta[q], s);
-        bst::fill_num_params(b->plans[q], r.a, static_cast<char *>(b->h_params) + q * b->pbytes);
+        Args r = plan_args(b->plans[q], alpha[q], beta[q], s,
+                           !(b->stage_elems > 0 && bst::fp64_reads_slabs(b->plans[q], 1)));
+        bst::fill_num_params(b->plans[q], r.a, static_cast<char *>(b->h_params) + q * b->pbytes,
+                             b->stage_elems > 0);
       }
       BST_CUDA(cudaMemcpyAsync(b->d_params, b->h_params, b->pbytes * n, cudaMemcpyHostToDevice, s));
       if (b->stage_elems > 0)

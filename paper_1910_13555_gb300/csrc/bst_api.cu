@@ -82,14 +82,6 @@ void use_device(const bst_ctx *ctx) {
   if (cur != ctx->device) BST_CUDA(cudaSetDevice(ctx->device));
 }
 
-template <class T>
-T *upload(bst::Arena &ar, const std::vector<T> &v, cudaStream_t s) {
-  T *d = ar.alloc_n<T>(v.size());
-  if (!v.empty())
-    BST_CUDA(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
-  return d;
-}
-
 }  // namespace
 
 extern "C" {
@@ -168,6 +160,7 @@ bst_status bst_context_destroy(bst_ctx *ctx) {
     cudaMemPoolDestroy(ctx->pool);
   }
   if (ctx && ctx->rb_host) cudaFreeHost(ctx->rb_host);
+  if (ctx && ctx->up_host) cudaFreeHost(ctx->up_host);
   delete static_cast<bst::Ctx *>(ctx);
   API_END
 }
@@ -226,14 +219,15 @@ bst_status bst_matrix_create(bst_ctx *ctx, bst_matrix **out, int32_t nbr,
     m->h_csz.assign(col_blk_sizes, col_blk_sizes + nbc);
     m->nblocks = nblocks;
     m->nelem = acc;
-    m->rsz = upload(m->arena, m->h_rsz, s);
-    m->csz = upload(m->arena, m->h_csz, s);
-    m->rowptr = upload(m->arena, rowptr, s);
-    m->row = upload(m->arena, row, s);
-    m->col = upload(m->arena, col, s);
-    m->off = upload(m->arena, off, s);
+    bst::Upload up(ctx, s);
+    m->rsz = up.add_vector(m->arena, m->h_rsz);
+    m->csz = up.add_vector(m->arena, m->h_csz);
+    m->rowptr = up.add_vector(m->arena, rowptr);
+    m->row = up.add_vector(m->arena, row);
+    m->col = up.add_vector(m->arena, col);
+    m->off = up.add_vector(m->arena, off);
     m->data = data;
-    BST_CUDA(cudaStreamSynchronize(s));  // the host staging vectors end here
+    up.done();  // the host staging vectors end here
   } catch (...) {
     delete m;
     throw;
@@ -376,6 +370,16 @@ bst_status bst_plan_split_histogram(const bst_plan *plan, int64_t *hist) {
   API_END
 }
 
+bst_status bst_plan_schedule_info(const bst_plan *plan, int32_t *info) {
+  API_BEGIN
+  BST_REQUIRE(plan && info, BST_ERR_INVALID_ARG, "NULL argument");
+  info[0] = plan->stage_elems > 0;
+  info[1] = plan->stage_elems > 0 && plan->stage_strided;
+  info[2] = plan->stage_elems > 0 && plan->stage_split;
+  info[3] = plan->stage_elems > 0 && plan->a_slab;
+  API_END
+}
+
 bst_status bst_plan_get_stacks(const bst_plan *plan, int32_t *mnk, int64_t *bucket_ptr,
                                int32_t *a_off, int32_t *b_off, int32_t *c_off) {
   API_BEGIN
@@ -412,9 +416,13 @@ bst_status bst_multiply_execute(bst_plan *plan, double alpha, double beta, int32
   BST_REQUIRE(std::isfinite(alpha) && std::isfinite(beta), BST_ERR_INVALID_ARG,
               "alpha and beta must be finite");
   use_device(plan->ctx);
+  int split = 1;
+  if (precision == BST_FP64)
+    split = split_k == 0 ? bst::choose_split(plan, plan->ctx->num_sms) : split_k;
   if (plan->contract)
     bst::contract_prepare(plan, beta != 0.0 && plan->Cin && plan->Cin->nblocks > 0,
-                          as_stream(stream));
+                          as_stream(stream),
+                          !(precision == BST_FP64 && bst::fp64_reads_slabs(plan, split)));
   const bst_matrix *C = plan->C;
   BST_REQUIRE(C->nelem == 0 || C->data, BST_ERR_STATE, "C_out data not bound");
   BST_REQUIRE(plan->A->nblocks == 0 || plan->A->data, BST_ERR_STATE, "A data not bound");
@@ -430,10 +438,8 @@ bst_status bst_multiply_execute(bst_plan *plan, double alpha, double beta, int32
   a.C = C->data;
   a.alpha = alpha;
   a.beta = read_cin ? beta : 0.0;
-  int split = 1;
   switch (precision) {
     case BST_FP64:
-      split = split_k == 0 ? bst::choose_split(plan, plan->ctx->num_sms) : split_k;
       bst::execute_fp64(plan, a, split, s);
       break;
     case BST_FP64_EMU_BF16:
@@ -493,6 +499,10 @@ bst_status bst_tune_set(bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t
       else
         ctx->tune_emu_swap[{m, n}] = value;
       break;
+    case BST_TUNE_CONTRACT_SLAB:
+      BST_REQUIRE(value == 0 || value == 1, BST_ERR_INVALID_ARG, "value must be 0 or 1");
+      ctx->tune_contract_slab = value;
+      break;
     case BST_TUNE_F64_SPLIT:
       BST_REQUIRE(value == -1 || (value >= 1 && value <= 16), BST_ERR_INVALID_ARG,
                   "value must be -1 or 1..16");
@@ -521,6 +531,9 @@ bst_status bst_tune_get(const bst_ctx *ctx, int32_t key, int32_t m, int32_t n, i
       *value = it == ctx->tune_emu_swap.end() ? -1 : it->second;
       break;
     }
+    case BST_TUNE_CONTRACT_SLAB:
+      *value = ctx->tune_contract_slab;
+      break;
     case BST_TUNE_F64_SPLIT: {
       auto it = ctx->tune_f64_split.find({m, n});
       *value = it == ctx->tune_f64_split.end() ? -1 : it->second;

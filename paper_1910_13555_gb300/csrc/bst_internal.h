@@ -83,6 +83,10 @@ struct bst_ctx {
   void *rb_host = nullptr;
   size_t rb_cap = 0;
   std::mutex rb_mutex;
+  // mapped pinned staging for Upload (grown on demand), held for one Upload at a time
+  void *up_host = nullptr;
+  size_t up_cap = 0;
+  std::mutex up_mutex;
   // kernel choices (bst_tune_set): emulated-FP64 digit scaling per whole op row /
   // column (1) or per block row / column (0); per (m, n) C block class, the tile
   // orientation of the emulated kernel (1 = MMA rows run over the C block's columns);
@@ -92,6 +96,9 @@ struct bst_ctx {
   // per (m, n) C block class, the largest inner split of the staged FP64 kernel's tiles
   // (1 = none); classes without an entry use the built-in bound
   std::map<std::pair<int32_t, int32_t>, int32_t> tune_f64_split;
+  // contractions: read an operand whose matrix view is a sequence of contiguous slabs of
+  // each tensor block in place (1) or through a permuted copy (0)
+  int tune_contract_slab = 0;
   int64_t tune_version = 0;
 };
 
@@ -184,6 +191,32 @@ struct ReadBack {
   void finish();  // values are in place afterwards
   void done();    // finish() and release the staging buffer to other threads
 };
+// Host -> device copies of index arrays the same way: the bytes are staged in the
+// context's mapped pinned buffer and a kernel copies them to the device, so the upload
+// never queues behind other streams' DMA transfers either.  done() waits for this
+// stream's copies (the staging buffer is then free for the next Upload).
+struct Upload {
+  bst_ctx *ctx;
+  cudaStream_t s;
+  struct Item {
+    void *dst;
+    size_t off, bytes;
+  };
+  std::vector<Item> items;
+  size_t used = 0;
+  bool locked = false;
+  Upload(bst_ctx *c, cudaStream_t st);
+  ~Upload();
+  void add(void *dev_dst, const void *host_src, size_t bytes);
+  template <class T>
+  T *add_vector(Arena &ar, const std::vector<T> &v) {
+    T *d = ar.alloc_n<T>(v.size());
+    add(d, v.data(), sizeof(T) * v.size());
+    return d;
+  }
+  void flush();  // launch the copies staged so far and wait for them
+  void done();   // flush() and release the staging buffer to other threads
+};
 void gather_i32(const int32_t *src, const int32_t *idx, int32_t *dst, int64_t n, cudaStream_t s);
 
 template <class T>
@@ -268,6 +301,15 @@ struct bst_plan {
   int32_t *tkeys = nullptr;    // each tile's cost key
   int64_t split_version = -1;  // tune_version the tiles' inner splits were chosen for
   bool stage_split = false;    // some tile splits its inner dimension
+  bst::Arena sched_ar;         // the staged schedule's arrays (rebuilt for slab reading)
+  // Slab reading of a contraction operand (set by the contraction before the staged
+  // schedule is built): A's stored block (m x k, k = k_o * k_i) is k_o contiguous m x k_i
+  // slabs of the tensor block, read in place.  Per k class k_i (empty: no slab reading),
+  // per A view block its tensor element offset; a_slab_base = the tensor's data.
+  std::vector<int32_t> a_slab_kin;
+  int64_t *a_slab_toff = nullptr;
+  bool a_slab = false;         // the staged schedule reads A as slabs
+  double *a_slab_base = nullptr;
   // stats
   bst_stats stats{};
   // emulated-precision state (numeric_emu.cu), built on first use
@@ -298,7 +340,9 @@ void execute_tf32x3(bst_plan *p, const NumArgs &a, cudaStream_t s);
 void emu_state_free(bst_plan *p);
 void adj_state_free(bst_plan *p);
 // contractions (contract.cu)
-void contract_prepare(bst_plan *p, bool read_cin, cudaStream_t s);
+void contract_prepare(bst_plan *p, bool read_cin, cudaStream_t s, bool a_copy = true);
+// the native-FP64 execute with `split` K parts reads A in place (slab schedule)
+bool fp64_reads_slabs(const bst_plan *p, int split);
 void contract_finish(bst_plan *p, cudaStream_t s);
 void contract_adjoint(bst_plan *p, const double *dR, double *dT1, double *dT2, double *dRin,
                       double alpha, double beta, cudaStream_t s);
@@ -310,7 +354,7 @@ void scale_cin_grad(bst_plan *p, const double *dC, double *dCin, double beta, cu
 int choose_split(const bst_plan *p, int num_sms);
 // persistent FP64 numeric (numeric_fp64.cu)
 size_t num_params_bytes();
-void fill_num_params(bst_plan *p, const NumArgs &a, void *out);
+void fill_num_params(bst_plan *p, const NumArgs &a, void *out, bool staged);
 void build_plan_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys, cudaStream_t s);
 void sort_items(const int64_t *items, const int32_t *keys, int64_t n, int64_t *out, Arena &scratch,
                 cudaStream_t s);

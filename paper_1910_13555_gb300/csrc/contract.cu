@@ -21,6 +21,7 @@
 // = the free modes of T2; it is the result tensor itself when result_order is the
 // identity, and is permuted block by block into the result tensor otherwise.
 #include <algorithm>
+#include <map>
 #include <climits>
 #include <cstring>
 #include <numeric>
@@ -257,10 +258,12 @@ void build_view(bst_ctx *ctx, const bst_tensor *T, const std::vector<int32_t> &r
   M->nbc = (int32_t)M->h_csz.size();
   M->nblocks = T->nblocks;
   M->nelem = T->nelem;
-  M->rsz = ar.alloc_n<int32_t>(M->h_rsz.size());
-  M->csz = ar.alloc_n<int32_t>(M->h_csz.size());
-  BST_CUDA(cudaMemcpyAsync(M->rsz, M->h_rsz.data(), 4 * M->h_rsz.size(), cudaMemcpyHostToDevice, s));
-  BST_CUDA(cudaMemcpyAsync(M->csz, M->h_csz.data(), 4 * M->h_csz.size(), cudaMemcpyHostToDevice, s));
+  {
+    Upload up(ctx, s);
+    M->rsz = up.add_vector(ar, M->h_rsz);
+    M->csz = up.add_vector(ar, M->h_csz);
+    up.done();
+  }
   const int64_t n = T->nblocks;
   FoldArgs F{};
   F.nblocks = n;
@@ -357,6 +360,59 @@ void permute_view(const View &V, const double *src, double *dst, bool to_view, c
   BST_CHECK_LAUNCH();
 }
 
+// Slab reading of T1 (the second remap of a non-fold view).  When T1's modes are stored
+// as (outer contracted modes, free modes, inner contracted modes), each in the order the
+// view folds them, the view's m x k block (rows = free fold, k = outer fold x inner fold)
+// is the tensor block itself read as k / k_i consecutive m x k_i slabs (k_i = the inner
+// fold's size): column o k_i + i of row r sits at o m k_i + r k_i + i.  The native-FP64
+// staged schedule can then read A in place instead of through the permuted copy.  Needs
+// k_i to be a function of the k block size (one slab width per k class).
+void setup_slab_read(bst_plan *p, const View &V, const std::vector<int32_t> &F1,
+                     const std::vector<int32_t> &C1, Arena &ar, cudaStream_t s) {
+  const bst_tensor *T = V.T;
+  const int nc = (int)C1.size();
+  int j = -1;
+  for (int q = 1; q < nc && j < 0; ++q) {
+    std::vector<int32_t> o(C1.begin(), C1.begin() + q);
+    o.insert(o.end(), F1.begin(), F1.end());
+    o.insert(o.end(), C1.begin() + q, C1.end());
+    bool id = true;
+    for (int d = 0; d < (int)o.size(); ++d) id &= o[d] == d;
+    if (id) j = q;
+  }
+  if (j < 0 || V.M->nblocks == 0) return;
+  // k_i of every k block (mixed radix over C1, first listed most significant)
+  std::map<int32_t, int32_t> kin_of;
+  const int64_t nk = (int64_t)V.M->h_csz.size();
+  for (int64_t x = 0; x < nk; ++x) {
+    int64_t rem = x, ki = 1;
+    for (int q = nc - 1; q >= 0; --q) {
+      const int32_t d = C1[q];
+      if (q >= j) ki *= T->h_sz[d][rem % T->h_nblk[d]];
+      rem /= T->h_nblk[d];
+    }
+    const int32_t k = V.M->h_csz[(size_t)x];
+    auto it = kin_of.find(k);
+    if (it == kin_of.end())
+      kin_of[k] = (int32_t)ki;
+    else if (it->second != ki)
+      return;  // two slab widths for one k class
+  }
+  std::vector<int32_t> kin(p->k_vals.size());
+  for (size_t kc = 0; kc < kin.size(); ++kc) {
+    auto it = kin_of.find(p->k_vals[kc]);
+    kin[kc] = it == kin_of.end() ? p->k_vals[kc] : it->second;
+  }
+  const int64_t n = V.M->nblocks;
+  int64_t *toff = ar.alloc_n<int64_t>((size_t)n);
+  k_gather_i64<<<nblk(n, 256), 256, 0, s>>>(T->off, V.tblk, toff, n);
+  BST_CHECK_LAUNCH();
+  p->a_slab_kin = kin;
+  p->a_slab_toff = toff;
+  p->a_slab_base = T->data;
+  build_f64_schedule(p, s);
+}
+
 void free_view(View &V) {
   if (V.M) {
     V.M->owned_by_plan = false;
@@ -383,13 +439,14 @@ void contract_free(bst_plan *p) {
 
 // Refresh the views' data before an execute: permute the inputs that are copies and
 // point the C matrix at the result data.  Returns the C data pointer to use.
-void contract_prepare(bst_plan *p, bool read_cin, cudaStream_t s) {
+void contract_prepare(bst_plan *p, bool read_cin, cudaStream_t s, bool a_copy) {
   Contract &K = *p->contract;
   BST_REQUIRE(K.A.T->nblocks == 0 || K.A.T->data, BST_ERR_STATE, "T1 data not bound");
   BST_REQUIRE(K.B.T->nblocks == 0 || K.B.T->data, BST_ERR_STATE, "T2 data not bound");
   K.A.M->data = K.A.copy ? K.A.buf : K.A.T->data;
   K.B.M->data = K.B.copy ? K.B.buf : K.B.T->data;
-  permute_view(K.A, K.A.T->data, K.A.buf, true, s);
+  p->a_slab_base = K.A.T->data;
+  if (a_copy) permute_view(K.A, K.A.T->data, K.A.buf, true, s);
   permute_view(K.B, K.B.T->data, K.B.buf, true, s);
   if (K.has_cin) {
     K.Ci.M->data = K.Ci.copy ? K.Ci.buf : K.Ci.T->data;
@@ -558,14 +615,13 @@ bst_status bst_tensor_create(bst_ctx *ctx, bst_tensor **out, int32_t rank, const
     for (auto &v : sz) flat.insert(flat.end(), v.begin(), v.end());
     t->idx = t->arena.alloc_n<int32_t>(t->h_idx.size());
     t->off = t->arena.alloc_n<int64_t>(t->h_off.size() + 1);
-    t->sz = t->arena.alloc_n<int32_t>(flat.size());
-    if (!t->h_idx.empty())
-      BST_CUDA(cudaMemcpyAsync(t->idx, t->h_idx.data(), 4 * t->h_idx.size(), cudaMemcpyHostToDevice, s));
-    if (!t->h_off.empty())
-      BST_CUDA(cudaMemcpyAsync(t->off, t->h_off.data(), 8 * t->h_off.size(), cudaMemcpyHostToDevice, s));
-    if (!flat.empty())
-      BST_CUDA(cudaMemcpyAsync(t->sz, flat.data(), 4 * flat.size(), cudaMemcpyHostToDevice, s));
-    BST_CUDA(cudaStreamSynchronize(s));
+    {
+      bst::Upload up(ctx, s);
+      up.add(t->idx, t->h_idx.data(), 4 * t->h_idx.size());
+      up.add(t->off, t->h_off.data(), 8 * t->h_off.size());
+      t->sz = up.add_vector(t->arena, flat);
+      up.done();
+    }
     t->data = data;
   } catch (...) {
     delete t;
@@ -711,6 +767,8 @@ bst_status bst_contract_plan(bst_ctx *ctx, const bst_tensor *T1, const bst_tenso
                                       R_in ? K->Ci.M : nullptr, eps, stream, &p);
     if (st != BST_OK) throw Error{st, bst_last_error()};
     p->contract = K;
+    if (!ta && K->A.copy && static_cast<bst::Ctx *>(ctx)->tune_contract_slab)
+      bst::setup_slab_read(p, K->A, F1, C1, K->ar, s);
     // result tensor: blocks of C unfolded into result-order tuples
     const bst_matrix *C = p->C;
     auto *R = new bst_tensor();
@@ -728,8 +786,11 @@ bst_status bst_contract_plan(bst_ctx *ctx, const bst_tensor *T1, const bst_tenso
     }
     R->nblocks = C->nblocks;
     R->nelem = C->nelem;
-    R->sz = K->ar.alloc_n<int32_t>(flat.size());
-    BST_CUDA(cudaMemcpyAsync(R->sz, flat.data(), 4 * flat.size(), cudaMemcpyHostToDevice, s));
+    {
+      bst::Upload up(ctx, s);
+      R->sz = up.add_vector(K->ar, flat);
+      up.done();
+    }
     bool rid = true;
     for (int r = 0; r < rr; ++r) rid &= ro[r] == r;
     K->r_identity = rid;
@@ -798,11 +859,12 @@ bst_status bst_contract_plan(bst_ctx *ctx, const bst_tensor *T1, const bst_tenso
     }
     R->h_idx.resize((size_t)nc * rr);
     R->h_off.resize((size_t)nc);
-    if (nc > 0) {
-      BST_CUDA(cudaMemcpyAsync(R->h_idx.data(), R->idx, 4 * (size_t)nc * rr, cudaMemcpyDeviceToHost, s));
-      BST_CUDA(cudaMemcpyAsync(R->h_off.data(), R->off, 8 * (size_t)nc, cudaMemcpyDeviceToHost, s));
+    {
+      bst::ReadBack rb(ctx, s);
+      rb.add(R->h_idx.data(), R->idx, 4 * (size_t)nc * rr);
+      rb.add(R->h_off.data(), R->off, 8 * (size_t)nc);
+      rb.done();
     }
-    BST_CUDA(cudaStreamSynchronize(s));
     scratch.release_all();
   } catch (...) {
     if (p) {

@@ -953,19 +953,21 @@ void emu_index(bst_plan *p, EmuState &E, cudaStream_t s) {
   }
   E.ncls = ncls;
   E.nwarps = ws.back();
-  E.wstart = ar.alloc_n<int64_t>(ws.size());
-  BST_CUDA(cudaMemcpyAsync(E.wstart, ws.data(), 8 * ws.size(), cudaMemcpyHostToDevice, s));
   // global element starts of op(A) row blocks and op(B) column blocks
-  auto starts = [&](const std::vector<int32_t> &sz, int64_t *&out, int64_t &total) {
+  auto starts = [&](const std::vector<int32_t> &sz, int64_t &total) {
     std::vector<int64_t> h(sz.size() + 1, 0);
     for (size_t q = 0; q < sz.size(); ++q) h[q + 1] = h[q] + sz[q];
     total = h.back();
-    out = ar.alloc_n<int64_t>(h.size());
-    BST_CUDA(cudaMemcpyAsync(out, h.data(), 8 * h.size(), cudaMemcpyHostToDevice, s));
-    BST_CUDA(cudaStreamSynchronize(s));
+    return h;
   };
-  starts(p->oa.h_rs, E.a_rowstart, E.nrows);
-  starts(p->ob.h_cs, E.b_colstart, E.ncols);
+  {
+    const std::vector<int64_t> ha = starts(p->oa.h_rs, E.nrows), hb = starts(p->ob.h_cs, E.ncols);
+    Upload up(p->ctx, s);
+    E.wstart = up.add_vector(ar, ws);
+    E.a_rowstart = up.add_vector(ar, ha);
+    E.b_colstart = up.add_vector(ar, hb);
+    up.done();
+  }
   BST_CUDA(cudaStreamSynchronize(s));
   scratch.release_all();
   E.index_ready = true;
@@ -1114,7 +1116,11 @@ static void emu_schedule(bst_plan *p, EmuState &E, cudaStream_t s) {
   if (!E.cls_swap) E.cls_swap = E.ar.alloc_n<int32_t>(sw.size());
   if (!E.desc) E.desc = E.ar.alloc_n<int32_t>((size_t)std::max<int64_t>(nc, 1) * kDescWords);
   if (!E.counter) E.counter = E.ar.alloc_n<unsigned long long>(1);
-  BST_CUDA(cudaMemcpyAsync(E.cls_swap, sw.data(), 4 * sw.size(), cudaMemcpyHostToDevice, s));
+  {
+    Upload up(p->ctx, s);
+    up.add(E.cls_swap, sw.data(), 4 * sw.size());
+    up.done();
+  }
   if (nc > 0) {
     k_emu_desc<<<nblk(nc, 256), 256, 0, s>>>(nc, p->Dk, p->run_len, p->kval, E.ebeg, p->C->off,
                                              p->C->row, p->C->col, p->c_cls, p->cls_m, p->cls_n,

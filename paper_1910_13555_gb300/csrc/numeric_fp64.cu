@@ -319,10 +319,20 @@ __device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_gro
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // `rows` segments of `len` doubles, `stride` apart, packed into dst (out of line: only
-// panels and tiles of large products take it)
+// panels and tiles of large products take it).  stride < len: the source is len / stride
+// consecutive slabs of rows x stride doubles (a slab-read operand), one contiguous range
+// whose slab j supplies columns j stride .. (j + 1) stride - 1 of every row.
 __device__ __noinline__ void stage_strided(double *dst, const double *src, int rows, int len,
                                            int stride) {
   const int lane = threadIdx.x & 31;
+  if (stride < len) {
+    const int per = rows * stride;
+    for (int i = lane; i < rows * len; i += 32) {
+      const int j = i / per, rem = i - j * per, r = rem / stride;
+      cp_async8(dst + r * len + j * stride + (rem - r * stride), src + i);
+    }
+    return;
+  }
   for (int r = 0; r < rows; ++r)
     for (int c = lane; c < len; c += 32) cp_async8(dst + r * len + c, src + (int64_t)r * stride + c);
 }
@@ -659,7 +669,22 @@ struct SchedTabs {
   const int32_t *wpanel;                     // per (class, k class): panel width
   const int32_t *kval;
   int32_t Dk, ta, tb;
+  // slab reading of A (null: none): per k class the slab width k_i, per entry its stored
+  // A block, per stored A block its element offset in the tensor
+  const int32_t *kin, *s_ab;
+  const int64_t *a_toff;
 };
+
+// panels of one product of inner size k at panel width w: whole panels, or with slab
+// width ki > 0 panels that never cross a slab (several whole slabs when w >= ki)
+__device__ __forceinline__ int panel_count(int k, int w, int ki) {
+  if (ki <= 0) return (k + w - 1) / w;
+  if (w >= ki) {
+    const int ws = (w / ki) * ki;
+    return (k + ws - 1) / ws;
+  }
+  return (k / ki) * ((ki + w - 1) / w);
+}
 
 __device__ __forceinline__ int ntiles_of(const SchedTabs &S, int cls) {
   const int tr = S.tile_rows[cls];
@@ -682,7 +707,7 @@ __global__ void k_f64_ent_count(int64_t nc, const int32_t *__restrict__ c_cls,
   int s = 0;
   for (int kc = 0; kc < S.Dk; ++kc) {
     const int w = S.wpanel[cls * S.Dk + kc], k = S.kval[kc];
-    s += run_len[c * S.Dk + kc] * ((k + w - 1) / w);
+    s += run_len[c * S.Dk + kc] * panel_count(k, w, S.kin ? S.kin[kc] : 0);
   }
   const int nt = ntiles_of(S, cls);
   for (int t = 0; t < nt; ++t) cnt[tbeg[c] + t] = s;
@@ -715,13 +740,35 @@ __global__ void k_f64_tiles(int64_t nc, const int32_t *__restrict__ c_cls,
       // stored row strides of the panels: A is m x k (k x m when transposed), B is k x n
       // (n x k when transposed)
       const int strides = (S.ta ? m : k) | ((S.tb ? k : n) << 16);
-      for (int e = e0; e < e0 + len; ++e)
+      const int ki = S.kin ? S.kin[kc] : 0;
+      for (int e = e0; e < e0 + len; ++e) {
+        if (ki > 0) {
+          // slabs of the tensor block (whole blocks only: p0 == 0): stored row stride ki
+          const int64_t ab = S.a_toff[S.s_ab[e]];
+          const int st = ki | ((S.tb ? k : n) << 16);
+          if (w >= ki) {
+            const int ws = (w / ki) * ki;
+            for (int l0 = 0; l0 < k; l0 += ws) {
+              const int b = s_b[e] + (S.tb ? l0 : l0 * n);
+              ents[q++] = make_int4((int)(ab + (int64_t)(l0 / ki) * m * ki), b, min(ws, k - l0), st);
+            }
+          } else {
+            for (int l0 = 0; l0 < k; l0 += ki)
+              for (int c0 = 0; c0 < ki; c0 += w) {
+                const int b = s_b[e] + (S.tb ? l0 + c0 : (l0 + c0) * n);
+                ents[q++] = make_int4((int)(ab + (int64_t)(l0 / ki) * m * ki + c0), b,
+                                      min(w, ki - c0), st);
+              }
+          }
+          continue;
+        }
         for (int l0 = 0; l0 < k; l0 += w) {
           const int wl = min(w, k - l0);
           const int a = s_a[e] + (S.ta ? l0 * m + p0 : p0 * k + l0);
           const int b = s_b[e] + (S.tb ? l0 : l0 * n);
           ents[q++] = make_int4(a, b, wl, strides);
         }
+      }
       flops += (unsigned long long)len * mt * n * k;
     }
     int32_t *d = desc + tile * kF64Desc;
@@ -750,9 +797,10 @@ constexpr int kSplitMinInner = 48;
 constexpr int kSplitLongInner = 128;
 
 __device__ int f64_split_of(int32_t *__restrict__ d, const int4 *__restrict__ ents, int smax,
-                            long long &c1, long long &saved) {
+                            int slot_elems, long long &c1, long long &saved) {
   const int mn = (d[3] & 0xfff) * ((d[3] >> 12) & 0xfff), ne = d[2];
-  smax = min(min(smax, kMaxSplit), kTile / max(mn, 1));
+  // s m n partial sums fit the accumulators and, for the final sums, one slot
+  smax = min(min(smax, kMaxSplit), min(kTile, slot_elems) / max(mn, 1));
   const long long v1 = (mn + 31) / 32;
   int best = 1;
   c1 = 0;
@@ -780,12 +828,13 @@ __device__ int f64_split_of(int32_t *__restrict__ d, const int4 *__restrict__ en
 // sums[0] += unsplit FP64 instruction counts, sums[1] += savings of the chosen splits
 __global__ void k_f64_split(int64_t ntiles, const int4 *__restrict__ ents,
                             const int32_t *__restrict__ c_cls, const int32_t *__restrict__ cls_smax,
-                            int32_t *__restrict__ desc, unsigned long long *__restrict__ sums) {
+                            int slot_elems, int32_t *__restrict__ desc,
+                            unsigned long long *__restrict__ sums) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   long long c1 = 0, saved = 0;
   if (t < ntiles) {
     int32_t *d = desc + t * kF64Desc;
-    d[7] = f64_split_of(d, ents, cls_smax[c_cls[d[6]]], c1, saved);
+    d[7] = f64_split_of(d, ents, cls_smax[c_cls[d[6]]], slot_elems, c1, saved);
   }
   for (int o = 16; o > 0; o >>= 1) {
     c1 += __shfl_down_sync(0xffffffffu, c1, o);
@@ -849,7 +898,7 @@ __global__ void k_splitk_reduce(NumParams P, int64_t nc, const int32_t *__restri
 
 NumParams make_params(bst_plan *p, const NumArgs &a, int split) {
   NumParams P;
-  P.A = a.A;
+  P.A = (p->a_slab && p->stage_elems > 0 && split <= 1) ? p->a_slab_base : a.A;
   P.B = a.B;
   P.Cin = a.Cin;
   P.C = a.C;
@@ -885,10 +934,15 @@ NumParams make_params(bst_plan *p, const NumArgs &a, int split) {
 
 }  // namespace
 
+bool fp64_reads_slabs(const bst_plan *p, int split) {
+  return p->a_slab && p->stage_elems > 0 && split <= 1;
+}
+
 size_t num_params_bytes() { return sizeof(NumParams); }
 
-void fill_num_params(bst_plan *p, const NumArgs &a, void *out) {
+void fill_num_params(bst_plan *p, const NumArgs &a, void *out, bool staged) {
   NumParams P = make_params(p, a, 1);
+  if (!staged) P.A = a.A;  // the direct-load kernel reads A through the stacks
   std::memcpy(out, &P, sizeof(P));
 }
 
@@ -923,6 +977,10 @@ void sort_items(const int64_t *items, const int32_t *keys, int64_t n, int64_t *o
 static bool build_staged(bst_plan *p, cudaStream_t s) {
   p->stage_elems = 0;
   p->n_tiles = 0;
+  p->a_slab = false;
+  p->sched_ar.ctx = static_cast<Ctx *>(p->ctx);
+  p->sched_ar.stream = s;
+  p->sched_ar.release_all();
   const int64_t nc = p->C->nblocks;
   if (nc == 0 || p->T == 0) return false;
   const int32_t ncls = p->Dm * p->Dn, Dk = p->Dk;
@@ -939,6 +997,9 @@ static bool build_staged(bst_plan *p, cudaStream_t s) {
   for (int32_t c = 0; c < ncls; ++c)
     if (p->h_class_ptr[c + 1] > p->h_class_ptr[c] && tile_rows[(size_t)c] < p->m_vals[c / p->Dn])
       strided = true;
+  // slab reading of A: whole C blocks only (a slab holds all m rows), op(A) = A
+  const bool slab = !p->a_slab_kin.empty() && !strided && !p->ta && p->a_slab_toff;
+  if (slab) strided = true;
   int64_t slot = 1;
   for (int32_t b = 0; b < p->nb_all; ++b) {
     if (p->h_bucket_ptr[b + 1] == p->h_bucket_ptr[b]) continue;
@@ -950,14 +1011,18 @@ static bool build_staged(bst_plan *p, cudaStream_t s) {
     if (w < k) strided = true;
     slot = std::max(slot, (tr + n) * w);
   }
-  Arena &ar = p->arena;
+  Arena &ar = p->sched_ar;
   Arena scratch;
   scratch.ctx = static_cast<Ctx *>(p->ctx);
   scratch.stream = s;
-  int32_t *d_tr = scratch.alloc_n<int32_t>(tile_rows.size());
-  int32_t *d_wp = scratch.alloc_n<int32_t>(wpanel.size());
-  BST_CUDA(cudaMemcpyAsync(d_tr, tile_rows.data(), 4 * tile_rows.size(), cudaMemcpyHostToDevice, s));
-  BST_CUDA(cudaMemcpyAsync(d_wp, wpanel.data(), 4 * wpanel.size(), cudaMemcpyHostToDevice, s));
+  int32_t *d_tr, *d_wp, *d_kin = nullptr;
+  {
+    Upload up(p->ctx, s);
+    d_tr = up.add_vector(scratch, tile_rows);
+    d_wp = up.add_vector(scratch, wpanel);
+    if (slab) d_kin = up.add_vector(scratch, p->a_slab_kin);
+    up.done();
+  }
   SchedTabs S;
   S.cls_m = p->cls_m;
   S.cls_n = p->cls_n;
@@ -967,6 +1032,9 @@ static bool build_staged(bst_plan *p, cudaStream_t s) {
   S.Dk = Dk;
   S.ta = p->ta;
   S.tb = p->tb;
+  S.kin = d_kin;
+  S.s_ab = p->s_ab;
+  S.a_toff = p->a_slab_toff;
   int32_t *tcnt = scratch.alloc_n<int32_t>((size_t)nc);
   int64_t *tbeg = scratch.alloc_n<int64_t>((size_t)nc + 1);
   k_f64_tile_count<<<nblk(nc, 256), 256, 0, s>>>(nc, p->c_cls, S, tcnt);
@@ -1009,6 +1077,7 @@ static bool build_staged(bst_plan *p, cudaStream_t s) {
   p->n_tiles = ntiles;
   p->stage_elems = (int32_t)slot;
   p->stage_strided = strided;
+  p->a_slab = slab;
   p->split_version = -1;
   refresh_f64_split(p, s);
   return true;
@@ -1032,12 +1101,16 @@ void refresh_f64_split(bst_plan *p, cudaStream_t s) {
   Arena scratch;
   scratch.ctx = ctx;
   scratch.stream = s;
-  int32_t *d_smax = scratch.alloc_n<int32_t>((size_t)ncls);
+  int32_t *d_smax;
+  {
+    Upload up(p->ctx, s);
+    d_smax = up.add_vector(scratch, smax);
+    up.done();
+  }
   unsigned long long *d_sums = scratch.alloc_n<unsigned long long>(2);
-  BST_CUDA(cudaMemcpyAsync(d_smax, smax.data(), 4 * (size_t)ncls, cudaMemcpyHostToDevice, s));
   BST_CUDA(cudaMemsetAsync(d_sums, 0, 2 * sizeof(unsigned long long), s));
   k_f64_split<<<nblk(p->n_tiles, 128), 128, 0, s>>>(p->n_tiles, p->fents, p->c_cls, d_smax,
-                                                   p->fdesc, d_sums);
+                                                   p->stage_elems, p->fdesc, d_sums);
   BST_CHECK_LAUNCH();
   unsigned long long sums[2] = {0, 0};
   {

@@ -4,6 +4,7 @@
 // All of them are deterministic: the counting sort is stable because every warp
 // owns one contiguous segment of the input and emits it in order, with the ranks of
 // equal keys inside a 32-element batch taken from __match_any_sync.
+#include <algorithm>
 #include <cstring>
 
 #include "bst_internal.h"
@@ -217,6 +218,16 @@ __global__ void k_copy_bytes(unsigned char *__restrict__ dst, const unsigned cha
     dst[i] = src[i];
 }
 
+// n bytes, both ends 16-byte aligned: 16-byte words, then the tail byte by byte
+__global__ void k_copy_aligned(unsigned char *__restrict__ dst, const unsigned char *__restrict__ src,
+                               int64_t n) {
+  const int64_t nw = n >> 4, stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t i = i0; i < nw; i += stride)
+    reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
+  for (int64_t i = (nw << 4) + i0; i < n; i += stride) dst[i] = src[i];
+}
+
 ReadBack::ReadBack(bst_ctx *c, cudaStream_t st) : ctx(c), s(st) {
   ctx->rb_mutex.lock();
   locked = true;
@@ -242,9 +253,10 @@ void ReadBack::add(void *host_dst, const void *dev_src, size_t bytes) {
   if (bytes == 0) return;
   const size_t off = (used + 15) & ~(size_t)15;
   if (off + bytes > ctx->rb_cap) {
-    // grow: earlier items of this ReadBack are still pending, so finish them first
+    // grow (geometrically, never shrinking: freeing pinned memory synchronises the whole
+    // device): earlier items of this ReadBack are still pending, so finish them first
     if (!items.empty()) finish();
-    const size_t cap = std::max<size_t>(1 << 16, 2 * (bytes + 16));
+    const size_t cap = std::max<size_t>({(size_t)1 << 20, 2 * ctx->rb_cap, 2 * (off + bytes)});
     BST_CUDA(cudaStreamSynchronize(s));
     if (ctx->rb_host) BST_CUDA(cudaFreeHost(ctx->rb_host));
     ctx->rb_host = nullptr;
@@ -268,6 +280,69 @@ void ReadBack::finish() {
   BST_CUDA(cudaStreamSynchronize(s));
   for (const Item &it : items)
     std::memcpy(it.dst, static_cast<const char *>(ctx->rb_host) + it.off, it.bytes);
+  items.clear();
+  used = 0;
+}
+
+Upload::Upload(bst_ctx *c, cudaStream_t st) : ctx(c), s(st) {
+  ctx->up_mutex.lock();
+  locked = true;
+}
+
+Upload::~Upload() {
+  if (locked) {
+    // an exception left copies in flight: let them land before the buffer is reused
+    if (!items.empty() || used) (void)cudaStreamSynchronize(s);
+    ctx->up_mutex.unlock();
+  }
+}
+
+void Upload::done() {
+  flush();
+  if (locked) {
+    locked = false;
+    ctx->up_mutex.unlock();
+  }
+}
+
+void Upload::add(void *dev_dst, const void *host_src, size_t bytes) {
+  if (bytes == 0) return;
+  const size_t off = (used + 15) & ~(size_t)15;
+  if (off + bytes > ctx->up_cap) {
+    // grow (geometrically, never shrinking: freeing pinned memory synchronises the whole
+    // device): the items staged so far are copied out first
+    flush();
+    const size_t cap = std::max<size_t>({(size_t)1 << 20, 2 * ctx->up_cap, 2 * (off + bytes)});
+    if (ctx->up_host) BST_CUDA(cudaFreeHost(ctx->up_host));
+    ctx->up_host = nullptr;
+    ctx->up_cap = 0;
+    BST_CUDA(cudaHostAlloc(&ctx->up_host, cap, cudaHostAllocMapped));
+    ctx->up_cap = cap;
+    return add(dev_dst, host_src, bytes);
+  }
+  std::memcpy(static_cast<char *>(ctx->up_host) + off, host_src, bytes);
+  items.push_back({dev_dst, off, bytes});
+  used = off + bytes;
+}
+
+void Upload::flush() {
+  if (items.empty()) return;
+  void *dev_view = nullptr;
+  BST_CUDA(cudaHostGetDevicePointer(&dev_view, ctx->up_host, 0));
+  for (const Item &it : items) {
+    const int64_t n = (int64_t)it.bytes;
+    unsigned char *dst = static_cast<unsigned char *>(it.dst);
+    const unsigned char *src = static_cast<const unsigned char *>(dev_view) + it.off;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+      const unsigned blocks = (unsigned)std::min<int64_t>((n / 16 + 255) / 256 + 1, 1024);
+      k_copy_aligned<<<blocks, 256, 0, s>>>(dst, src, n);
+    } else {
+      const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);
+      k_copy_bytes<<<blocks, 256, 0, s>>>(dst, src, n);
+    }
+    BST_CHECK_LAUNCH();
+  }
+  BST_CUDA(cudaStreamSynchronize(s));
   items.clear();
   used = 0;
 }

@@ -394,15 +394,11 @@ static std::vector<int32_t> distinct_sorted(const std::vector<int32_t> &v) {
 }
 
 static int32_t *upload_classes(const std::vector<int32_t> &sizes, const std::vector<int32_t> &vals,
-                               Arena &ar, cudaStream_t s, std::vector<int32_t> &host_keep) {
-  host_keep.resize(sizes.size());
+                               Arena &ar, Upload &up) {
+  std::vector<int32_t> cls(sizes.size());
   for (size_t i = 0; i < sizes.size(); ++i)
-    host_keep[i] = (int32_t)(std::lower_bound(vals.begin(), vals.end(), sizes[i]) - vals.begin());
-  int32_t *d = ar.alloc_n<int32_t>(sizes.size());
-  if (!sizes.empty())
-    BST_CUDA(cudaMemcpyAsync(d, host_keep.data(), sizeof(int32_t) * sizes.size(),
-                             cudaMemcpyHostToDevice, s));
-  return d;
+    cls[i] = (int32_t)(std::lower_bound(vals.begin(), vals.end(), sizes[i]) - vals.begin());
+  return up.add_vector(ar, cls);
 }
 
 void symbolic_phase(bst_plan *p, cudaStream_t s) {
@@ -424,11 +420,11 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
   const int64_t nb_all = (int64_t)p->Dm * p->Dn * p->Dk;
   BST_REQUIRE(nb_all <= (1 << 20), BST_ERR_UNSUPPORTED, "more than 2^20 (m,n,k) size buckets");
   p->nb_all = (int32_t)nb_all;
-  std::vector<int32_t> hm, hn, hk;
-  p->m_cls = upload_classes(oa.h_rs, p->m_vals, ar, s, hm);
-  p->n_cls = upload_classes(ob.h_cs, p->n_vals, ar, s, hn);
-  p->k_cls = upload_classes(oa.h_cs, p->k_vals, ar, s, hk);
   {
+    Upload up(p->ctx, s);
+    p->m_cls = upload_classes(oa.h_rs, p->m_vals, ar, up);
+    p->n_cls = upload_classes(ob.h_cs, p->n_vals, ar, up);
+    p->k_cls = upload_classes(oa.h_cs, p->k_vals, ar, up);
     std::vector<int32_t> cm((size_t)p->Dm * p->Dn), cn((size_t)p->Dm * p->Dn), kv(p->k_vals);
     for (int32_t a = 0; a < p->Dm; ++a)
       for (int32_t b = 0; b < p->Dn; ++b) {
@@ -436,13 +432,10 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
         cn[(size_t)a * p->Dn + b] = p->n_vals.empty() ? 0 : p->n_vals[b];
       }
     if (kv.empty()) kv.push_back(0);
-    p->cls_m = ar.alloc_n<int32_t>(cm.size());
-    p->cls_n = ar.alloc_n<int32_t>(cn.size());
-    p->kval = ar.alloc_n<int32_t>(kv.size());
-    BST_CUDA(cudaMemcpyAsync(p->cls_m, cm.data(), 4 * cm.size(), cudaMemcpyHostToDevice, s));
-    BST_CUDA(cudaMemcpyAsync(p->cls_n, cn.data(), 4 * cn.size(), cudaMemcpyHostToDevice, s));
-    BST_CUDA(cudaMemcpyAsync(p->kval, kv.data(), 4 * kv.size(), cudaMemcpyHostToDevice, s));
-    BST_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+    p->cls_m = up.add_vector(ar, cm);
+    p->cls_n = up.add_vector(ar, cn);
+    p->kval = up.add_vector(ar, kv);
+    up.done();  // host vectors go out of scope
   }
 
   // block norms (filter input)
@@ -547,8 +540,9 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
   }
   {
     const int32_t tv = (int32_t)T;
-    BST_CUDA(cudaMemcpyAsync(p->t_start + nnzC, &tv, 4, cudaMemcpyHostToDevice, s));
-    BST_CUDA(cudaStreamSynchronize(s));  // tv lives on this frame
+    Upload up(p->ctx, s);
+    up.add(p->t_start + nnzC, &tv, 4);
+    up.done();  // tv lives on this frame
   }
 
   // element offsets and (m,n) class of every C block

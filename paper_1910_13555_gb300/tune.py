@@ -14,6 +14,10 @@ For every class present in a plan the tuner times the plan's execute with that c
 to each choice (the others unchanged), keeps the fastest, and returns a table that can be
 saved as JSON (keyed by GPU name) and applied to a context later.
 
+Per contraction, tune_contract_slab chooses between the two remaps of a first tensor
+stored as (outer contracted, free, inner contracted) modes: a permuted copy before every
+execute, or reading each block in place as consecutive contiguous slabs.
+
 Timing uses CUDA events on the current stream, after a warm-up, minimum over repeats.
 """
 from __future__ import annotations
@@ -81,6 +85,28 @@ def tune_fp64_split(plan, device=0, reps=3, choices=SPLIT_CHOICES) -> dict:
         bst.bst_tune_set(ctx, bst.BST_TUNE_F64_SPLIT, best, m, n)
         table[(m, n)] = {"split": best, "ms": times}
     return table
+
+
+def tune_contract_slab(T1, T2, c1, c2, f1, f2, result_order=None, R_in=None, eps=0.0, device=0,
+                       reps=3) -> dict:
+    """Choose how a contraction reads a first tensor stored (outer contracted, free, inner
+    contracted): in place as slabs (1) or through a permuted copy (0).  Builds the plan
+    both ways, times its native-FP64 execute, leaves the faster choice set in the context
+    (BST_TUNE_CONTRACT_SLAB, taken by plans created afterwards).  Returns
+    {"slab": best, "ms": {0: t0, 1: t1}, "eligible": {0: ..., 1: ...}} where eligible says
+    whether the plan really read slabs."""
+    ctx = bst.context(device)
+    times, used = {}, {}
+    for v in (0, 1):
+        bst.bst_tune_set(ctx, bst.BST_TUNE_CONTRACT_SLAB, v)
+        plan = bst.contract_plan(T1, T2, c1, c2, f1, f2, result_order, R_in, eps, device)
+        plan.alloc_result(device)
+        times[v] = time_execute(plan, bst.BST_FP64, reps)
+        used[v] = plan.schedule_info()["slab"] == bool(v)
+        del plan
+    best = min(times, key=times.get)
+    bst.bst_tune_set(ctx, bst.BST_TUNE_CONTRACT_SLAB, best)
+    return {"slab": best, "ms": times, "eligible": used}
 
 
 def gpu_name(device=0) -> str:

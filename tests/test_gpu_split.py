@@ -144,3 +144,18 @@ def test_split_bound_rejects_bad_values(ctx):
             bst.bst_tune_set(ctx, bst.BST_TUNE_F64_SPLIT, v, 5, 13)
         assert e.value.name == "BST_ERR_INVALID_ARG"
     assert bst.bst_tune_get(ctx, bst.BST_TUNE_F64_SPLIT, 5, 13) == -1
+
+
+def test_split_never_outgrows_a_small_slot(ctx):
+    # only 5 x 5 x 5 products, ~15 per C block: a slot holds 50 doubles, fewer than the
+    # 125 partial sums a 5-way split would add through it
+    rng = np.random.default_rng(44)
+    sz = np.full(60, 5, np.int32)
+    A = make_matrix(rng, sz, sz, *bernoulli_pattern(rng, 60, 60, 0.5))
+    B = make_matrix(rng, sz, sz, *bernoulli_pattern(rng, 60, 60, 0.5))
+    p = Problem(A, B)
+    out = run_multiply(p, stacks=False)
+    ref = _ref(p)
+    assert rel_fro(out["data"], ref["data"]) <= 1e-12
+    hist = out["plan"].split_histogram()
+    assert hist[3:].sum() == 0  # s m n <= 50
