@@ -805,6 +805,13 @@ __device__ int f64_split_of(int32_t *__restrict__ d, const int4 *__restrict__ en
   int best = 1;
   c1 = 0;
   saved = 0;
+  // short tiles (most of a plan of small products) never split: one pass over the widths
+  long long w1 = 0;
+  for (int e = 0; e < ne; ++e) w1 += ents[(int64_t)d[1] + e].z;
+  if (w1 < kSplitMinInner || smax < 2) {
+    c1 = v1 * w1;
+    return 1;
+  }
   long long W[kMaxSplit + 1];
   for (int s = 1; s <= max(smax, 1); ++s) W[s] = 0;
   for (int e = 0; e < ne; ++e) {
@@ -1122,7 +1129,7 @@ void refresh_f64_split(bst_plan *p, cudaStream_t s) {
   // (a longer loop body, more instruction-fetch stalls), so a plan splits only when the
   // chosen splits save at least 1/25 of all its FP64 instructions.
   p->stage_split = sums[1] > 0 && 25 * sums[1] >= sums[0];
-  if (!p->stage_split) {
+  if (!p->stage_split && sums[1] > 0) {  // with no saving every tile already has s = 1
     k_f64_nosplit<<<nblk(p->n_tiles, 256), 256, 0, s>>>(p->n_tiles, p->fdesc);
     BST_CHECK_LAUNCH();
   }
