@@ -265,9 +265,9 @@ bst_status bst_plan_destroy(bst_plan *plan);
  *     stored as (outer contracted modes, free modes, inner contracted modes), e.g.
  *     T(P, mu, nu) contracted over (P, nu), its matrix view is read in place as
  *     consecutive contiguous slabs by native-FP64 executes that run the staged kernel
- *     (no permuted copy is made before them); 0 = always through the permuted copy
- *     (default).  Taken when a contraction plan is created; tune.tune_contract_slab
- *     times both on a given contraction.
+ *     (no permuted copy is made before them) (default); 0 = always through the permuted
+ *     copy.  Taken when a contraction plan is created; tune.tune_contract_slab times
+ *     both on a given contraction.
  * Changing a choice takes effect at the next execute of a plan; a batch built before
  * the change refuses emulated-FP64 execution (BST_ERR_STATE) and must be created again.
  * A plan or batch whose native-FP64 tiles must be split again after a change returns

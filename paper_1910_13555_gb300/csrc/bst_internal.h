@@ -98,7 +98,7 @@ struct bst_ctx {
   std::map<std::pair<int32_t, int32_t>, int32_t> tune_f64_split;
   // contractions: read an operand whose matrix view is a sequence of contiguous slabs of
   // each tensor block in place (1) or through a permuted copy (0)
-  int tune_contract_slab = 0;
+  int tune_contract_slab = 1;
   int64_t tune_version = 0;
 };
 

@@ -367,31 +367,12 @@ __device__ __forceinline__ void stage_product(double *slot, const double *a, con
     stage_2d<STRIDED>(slot + m * w, b, w, n, sb);
 }
 
-// acc[r] += op(A)(p_r, :) . op(B)(:, q_r) from a slot, o = lane + 32 r = p_r N + q_r
-template <int M, int N, int KC>
-__device__ __forceinline__ void slot_product(const NumParams &P, const double *__restrict__ As,
-                                             int kk, double (&acc)[kMaxR]) {
-  constexpr int MN = M * N, R = (MN + 31) / 32;
-  static_assert(R <= kMaxR, "C block too large for the staged kernel");
-  const int lane = threadIdx.x & 31;
-  const int k = KC ? KC : kk;
-  const double *__restrict__ Bs = As + M * k;
-  const int a_sp = P.ta ? 1 : k, a_sl = P.ta ? M : 1;
-  const int b_sl = P.tb ? 1 : N, b_sq = P.tb ? k : 1;
-#pragma unroll 1
-  for (int l = 0; l < k; ++l) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int o = lane + 32 * r;
-      if (r < R - 1 || o < MN)
-        acc[r] = fma(As[(o / N) * a_sp + l * a_sl], Bs[(o % N) * b_sq + l * b_sl], acc[r]);
-    }
-  }
-}
-
-// any (m, n) with m n <= 32 R: runtime sizes, R accumulators
-// any (m, n) with m n <= 32 kMaxR: runtime sizes, one body for every size (a body per
-// accumulator count thrashed the instruction cache on plans with many block sizes)
+// acc[r] += op(A)(p_r, :) . op(B)(:, q_r) from a slot for o = lane + 32 r = p_r n + q_r:
+// any (m, n) with m n <= 32 kMaxR, runtime sizes, one body for every size.  Bodies
+// specialised at compile time per (m, n) in {5, 13, 23}^2 and k in {5, 13, 23} were no
+// faster on GB300 (the FP64 pipe, not the index arithmetic, bounds the product) and their
+// code cost instruction-fetch stalls; one body per accumulator count thrashed the
+// instruction cache outright.
 __device__ __forceinline__ void slot_product_rt(const NumParams &P, const double *__restrict__ As,
                                                 int m, int n, int k, double (&acc)[kMaxR]) {
   const int lane = threadIdx.x & 31, mn = m * n;
@@ -487,31 +468,8 @@ __device__ __forceinline__ void split_reduce(double *red, int mn, int s, double 
   __syncwarp();
 }
 
-template <int M, int N>
-__device__ __forceinline__ void slot_product_k(const NumParams &P, const double *As, int k,
-                                               double (&acc)[kMaxR]) {
-  switch (k) {
-    case 5: slot_product<M, N, 5>(P, As, k, acc); break;
-    case 13: slot_product<M, N, 13>(P, As, k, acc); break;
-    case 23: slot_product<M, N, 23>(P, As, k, acc); break;
-    default: slot_product<M, N, 0>(P, As, k, acc); break;
-  }
-}
-
 __device__ __forceinline__ void slot_dispatch(const NumParams &P, const double *As, int m, int n,
                                               int k, double (&acc)[kMaxR]) {
-#define BST_MN(MM, NN) \
-  if (m == MM && n == NN) { slot_product_k<MM, NN>(P, As, k, acc); return; }
-  BST_MN(5, 5)
-  BST_MN(5, 13)
-  BST_MN(5, 23)
-  BST_MN(13, 5)
-  BST_MN(13, 13)
-  BST_MN(13, 23)
-  BST_MN(23, 5)
-  BST_MN(23, 13)
-  BST_MN(23, 23)
-#undef BST_MN
   slot_product_rt(P, As, m, n, k, acc);
 }
 
