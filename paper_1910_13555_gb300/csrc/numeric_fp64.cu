@@ -671,17 +671,65 @@ __global__ void k_f64_ent_count(int64_t nc, const int32_t *__restrict__ c_cls,
   for (int t = 0; t < nt; ++t) cnt[tbeg[c] + t] = s;
 }
 
-// descriptors and entries of every tile of block c, and each tile's cost key
-// (63 - floor(log2(flops)): a stable partition on it lists costly tiles first)
-__global__ void k_f64_tiles(int64_t nc, const int32_t *__restrict__ c_cls,
-                            const int32_t *__restrict__ run_start, const int32_t *__restrict__ run_len,
-                            const int32_t *__restrict__ s_a, const int32_t *__restrict__ s_b,
-                            const int64_t *__restrict__ c_off, const int32_t *__restrict__ c_cin,
-                            const int64_t *__restrict__ tbeg, const int64_t *__restrict__ ebeg,
-                            SchedTabs S, int32_t *__restrict__ desc, int4 *__restrict__ ents,
-                            int32_t *__restrict__ key) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
+// Inner split of every tile (descriptor word 7): the s <= smax of the tile's class that
+// needs the fewest FP64 warp instructions -- ceil(s mt n / 32) for each of the
+// ceil(w / s) steps of a panel of width w, plus (s - 1) ceil(mt n / 32) adds for the
+// final sums -- when it saves anything on a tile with at least kSplitLongInner inner
+// elements in all, at least 1/8 of the unsplit count on one with kSplitMinInner or more,
+// else 1 (on short tiles the final sums cost more than the idle lanes).  The plan-wide
+// sums of the unsplit counts and of the savings decide whether the plan splits at all
+// (refresh_f64_split).
+constexpr int kMaxSplit = 16;
+constexpr int kSplitMinInner = 48;
+constexpr int kSplitLongInner = 128;
+
+__device__ int f64_split_of(int32_t *__restrict__ d, const int4 *__restrict__ ents, int smax,
+                            int slot_elems, long long &c1, long long &saved) {
+  const int mn = (d[3] & 0xfff) * ((d[3] >> 12) & 0xfff), ne = d[2];
+  // s m n partial sums fit the accumulators and, for the final sums, one slot
+  smax = min(min(smax, kMaxSplit), min(kTile, slot_elems) / max(mn, 1));
+  const long long v1 = (mn + 31) / 32;
+  int best = 1;
+  c1 = 0;
+  saved = 0;
+  // short tiles (most of a plan of small products) never split: one pass over the widths
+  long long w1 = 0;
+  for (int e = 0; e < ne; ++e) w1 += ents[(int64_t)d[1] + e].z;
+  if (w1 < kSplitMinInner || smax < 2) {
+    c1 = v1 * w1;
+    return 1;
+  }
+  long long W[kMaxSplit + 1];
+  for (int s = 1; s <= max(smax, 1); ++s) W[s] = 0;
+  for (int e = 0; e < ne; ++e) {
+    const int w = ents[(int64_t)d[1] + e].z;
+    for (int s = 1; s <= max(smax, 1); ++s) W[s] += (w + s - 1) / s;
+  }
+  c1 = v1 * W[1];
+  long long cb = c1;
+  for (int s = 2; s <= smax; ++s) {
+    const long long c = (long long)((s * mn + 31) / 32) * W[s] + (s - 1) * v1;
+    if (c < cb) {
+      cb = c;
+      best = s;
+    }
+  }
+  if ((W[1] >= kSplitLongInner ? cb >= c1 : 8 * cb > 7 * c1) || W[1] < kSplitMinInner) best = 1;
+  if (best > 1) saved = c1 - cb;
+  return best;
+}
+
+// descriptors and entries of every tile of C block c, each tile's cost key
+// (63 - floor(log2(flops)): a stable partition on it lists costly tiles first) and its
+// inner split, with its FP64 instruction counts added to c1_sum / saved_sum
+__device__ __forceinline__ void f64_tiles_of(
+    int64_t c, const int32_t *__restrict__ c_cls, const int32_t *__restrict__ run_start,
+    const int32_t *__restrict__ run_len, const int32_t *__restrict__ s_a,
+    const int32_t *__restrict__ s_b, const int64_t *__restrict__ c_off,
+    const int32_t *__restrict__ c_cin, const int64_t *__restrict__ tbeg,
+    const int64_t *__restrict__ ebeg, const SchedTabs &S, int32_t *__restrict__ desc,
+    int4 *__restrict__ ents, int32_t *__restrict__ key, const int32_t *__restrict__ cls_smax,
+    int slot_elems, long long &c1_sum, long long &saved_sum) {
   const int cls = c_cls[c];
   const int m = S.cls_m[cls], n = S.cls_n[cls], tr = S.tile_rows[cls];
   const int nt = (m + tr - 1) / tr;
@@ -737,57 +785,35 @@ __global__ void k_f64_tiles(int64_t nc, const int32_t *__restrict__ c_cls,
     d[4] = c_cin[c];
     d[5] = p0 * n;
     d[6] = (int32_t)c;
-    d[7] = 0;
     key[tile] = __clzll(flops + 1ull);
+    long long c1, saved;
+    d[7] = f64_split_of(d, ents, cls_smax[cls], slot_elems, c1, saved);
+    c1_sum += c1;
+    saved_sum += saved;
   }
 }
 
-// Inner split of every tile (descriptor word 7): the s <= smax of the tile's class that
-// needs the fewest FP64 warp instructions -- ceil(s mt n / 32) for each of the
-// ceil(w / s) steps of a panel of width w, plus (s - 1) ceil(mt n / 32) adds for the
-// final sums -- when it saves anything on a tile with at least kSplitLongInner inner
-// elements in all, at least 1/8 of the unsplit count on one with kSplitMinInner or more,
-// else 1 (on short tiles the final sums cost more than the idle lanes).  The plan-wide
-// sums of the unsplit counts and of the savings decide whether the plan splits at all
-// (refresh_f64_split).
-constexpr int kMaxSplit = 16;
-constexpr int kSplitMinInner = 48;
-constexpr int kSplitLongInner = 128;
-
-__device__ int f64_split_of(int32_t *__restrict__ d, const int4 *__restrict__ ents, int smax,
-                            int slot_elems, long long &c1, long long &saved) {
-  const int mn = (d[3] & 0xfff) * ((d[3] >> 12) & 0xfff), ne = d[2];
-  // s m n partial sums fit the accumulators and, for the final sums, one slot
-  smax = min(min(smax, kMaxSplit), min(kTile, slot_elems) / max(mn, 1));
-  const long long v1 = (mn + 31) / 32;
-  int best = 1;
-  c1 = 0;
-  saved = 0;
-  // short tiles (most of a plan of small products) never split: one pass over the widths
-  long long w1 = 0;
-  for (int e = 0; e < ne; ++e) w1 += ents[(int64_t)d[1] + e].z;
-  if (w1 < kSplitMinInner || smax < 2) {
-    c1 = v1 * w1;
-    return 1;
+// all C blocks; sums[0] += unsplit FP64 instruction counts, sums[1] += split savings
+__global__ void k_f64_tiles(int64_t nc, const int32_t *__restrict__ c_cls,
+                            const int32_t *__restrict__ run_start, const int32_t *__restrict__ run_len,
+                            const int32_t *__restrict__ s_a, const int32_t *__restrict__ s_b,
+                            const int64_t *__restrict__ c_off, const int32_t *__restrict__ c_cin,
+                            const int64_t *__restrict__ tbeg, const int64_t *__restrict__ ebeg,
+                            SchedTabs S, int32_t *__restrict__ desc, int4 *__restrict__ ents,
+                            int32_t *__restrict__ key, const int32_t *__restrict__ cls_smax,
+                            int slot_elems, unsigned long long *__restrict__ sums) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  long long c1_sum = 0, saved_sum = 0;
+  if (c < nc) f64_tiles_of(c, c_cls, run_start, run_len, s_a, s_b, c_off, c_cin, tbeg, ebeg, S,
+                           desc, ents, key, cls_smax, slot_elems, c1_sum, saved_sum);
+  for (int o = 16; o > 0; o >>= 1) {
+    c1_sum += __shfl_down_sync(0xffffffffu, c1_sum, o);
+    saved_sum += __shfl_down_sync(0xffffffffu, saved_sum, o);
   }
-  long long W[kMaxSplit + 1];
-  for (int s = 1; s <= max(smax, 1); ++s) W[s] = 0;
-  for (int e = 0; e < ne; ++e) {
-    const int w = ents[(int64_t)d[1] + e].z;
-    for (int s = 1; s <= max(smax, 1); ++s) W[s] += (w + s - 1) / s;
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sums[0], (unsigned long long)c1_sum);
+    if (saved_sum) atomicAdd(&sums[1], (unsigned long long)saved_sum);
   }
-  c1 = v1 * W[1];
-  long long cb = c1;
-  for (int s = 2; s <= smax; ++s) {
-    const long long c = (long long)((s * mn + 31) / 32) * W[s] + (s - 1) * v1;
-    if (c < cb) {
-      cb = c;
-      best = s;
-    }
-  }
-  if ((W[1] >= kSplitLongInner ? cb >= c1 : 8 * cb > 7 * c1) || W[1] < kSplitMinInner) best = 1;
-  if (best > 1) saved = c1 - cb;
-  return best;
 }
 
 // sums[0] += unsplit FP64 instruction counts, sums[1] += savings of the chosen splits
@@ -939,6 +965,9 @@ void sort_items(const int64_t *items, const int32_t *keys, int64_t n, int64_t *o
 // Tiles, entries, descriptors and slot size of the staged kernel; false (stage_elems
 // stays 0) when a block size does not fit the descriptor's 12 bits or a row of C (n
 // elements) exceeds one output tile.
+static std::vector<int32_t> class_split_bounds(const bst_plan *p);
+static void apply_split_gate(bst_plan *p, const unsigned long long sums[2], cudaStream_t s);
+
 static bool build_staged(bst_plan *p, cudaStream_t s) {
   p->stage_elems = 0;
   p->n_tiles = 0;
@@ -980,14 +1009,17 @@ static bool build_staged(bst_plan *p, cudaStream_t s) {
   Arena scratch;
   scratch.ctx = static_cast<Ctx *>(p->ctx);
   scratch.stream = s;
-  int32_t *d_tr, *d_wp, *d_kin = nullptr;
+  int32_t *d_tr, *d_wp, *d_kin = nullptr, *d_smax;
   {
     Upload up(p->ctx, s);
     d_tr = up.add_vector(scratch, tile_rows);
     d_wp = up.add_vector(scratch, wpanel);
+    d_smax = up.add_vector(scratch, class_split_bounds(p));
     if (slab) d_kin = up.add_vector(scratch, p->a_slab_kin);
     up.done();
   }
+  unsigned long long *d_sums = scratch.alloc_n<unsigned long long>(2);
+  BST_CUDA(cudaMemsetAsync(d_sums, 0, 2 * sizeof(unsigned long long), s));
   SchedTabs S;
   S.cls_m = p->cls_m;
   S.cls_n = p->cls_n;
@@ -1029,7 +1061,7 @@ static bool build_staged(bst_plan *p, cudaStream_t s) {
   p->tkeys = ar.alloc_n<int32_t>((size_t)ntiles);
   k_f64_tiles<<<nblk(nc, 256), 256, 0, s>>>(nc, p->c_cls, p->run_start, p->run_len, p->s_a,
                                             p->s_b, p->C->off, p->c_cin, tbeg, ebeg, S, p->fdesc,
-                                            p->fents, p->tkeys);
+                                            p->fents, p->tkeys, d_smax, (int)slot, d_sums);
   BST_CHECK_LAUNCH();
   // tiles by decreasing cost
   int64_t *it0 = scratch.alloc_n<int64_t>((size_t)ntiles);
@@ -1037,15 +1069,43 @@ static bool build_staged(bst_plan *p, cudaStream_t s) {
   k_plan_items<<<nblk(ntiles, 256), 256, 0, s>>>(ntiles, 0, it0);
   BST_CHECK_LAUNCH();
   sort_items(it0, p->tkeys, ntiles, p->titems, scratch, s);
-  BST_CUDA(cudaStreamSynchronize(s));
+  unsigned long long sums[2] = {0, 0};
+  {
+    ReadBack rb(p->ctx, s);
+    rb.add(sums, d_sums, sizeof(sums));
+    rb.done();
+  }
   scratch.release_all();
   p->n_tiles = ntiles;
   p->stage_elems = (int32_t)slot;
   p->stage_strided = strided;
   p->a_slab = slab;
-  p->split_version = -1;
-  refresh_f64_split(p, s);
+  apply_split_gate(p, sums, s);
   return true;
+}
+
+// per (m, n) class of the plan, the largest inner split the context's tuning allows
+static std::vector<int32_t> class_split_bounds(const bst_plan *p) {
+  const Ctx *ctx = static_cast<const Ctx *>(p->ctx);
+  const int32_t ncls = p->Dm * p->Dn;
+  std::vector<int32_t> smax((size_t)ncls, kMaxSplit);
+  for (int32_t c = 0; c < ncls; ++c) {
+    auto it = ctx->tune_f64_split.find({(int32_t)p->m_vals[c / p->Dn], (int32_t)p->n_vals[c % p->Dn]});
+    if (it != ctx->tune_f64_split.end()) smax[(size_t)c] = it->second;
+  }
+  return smax;
+}
+
+// The plan runs the split instance only when the chosen splits save at least 1/25 of all
+// its FP64 instructions (a safeguard: a longer loop body once cost every tile a few per
+// cent); otherwise every tile is set back to s = 1.
+static void apply_split_gate(bst_plan *p, const unsigned long long sums[2], cudaStream_t s) {
+  p->stage_split = sums[1] > 0 && 25 * sums[1] >= sums[0];
+  if (!p->stage_split && sums[1] > 0) {  // with no saving every tile already has s = 1
+    k_f64_nosplit<<<nblk(p->n_tiles, 256), 256, 0, s>>>(p->n_tiles, p->fdesc);
+    BST_CHECK_LAUNCH();
+  }
+  p->split_version = static_cast<const Ctx *>(p->ctx)->tune_version;
 }
 
 // (Re)choose the inner split of every staged tile for the context's current tuning.
@@ -1057,12 +1117,7 @@ void refresh_f64_split(bst_plan *p, cudaStream_t s) {
   BST_REQUIRE(cap == cudaStreamCaptureStatusNone, BST_ERR_STATE,
               "the context's tuning changed since the plan's FP64 tiles were split; "
               "execute once outside stream capture");
-  const int32_t ncls = p->Dm * p->Dn;
-  std::vector<int32_t> smax((size_t)ncls, kMaxSplit);
-  for (int32_t c = 0; c < ncls; ++c) {
-    auto it = ctx->tune_f64_split.find({(int32_t)p->m_vals[c / p->Dn], (int32_t)p->n_vals[c % p->Dn]});
-    if (it != ctx->tune_f64_split.end()) smax[(size_t)c] = it->second;
-  }
+  const std::vector<int32_t> smax = class_split_bounds(p);
   Arena scratch;
   scratch.ctx = ctx;
   scratch.stream = s;
@@ -1083,15 +1138,7 @@ void refresh_f64_split(bst_plan *p, cudaStream_t s) {
     rb.add(sums, d_sums, sizeof(sums));
     rb.done();
   }
-  // The kernel instance with the split body runs every tile a few per cent slower
-  // (a longer loop body, more instruction-fetch stalls), so a plan splits only when the
-  // chosen splits save at least 1/25 of all its FP64 instructions.
-  p->stage_split = sums[1] > 0 && 25 * sums[1] >= sums[0];
-  if (!p->stage_split && sums[1] > 0) {  // with no saving every tile already has s = 1
-    k_f64_nosplit<<<nblk(p->n_tiles, 256), 256, 0, s>>>(p->n_tiles, p->fdesc);
-    BST_CHECK_LAUNCH();
-  }
-  p->split_version = ctx->tune_version;
+  apply_split_gate(p, sums, s);
 }
 
 // C blocks by decreasing cost, for the direct-load persistent kernel
