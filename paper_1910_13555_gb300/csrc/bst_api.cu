@@ -192,7 +192,11 @@ bst_status bst_matrix_create(bst_ctx *ctx, bst_matrix **out, int32_t nbr,
   }
   std::vector<int32_t> ord((size_t)nblocks);
   std::iota(ord.begin(), ord.end(), 0);
-  std::sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return key[x] < key[y]; });
+  // blocks given in row-major order (the usual case) need no sort
+  bool sorted = true;
+  for (int64_t b = 1; b < nblocks && sorted; ++b) sorted = key[b - 1] < key[b];
+  if (!sorted)
+    std::sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return key[x] < key[y]; });
   std::vector<int32_t> row((size_t)nblocks), col((size_t)nblocks), rowptr((size_t)nbr + 1, 0);
   std::vector<int64_t> off((size_t)nblocks);
   int64_t acc = 0;
