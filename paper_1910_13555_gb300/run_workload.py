@@ -1,7 +1,7 @@
 """Run one of the synthetic workloads through the library a few times (a driver for
 profilers and quick timings).
 
-    python -m paper_1910_13555_gb300.run_workload <name> [--reps N] [--precision P]
+    python -m paper_1910_13555_gb300.run_workload <name> [--reps N] [--precision P] [--nb N] [--np P]
 
 name: banded | tall_skinny | rect_case2 | batched | rank3 | rank4 | sign
 precision: fp64 | emu | tf32x3
@@ -31,6 +31,8 @@ def main(argv=None) -> int:
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
     ap.add_argument("--nb", type=int, default=None, help="banded / sign: blocks per side")
+    ap.add_argument("--np", type=int, default=None,
+                    help="rank3 / rank4: P blocks (fewer products per C block, same C pattern)")
     a = ap.parse_args(argv)
     prec = getattr(bst, PRECISIONS[a.precision])
 
@@ -48,7 +50,8 @@ def main(argv=None) -> int:
         flops = plan.stats()["flops"]
         run = lambda: plan.execute(1.0, 0.0, prec, 1)  # noqa: E731
     elif a.name in ("rank3", "rank4"):
-        w = workloads.rank3() if a.name == "rank3" else workloads.rank4()
+        kw = {} if a.np is None else {"nP": a.np}
+        w = workloads.rank3(**kw) if a.name == "rank3" else workloads.rank4(**kw)
         t1 = bst.Tensor.from_host(w.T1.block_sizes, w.T1.index, w.T1.data)
         t2 = bst.Tensor.from_host(w.T2.block_sizes, w.T2.index, w.T2.data)
         plan = bst.contract(t1, t2, w.c1, w.c2, w.f1, w.f2, w.result_order, precision=prec)
