@@ -284,7 +284,10 @@ __global__ void __launch_bounds__(256, 2)
 
 constexpr int kMaxR = 17;         // accumulators per lane: tiles up to 544 elements
 constexpr int kTile = 32 * kMaxR;
-constexpr int kStageMax = 1536;   // doubles per slot (two slots per warp)
+// doubles per slot (two slots per warp): at most 1184 keeps three 4-warp CTAs resident
+// per SM (3 x (2 x 4 x 1184 x 8 B + 1 KB) <= 228 KB); the panels get narrower, but with
+// 1536 the contraction plans ran 2 CTAs per SM and lost 8-9 % (FP64 pipe 68-82 % busy)
+constexpr int kStageMax = 1184;
 constexpr int kStageWarps = 4;    // warps per CTA
 constexpr int kF64Desc = kF64DescWords;
 
