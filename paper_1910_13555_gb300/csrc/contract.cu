@@ -120,6 +120,8 @@ __global__ void k_volumes(VolArgs V) {
 // element permutation between tensor blocks (row-major over modes 0..rank-1) and view
 // blocks (row-major over modes ord[0..rank-1]); to_view: view <- tensor, else
 // tensor <- view
+constexpr int kPermThreads = 256;  // threads per tensor block in k_permute
+
 struct PermArgs {
   int64_t nblocks;
   int32_t rank;
@@ -131,9 +133,12 @@ struct PermArgs {
   int to_view;
 };
 
+// One CTA per tensor block: its elements are visited in view order, which reads (or
+// writes) the tensor layout out of order; with one block in flight per CTA (a few per
+// SM) its lines stay in L1 / L2 until every element is used.  A warp per block, with
+// dozens of blocks of up to ~175 KB in flight per SM, re-fetched them from DRAM.
 __global__ void k_permute(PermArgs P) {
-  const int lane = threadIdx.x & 31;
-  const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t q = blockIdx.x;
   if (q >= P.nblocks) return;
   const int64_t tb = P.tblk ? P.tblk[q] : q;
   const int32_t *t = P.idx + tb * P.rank;
@@ -147,7 +152,7 @@ __global__ void k_permute(PermArgs P) {
     len *= s[d];
   }
   const int64_t to = P.toff[tb], vo = P.voff[q];
-  for (int32_t e = lane; e < len; e += 32) {
+  for (int32_t e = threadIdx.x; e < len; e += blockDim.x) {
     int32_t rem = e, src = 0;
     for (int j = P.rank - 1; j >= 0; --j) {
       const int d = P.ord[j];
@@ -355,8 +360,7 @@ void permute_view(const View &V, const double *src, double *dst, bool to_view, c
   P.src = src;
   P.dst = dst;
   P.to_view = to_view;
-  const int wpb = 8;
-  k_permute<<<nblk(P.nblocks, wpb), 32 * wpb, 0, s>>>(P);
+  k_permute<<<(unsigned)P.nblocks, kPermThreads, 0, s>>>(P);
   BST_CHECK_LAUNCH();
 }
 
@@ -476,8 +480,7 @@ void contract_finish(bst_plan *p, cudaStream_t s) {
   P.src = K.cbuf;
   P.dst = K.R->data;
   P.to_view = 0;
-  const int wpb = 8;
-  k_permute<<<nblk(P.nblocks, wpb), 32 * wpb, 0, s>>>(P);
+  k_permute<<<(unsigned)P.nblocks, kPermThreads, 0, s>>>(P);
   BST_CHECK_LAUNCH();
 }
 
@@ -501,8 +504,7 @@ void contract_adjoint(bst_plan *p, const double *dR, double *dT1, double *dT2, d
     P.src = dR;
     P.dst = K.dcbuf;
     P.to_view = 1;
-    const int wpb = 8;
-    k_permute<<<nblk(P.nblocks, wpb), 32 * wpb, 0, s>>>(P);
+    k_permute<<<(unsigned)P.nblocks, kPermThreads, 0, s>>>(P);
     BST_CHECK_LAUNCH();
     dC = K.dcbuf;
   }
