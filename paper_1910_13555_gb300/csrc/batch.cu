@@ -4,8 +4,8 @@
 // (their symbolic phases are done).  Its work list is every C block of every plan,
 // tagged with the plan's index.  For native FP64 the list is sorted by decreasing cost
 // across the batch, so one persistent grid balances products of very different sizes
-// (the staged kernel takes items in a fixed stride, the direct-load kernel from a
-// counter).  For emulated FP64 the plans are listed by
+// (the staged kernel takes chunks of items from a counter after two of its own, the
+// direct-load kernel single items from a counter).  For emulated FP64 the plans are listed by
 // decreasing flops and each plan's C blocks in CSR order, and warps take a few
 // consecutive items at a time from a counter, so neighbouring warps share operand
 // digits.  bst_batch_execute only
@@ -212,7 +212,7 @@ bst_status bst_batch_execute(bst_batch *b, const double *alpha, const double *be
       BST_CUDA(cudaMemcpyAsync(b->d_params, b->h_params, b->pbytes * n, cudaMemcpyHostToDevice, s));
       if (b->stage_elems > 0)
         bst::launch_fp64_staged(b->d_params, b->titems, b->n_titems, b->stage_elems,
-                                b->stage_strided, split, b->ctx->num_sms, s);
+                                b->stage_strided, split, b->ctx->num_sms, b->counter, s);
       else
         bst::launch_fp64_persist(b->d_params, b->items, b->n_items, b->counter, b->grid, s);
     } else {

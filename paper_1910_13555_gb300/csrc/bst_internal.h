@@ -367,7 +367,8 @@ constexpr int kF64DescWords = 8;  // descriptor words per staged tile
 void build_plan_tile_items(bst_plan *p, int64_t base, int64_t *items, int32_t *keys,
                            cudaStream_t s);
 void launch_fp64_staged(const void *params, const int64_t *items, int64_t nitems,
-                        int slot_elems, bool strided, bool split, int num_sms, cudaStream_t s);
+                        int slot_elems, bool strided, bool split, int num_sms,
+                        unsigned long long *counter, cudaStream_t s);
 // persistent emulated-FP64 numeric (numeric_emu.cu)
 size_t emu_params_bytes();
 int64_t emu_item_count(bst_plan *p, cudaStream_t s);
