@@ -2,13 +2,14 @@
 profilers and quick timings).
 
     python -m paper_1910_13555_gb300.run_workload <name> [--reps N] [--precision P] [--nb N] [--np P]
+                                                        [--adjoint]
 
 name: banded | tall_skinny | rect_case2 | batched | rank3 | rank4 | sign
 precision: fp64 | emu | tf32x3
 
 Each run builds the plan once and executes it `reps` times (a batch for `batched`,
-one Newton-Schulz step for `sign`), then prints the flop count and the median CUDA-event
-time of the executes.
+one Newton-Schulz step for `sign`, the adjoint dT, dU with --adjoint for `rank3` and
+`rank4`), then prints the flop count and the median CUDA-event time of the executes.
 """
 from __future__ import annotations
 
@@ -33,6 +34,8 @@ def main(argv=None) -> int:
     ap.add_argument("--nb", type=int, default=None, help="banded / sign: blocks per side")
     ap.add_argument("--np", type=int, default=None,
                     help="rank3 / rank4: P blocks (fewer products per C block, same C pattern)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="rank3 / rank4: time the adjoint (dT, dU from dR = R) instead")
     a = ap.parse_args(argv)
     prec = getattr(bst, PRECISIONS[a.precision])
 
@@ -58,6 +61,14 @@ def main(argv=None) -> int:
         keep = [t1, t2, plan]
         flops = plan.stats()["flops"]
         run = lambda: plan.execute(1.0, 0.0, prec, 1)  # noqa: E731
+        if a.adjoint:
+            torch.cuda.synchronize()
+            ne = plan.result.info[2]
+            dR = plan.result.data[:ne].clone()
+            dT, dU = torch.empty_like(t1.data), torch.empty_like(t2.data)
+            keep += [dR, dT, dU]
+            flops = 2.0 * flops
+            run = lambda: bst.bst_plan_adjoint(plan.handle, dR, dT, dU, None, 1.0, 0.0)  # noqa: E731
     elif a.name == "batched":
         probs = workloads.batched()
         plans = []
