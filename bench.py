@@ -773,8 +773,16 @@ def other_configs(local_rank, stream):
     lens = np.ones(len(sel), np.int64)
     for d in range(3):
         lens *= rs[d][idx[sel, d]].astype(np.int64)
-    out["rank4_contraction"] = dict(rate(f, ms), rel_err_vs_oracle_sample=_rel(
-        _gather(R.data, offs[sel], lens), ref))
+    fwd4 = dict(rate(f, ms), rel_err_vs_oracle_sample=_rel(_gather(R.data, offs[sel], lens), ref))
+    ne = R.info[2]
+    dR = R.data[:ne].clone()
+    dV = torch.empty_like(t1.data)
+    dU = torch.empty_like(t2.data)
+    ms_adj = _median_ms(lambda: bst.bst_plan_adjoint(cplan.handle, dR, dV, dU, None, 1.0, 0.0),
+                        stream)
+    out["rank4_contraction"] = dict(fwd4, adjoint=dict(rate(2.0 * f, ms_adj),
+                                                       note="dV and dU, 2x the forward flop"))
+    del cplan, R, dR, dV, dU, t1, t2
     return out
 
 

@@ -10,8 +10,9 @@
 // Each output block has one owner warp (no atomics): the plan's stack entries are
 // grouped by stored A block and by stored B block once (stable counting sort, cached
 // in the plan), and warp `a` sums over the entries of A block `a`.  Lanes own output
-// elements (m x k of dop(A), k x n of dop(B)) in passes of 256; every block product
-// reads its dC block and the other operand's block from L1/L2.
+// elements (m x k of dop(A) column by column, k x n of dop(B) row by row) in passes of
+// 256, a block of more than 4 passes spread over several warps (chunks of 4 passes);
+// every block product reads its dC block and the other operand's block from L1/L2.
 #include <algorithm>
 
 #include "bst_internal.h"
@@ -38,25 +39,43 @@ struct AdjArgs {
   const int32_t *grp, *ptr;        // entries of each output block
   const int32_t *s_a, *s_b, *s_c, *s_cb;
   const int32_t *c_row, *c_col, *c_rsz, *c_csz;  // C block index and sizes
-  // stored blocks of the output side
+  // stored blocks of the output side; each is cut into nch chunks of `span` outputs
+  // (consecutive passes), one warp per (block, chunk), so that large blocks spread over
+  // several warps
   int64_t nblocks;
+  int32_t nch, span;
   const int32_t *row, *col, *rsz, *csz;
   const int64_t *off;
 };
 
-// dop(A) for stored A block b: lanes own (p, l) of the m x k op block
+// dop(A) for stored A block b: lanes own (p, l) of the m x k op block, numbered column
+// by column (o = l m + p), so that a pass of 32 RA outputs covers every row p of a few
+// columns l and reads each op(B) row it needs once per product.  (Numbered row by row,
+// a pass covered one or two rows p and every op(B) row came in again for each of the m
+// rows: on the rank-3 adjoint the kernel read 14.6 GB from DRAM for about 2 GB of
+// operands.)  The sums run over the entries, then q, in the same order either way.
 __global__ void k_adj_a(AdjArgs P) {
   const int lane = threadIdx.x & 31;
-  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t b = w / P.nch;
   if (b >= P.nblocks) return;
   const int R = P.rsz[P.row[b]], Cc = P.csz[P.col[b]];
   const int m = P.ta ? Cc : R, k = P.ta ? R : Cc;
+  const int64_t ob = (w - b * P.nch) * (int64_t)P.span;
+  if (ob >= m * k) return;
+  const int o1 = (int)min((int64_t)m * k, ob + P.span);
   const int e0 = P.ptr[b], e1 = P.ptr[b + 1];
   double *out = P.dA + P.off[b];
-  for (int o0 = 0; o0 < m * k; o0 += 32 * RA) {
+  for (int o0 = (int)ob; o0 < o1; o0 += 32 * RA) {
     double acc[RA];
+    int pr[RA], lr[RA];
 #pragma unroll
-    for (int r = 0; r < RA; ++r) acc[r] = 0.0;
+    for (int r = 0; r < RA; ++r) {
+      const int o = o0 + lane + 32 * r;
+      lr[r] = o / m;
+      pr[r] = o - lr[r] * m;
+      acc[r] = 0.0;
+    }
     for (int q0 = e0; q0 < e1; ++q0) {
       const int e = P.grp[q0];
       const int c = P.s_cb[e];
@@ -66,22 +85,18 @@ __global__ void k_adj_a(AdjArgs P) {
       const int b_sl = P.tb ? 1 : n, b_sq = P.tb ? k : 1;
 #pragma unroll
       for (int r = 0; r < RA; ++r) {
-        const int o = o0 + lane + 32 * r;
-        if (o < m * k) {
-          const int p = o / k, l = o % k;
+        if (o0 + lane + 32 * r < m * k) {
+          const double *gr = g + pr[r] * n, *br = bb + lr[r] * b_sl;
           double s = acc[r];
-          for (int q = 0; q < n; ++q) s = fma(__ldg(g + p * n + q), __ldg(bb + l * b_sl + q * b_sq), s);
+          for (int q = 0; q < n; ++q) s = fma(__ldg(gr + q), __ldg(br + q * b_sq), s);
           acc[r] = s;
         }
       }
     }
 #pragma unroll
     for (int r = 0; r < RA; ++r) {
-      const int o = o0 + lane + 32 * r;
-      if (o < m * k) {
-        const int p = o / k, l = o % k;
-        out[P.ta ? l * m + p : p * k + l] = P.alpha * acc[r];
-      }
+      if (o0 + lane + 32 * r < m * k)
+        out[P.ta ? lr[r] * m + pr[r] : pr[r] * k + lr[r]] = P.alpha * acc[r];
     }
   }
 }
@@ -89,13 +104,17 @@ __global__ void k_adj_a(AdjArgs P) {
 // dop(B) for stored B block b: lanes own (l, q) of the k x n op block
 __global__ void k_adj_b(AdjArgs P) {
   const int lane = threadIdx.x & 31;
-  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t b = w / P.nch;
   if (b >= P.nblocks) return;
   const int R = P.rsz[P.row[b]], Cc = P.csz[P.col[b]];
   const int k = P.tb ? Cc : R, n = P.tb ? R : Cc;
+  const int64_t ob = (w - b * P.nch) * (int64_t)P.span;
+  if (ob >= k * n) return;
+  const int o1 = (int)min((int64_t)k * n, ob + P.span);
   const int e0 = P.ptr[b], e1 = P.ptr[b + 1];
   double *out = P.dB + P.off[b];
-  for (int o0 = 0; o0 < k * n; o0 += 32 * RA) {
+  for (int o0 = (int)ob; o0 < o1; o0 += 32 * RA) {
     double acc[RA];
 #pragma unroll
     for (int r = 0; r < RA; ++r) acc[r] = 0.0;
@@ -140,6 +159,26 @@ __global__ void k_adj_cin(int64_t nc, const int32_t *c_cin, const int64_t *c_off
   if (ci < 0) return;
   const int len = rsz[c_row[c]] * csz[c_col[c]];
   for (int e = lane; e < len; e += 32) dCin[cin_off[ci] + e] = beta * dC[c_off[c] + e];
+}
+
+// Chunks of kAdjChunkPasses passes (of 32 RA outputs) per warp, as many per block as
+// the largest stored block of the output side needs; a warp whose chunk lies past its
+// block's end returns at once.  Without host block sizes: one chunk per block.
+constexpr int kAdjChunkPasses = 4;
+
+void chunking(AdjArgs &P, const bst_matrix &M) {
+  int32_t r = 0, c = 0;
+  for (int32_t v : M.h_rsz) r = std::max(r, v);
+  for (int32_t v : M.h_csz) c = std::max(c, v);
+  const int64_t span = (int64_t)kAdjChunkPasses * 32 * RA;
+  const int64_t most = (int64_t)r * c;
+  if (M.h_rsz.empty() || M.h_csz.empty() || most <= span) {
+    P.nch = 1;
+    P.span = 1 << 30;
+  } else {
+    P.nch = (int32_t)((most + span - 1) / span);
+    P.span = (int32_t)span;
+  }
 }
 
 }  // namespace
@@ -198,7 +237,8 @@ void adjoint_fp64(bst_plan *p, const double *A, const double *B, const double *d
     P.rsz = Am->rsz;
     P.csz = Am->csz;
     P.off = Am->off;
-    k_adj_a<<<nblk(Am->nblocks, wpb), 32 * wpb, 0, s>>>(P);
+    chunking(P, *Am);
+    k_adj_a<<<nblk(Am->nblocks * P.nch, wpb), 32 * wpb, 0, s>>>(P);
     BST_CHECK_LAUNCH();
   }
   if (Bm->nblocks > 0 && dB) {
@@ -210,7 +250,8 @@ void adjoint_fp64(bst_plan *p, const double *A, const double *B, const double *d
     P.rsz = Bm->rsz;
     P.csz = Bm->csz;
     P.off = Bm->off;
-    k_adj_b<<<nblk(Bm->nblocks, wpb), 32 * wpb, 0, s>>>(P);
+    chunking(P, *Bm);
+    k_adj_b<<<nblk(Bm->nblocks * P.nch, wpb), 32 * wpb, 0, s>>>(P);
     BST_CHECK_LAUNCH();
   }
 }
