@@ -53,22 +53,36 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // ---- block norms -------------------------------------------------------------------
 
+// One warp per group of 32 consecutive blocks.  Each block's sum of squares is summed
+// across the warp (lane-strided FMAs, then the butterfly) and parked in the lane of the
+// block's place in the group; the 32 square roots then run as one sequence.  GB300's
+// FP64 pipe takes as long for a warp instruction with one active lane as with 32, and
+// a square root is about a dozen of them: one per block made the kernel FP64-bound
+// (175 us for the banded workload's 1.6e5 blocks of A, against 27 us to read them).
+constexpr int kNormGroup = 32;
+
 __global__ void k_block_norms(int64_t nblocks, const int32_t *__restrict__ row,
                               const int32_t *__restrict__ col, const int32_t *__restrict__ rsz,
                               const int32_t *__restrict__ csz, const int64_t *__restrict__ off,
                               const double *__restrict__ data, double *__restrict__ norms) {
   const int lane = threadIdx.x & 31;
-  int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (b >= nblocks) return;
-  int64_t len = (int64_t)rsz[row[b]] * csz[col[b]];
-  const double *x = data + off[b];
-  double s = 0.0;
-  for (int64_t e = lane; e < len; e += 32) {
-    double v = __ldg(x + e);
-    s = fma(v, v, s);
+  const int64_t b0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kNormGroup;
+  if (b0 >= nblocks) return;
+  const int nb = (int)min((int64_t)kNormGroup, nblocks - b0);
+  double mine = 0.0;
+  for (int j = 0; j < nb; ++j) {
+    const int64_t b = b0 + j;
+    const int64_t len = (int64_t)rsz[row[b]] * csz[col[b]];
+    const double *x = data + off[b];
+    double s = 0.0;
+    for (int64_t e = lane; e < len; e += 32) {
+      double v = __ldg(x + e);
+      s = fma(v, v, s);
+    }
+    s = warp_sum_d(s);
+    if (lane == j) mine = s;
   }
-  s = warp_sum_d(s);
-  if (lane == 0) norms[b] = sqrt(s);
+  if (lane < nb) norms[b0 + lane] = sqrt(mine);
 }
 
 // ---- operand views -----------------------------------------------------------------
@@ -353,8 +367,9 @@ void block_norms(const bst_matrix *m, double *norms, cudaStream_t s) {
   if (m->nblocks == 0) return;
   BST_REQUIRE(m->data != nullptr, BST_ERR_STATE, "matrix data not bound");
   const int wpb = 8;
-  k_block_norms<<<nblk(m->nblocks, wpb), 32 * wpb, 0, s>>>(m->nblocks, m->row, m->col, m->rsz,
-                                                           m->csz, m->off, m->data, norms);
+  const int64_t groups = (m->nblocks + kNormGroup - 1) / kNormGroup;
+  k_block_norms<<<nblk(groups, wpb), 32 * wpb, 0, s>>>(m->nblocks, m->row, m->col, m->rsz,
+                                                       m->csz, m->off, m->data, norms);
   BST_CHECK_LAUNCH();
 }
 
