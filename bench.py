@@ -426,7 +426,8 @@ def run_ours(args):
                    "flop_per_step_per_gpu": flops, "c_blocks": stats["n_c_blocks"],
                    "stack_entries": stats["n_stack"], "filtered": stats["n_filtered"]},
         "numeric_only": {"value": flops / (num_avg * 1e-3) / 1e9, "unit": UNIT,
-                         "ms": num_avg},
+                         "ms": num_avg, "ms_median": statistics.median(num_ms),
+                         "launches_timed": len(num_ms)},
         "roofline": ({"bound": "alu", "kernel": kernel, "achieved": achieved,
                       "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                       "frac": achieved / FP64_PEAK_TFLOPS,
