@@ -207,6 +207,9 @@ enum {
  * warp; S > 1 = the K block range is cut into S equal parts whose partial sums go
  * to a workspace and are added in the fixed order 0..S-1 (paper Sec. 3.1);
  * 0 = choose S from the plan's shape.  With beta == 0 C_in is not read.
+ * Executes of one plan must not overlap on the GPU (e.g. on two streams at once):
+ * they write the same C_out and share the plan's work counter, from which the
+ * persistent kernels take their tiles; order them on one stream or with events.
  * Errors: STATE (C_out, A or B data not bound), INVALID_ARG, UNSUPPORTED. */
 bst_status bst_multiply_execute(bst_plan *plan, double alpha, double beta, int32_t precision,
                                 int32_t split_k, void *stream);
@@ -322,6 +325,8 @@ bst_status bst_plan_result_tensor(bst_plan *plan, bst_tensor **R);
  * Batches: many independent plans executed by one persistent kernel launch,
  * capturable into a CUDA graph.  Tile choices per (m,n) class come from the
  * library's tune table (bst_tune_*).  alpha/beta are host arrays of n values.
+ * Executes of one batch must not overlap on the GPU (they share its work counter),
+ * nor overlap an execute of one of its plans (they write the same C_out).
  * ------------------------------------------------------------------------- */
 bst_status bst_batch_create(bst_ctx *ctx, int32_t n, bst_plan *const *plans, bst_batch **out);
 bst_status bst_batch_execute(bst_batch *batch, const double *alpha, const double *beta,
