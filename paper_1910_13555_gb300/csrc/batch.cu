@@ -225,8 +225,14 @@ bst_status bst_batch_execute(bst_batch *b, const double *alpha, const double *be
                                     static_cast<char *>(b->h_eparams) + q * b->epbytes, s);
       }
       BST_CUDA(cudaMemcpyAsync(b->d_eparams, b->h_eparams, b->epbytes * n, cudaMemcpyHostToDevice, s));
+      double flops = 0.0;
+      int64_t nelem = 0;
+      for (auto *pl : b->plans) {
+        flops += pl->stats.flops;
+        nelem += pl->C->nelem;
+      }
       bst::launch_emu_persist(b->d_eparams, b->items_e, b->n_items_e, b->counter, b->grid_e,
-                              b->ctx->tune_emu_row_scale, s);
+                              b->ctx->tune_emu_row_scale, bst::emu_pipelined(flops, nelem), s);
     }
     for (int32_t q = 0; q < n; ++q) {
       if (b->plans[q]->contract) bst::contract_finish(b->plans[q], s);

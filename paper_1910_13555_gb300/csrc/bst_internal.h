@@ -375,7 +375,11 @@ int64_t emu_item_count(bst_plan *p, cudaStream_t s);
 void emu_build_items(bst_plan *p, int64_t base, int64_t *items, cudaStream_t s);
 void emu_prepare_and_fill(bst_plan *p, const NumArgs &a, void *out, cudaStream_t s);
 int emu_persist_grid(int num_sms, int row_scale);
+// true when row-scaled emulated tiles should take the pipelined loop: the C elements
+// sum at least 64 inner elements on average (flops >= 128 nelem_c)
+bool emu_pipelined(double flops, int64_t nelem_c);
 void launch_emu_persist(const void *params, const int64_t *items, int64_t nitems,
-                        unsigned long long *counter, int grid, int row_scale, cudaStream_t s);
+                        unsigned long long *counter, int grid, int row_scale, bool pipe,
+                        cudaStream_t s);
 
 }  // namespace bst

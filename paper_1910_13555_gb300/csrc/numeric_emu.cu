@@ -596,12 +596,12 @@ __device__ __forceinline__ int4 load_ent(const EmuParams &P, const EmuBlk &b, in
   return q < b.ne ? P.ents[(int64_t)b.eb + q] : make_int4(0, 0, 0, 0);
 }
 
-// Row-scaled tile: per entry, the row operand's six digit fragments (two 8-byte loads
-// each) and the column operand's six (one each) feed the 21 kept slice products into
+// Row-scaled tile, direct loads: per entry, the row operand's six digit fragments
+// (two 8-byte loads each) and the column operand's six (one each) feed the 21 kept slice products into
 // six FP32 level sums.  All products of an element share its scale, so the level sums
 // run across entries and are folded into the int64 accumulators every 32 inner
 // elements (or at the end).
-__device__ __forceinline__ void emu_tile_rs(const EmuParams &P, const EmuBlk &b, int mt, int ng,
+__device__ __forceinline__ void emu_tile_rs_direct(const EmuParams &P, const EmuBlk &b, int mt, int ng,
                                             const int4 &ent0) {
   const int lane = threadIdx.x & 31, t = lane & 3;
   const TileLane L = tile_lane(P, b, mt, ng);
@@ -656,6 +656,129 @@ __device__ __forceinline__ void emu_tile_rs(const EmuParams &P, const EmuBlk &b,
         }
         ++used;
       }
+    }
+  }
+  fold();
+  emu_store(P, b, L, acc);
+}
+
+// digit fragments of one (entry, 16-wide chunk) job of a row-scaled tile: the row
+// operand's six slices for the lane's two tile rows and the column operand's six
+struct EmuFrag {
+  uint2 a0[kSlices], a1[kSlices], b[kSlices];
+};
+
+__device__ __forceinline__ void emu_frag_load(EmuFrag &f, const TileLane &L,
+                                              const __nv_bfloat16 *a0, const __nv_bfloat16 *a1,
+                                              const __nv_bfloat16 *b0) {
+  const uint2 zero = make_uint2(0u, 0u);
+#pragma unroll
+  for (int s = 0; s < kSlices; ++s) {
+    f.b[s] = L.vB ? ld8(b0 + s * 16) : zero;
+    f.a0[s] = L.v0 ? ld8(a0 + s * 16) : zero;
+    f.a1[s] = L.v1 ? ld8(a1 + s * 16) : zero;
+  }
+}
+
+// the 21 kept slice products (levels s + t <= 5) of one job into the six level sums
+__device__ __forceinline__ void emu_frag_mma(float (&lv)[kSlices][4], const EmuFrag &f) {
+#pragma unroll
+  for (int s = 0; s < kSlices; ++s) {
+    const uint32_t af[4] = {f.a0[s].x, f.a1[s].x, f.a0[s].y, f.a1[s].y};
+#pragma unroll
+    for (int tt = 0; s + tt < kSlices; ++tt) mma_bf16(lv[s + tt], af, f.b[tt].x, f.b[tt].y);
+  }
+}
+
+// Row-scaled tile, pipelined: the tile's jobs -- (entry, 16-wide chunk) pairs, entry by
+// entry -- each feed the 21 kept slice products into six FP32 level sums; the fragments
+// of the next job are loaded while the current job's products run, so the MMAs do not
+// wait on L2 for their operands.  The second fragment set costs registers (52 bytes of
+// spills at the 128-register limit), which plans with short inner sums pay for without
+// gaining: the launch takes this loop only when a C element sums at least
+// kPipeMinInner inner elements on average (measured: tall-skinny A^T B, 311 per
+// element, 1088 -> 1181 GFLOP/s; banded, 21 per element, 2347 -> 2154 with it).  All products of an element share its scale, so the level
+// sums run across entries and are folded into the int64 accumulators every 32 inner
+// elements (or at the end).
+__device__ __forceinline__ void emu_tile_rs_pipe(const EmuParams &P, const EmuBlk &b, int mt, int ng,
+                                                 const int4 &ent0) {
+  const int lane = threadIdx.x & 31, t = lane & 3;
+  const TileLane L = tile_lane(P, b, mt, ng);
+  const __nv_bfloat16 *Xa = b.sw ? P.b_dig : P.a_dig, *Xb = b.sw ? P.a_dig : P.b_dig;
+  long long acc[4] = {0, 0, 0, 0};
+  float lv[kSlices][4];
+#pragma unroll
+  for (int s = 0; s < kSlices; ++s)
+#pragma unroll
+    for (int h = 0; h < 4; ++h) lv[s][h] = 0.f;
+  int used = 0;  // 16-wide chunks summed into lv since the last fold
+  auto fold = [&]() {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      if (L.valid[h]) {
+        const long long I = fold_levels(lv, h);
+        acc[h] += b.guard ? round_shift(I, b.guard) : I;
+      }
+#pragma unroll
+      for (int s = 0; s < kSlices; ++s) lv[s][h] = 0.f;
+    }
+    used = 0;
+  };
+  // per-thread digit pointers of entry j of the loaded group: chunk ch of outer row r
+  // starts at (r * nch + ch) * 96, slice s of it 16 elements further per s
+  auto entry = [&](const int4 &e, int j, const __nv_bfloat16 *&pa0, const __nv_bfloat16 *&pa1,
+                   const __nv_bfloat16 *&pb0, int &nch) {
+    const unsigned ea = (unsigned)__shfl_sync(kFull, e.x, j);
+    const unsigned eb = (unsigned)__shfl_sync(kFull, e.y, j);
+    nch = __shfl_sync(kFull, e.z, j);
+    const __nv_bfloat16 *Ad = Xa + 16 * (size_t)(b.sw ? eb : ea);
+    const __nv_bfloat16 *Bd = Xb + 16 * (size_t)(b.sw ? ea : eb);
+    const int rs = nch * (kSlices * 16);
+    pa0 = Ad + (L.r0 * rs + 4 * t);
+    pa1 = Ad + (L.r1 * rs + 4 * t);
+    pb0 = Bd + (L.colB * rs + 4 * t);
+  };
+  if (b.ne > 0) {
+    int4 ent = ent0;
+    int g0 = 0, j = 0, ch = 0, nch = 0;
+    const __nv_bfloat16 *a0, *a1, *b0;
+    entry(ent, 0, a0, a1, b0, nch);
+    EmuFrag cur;
+    emu_frag_load(cur, L, a0, a1, b0);
+    for (;;) {
+      int jn = j, chn = ch + 1, nnch = nch;
+      const __nv_bfloat16 *na0 = a0, *na1 = a1, *nb0 = b0;
+      bool more = true;
+      if (chn == nch) {
+        chn = 0;
+        jn = j + 1;
+        if (g0 + jn >= b.ne) {
+          more = false;
+        } else {
+          if (jn == 32) {
+            g0 += 32;
+            jn = 0;
+            ent = load_ent(P, b, g0 + lane);
+          }
+          entry(ent, jn, na0, na1, nb0, nnch);
+        }
+      }
+      EmuFrag nxt;
+      if (more) {
+        const int cofs = chn * (kSlices * 16);
+        emu_frag_load(nxt, L, na0 + cofs, na1 + cofs, nb0 + cofs);
+      }
+      if (used == kSegChunks) fold();
+      emu_frag_mma(lv, cur);
+      ++used;
+      if (!more) break;
+      cur = nxt;
+      j = jn;
+      ch = chn;
+      nch = nnch;
+      a0 = na0;
+      a1 = na1;
+      b0 = nb0;
     }
   }
   fold();
@@ -719,6 +842,7 @@ __device__ __forceinline__ void emu_tile_bs(const EmuParams &P, const EmuBlk &b,
   emu_store(P, b, L, acc);
 }
 
+// ROWS: 0 block-scaled tiles, 1 row-scaled with direct loads, 2 row-scaled pipelined
 template <int ROWS>
 __device__ __forceinline__ void emu_block(const EmuParams &P, const EmuBlk &b) {
   const int lane = threadIdx.x & 31;
@@ -727,8 +851,10 @@ __device__ __forceinline__ void emu_block(const EmuParams &P, const EmuBlk &b) {
   const int MT = (RM + 15) >> 4, NT = (RN + 7) >> 3;
   for (int mt = 0; mt < MT; ++mt)
     for (int ng = 0; ng < NT; ++ng) {
-      if (ROWS)
-        emu_tile_rs(P, b, mt, ng, ent0);
+      if (ROWS == 2)
+        emu_tile_rs_pipe(P, b, mt, ng, ent0);
+      else if (ROWS == 1)
+        emu_tile_rs_direct(P, b, mt, ng, ent0);
       else
         emu_tile_bs(P, b, mt, ng, ent0);
     }
@@ -743,6 +869,10 @@ __device__ __forceinline__ void emu_block(const EmuParams &P, const EmuBlk &b) {
 // path.  No waits: a warp whose chunk starts past the end returns.
 constexpr int kChunk = 4;
 static_assert(kChunk * kDescWords == 32, "one descriptor word per lane");
+
+// average inner length per C element (flops / 2 nelem(C)) from which row-scaled tiles
+// take the pipelined loop
+constexpr double kPipeMinInner = 64.0;
 
 template <int ROWS, class GetP>
 __device__ __forceinline__ void emu_persist(const int64_t *__restrict__ items, int64_t nitems,
@@ -1175,13 +1305,20 @@ static int emu_ctas_per_sm(bool batch, int row_scale) {
 
 int emu_persist_grid(int num_sms, int row_scale) { return emu_ctas_per_sm(true, row_scale) * num_sms; }
 
+bool emu_pipelined(double flops, int64_t nelem_c) {
+  return nelem_c > 0 && flops >= 2.0 * kPipeMinInner * (double)nelem_c;
+}
+
 void launch_emu_persist(const void *params, const int64_t *items, int64_t nitems,
-                        unsigned long long *counter, int grid, int row_scale, cudaStream_t s) {
+                        unsigned long long *counter, int grid, int row_scale, bool pipe,
+                        cudaStream_t s) {
   if (nitems == 0) return;
   BST_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
   const int g = (int)std::min<int64_t>(grid, (nitems + 8 * kChunk - 1) / (8 * kChunk));
   const EmuParams *P = static_cast<const EmuParams *>(params);
-  if (row_scale)
+  if (row_scale && pipe)
+    k_num_emu_bf16_persist<2><<<g, 256, 0, s>>>(P, items, nitems, counter);
+  else if (row_scale)
     k_num_emu_bf16_persist<1><<<g, 256, 0, s>>>(P, items, nitems, counter);
   else
     k_num_emu_bf16_persist<0><<<g, 256, 0, s>>>(P, items, nitems, counter);
@@ -1199,7 +1336,9 @@ void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
     const int g = (int)std::min<int64_t>((int64_t)emu_ctas_per_sm(false, P.row_scale) * p->ctx->num_sms,
                                          (E.nitems_b + 8 * kChunk - 1) / (8 * kChunk));
     BST_CUDA(cudaMemsetAsync(E.counter, 0, sizeof(unsigned long long), s));
-    if (P.row_scale)
+    if (P.row_scale && emu_pipelined(p->stats.flops, p->C->nelem))
+      k_num_emu_bf16_persist1<2><<<g, 256, 0, s>>>(P, E.nitems_b, E.counter);
+    else if (P.row_scale)
       k_num_emu_bf16_persist1<1><<<g, 256, 0, s>>>(P, E.nitems_b, E.counter);
     else
       k_num_emu_bf16_persist1<0><<<g, 256, 0, s>>>(P, E.nitems_b, E.counter);

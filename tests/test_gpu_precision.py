@@ -130,3 +130,35 @@ def test_emulated_many_products_per_block():
     assert per_block.max() > 64
     got = run_multiply(p, precision=bst.BST_FP64_EMU_BF16, stacks=False)
     assert rel_fro(got["data"], ref["data"]) <= 1e-11
+
+
+def test_emulated_long_inner_sums_alone_and_batched():
+    """Plans whose C elements sum at least 64 inner elements on average take the
+    pipelined row-scaled tile loop, alone and in a batch: within 1e-11 of the oracle,
+    and the batch equal to the single executes bit for bit."""
+    import torch
+
+    from gpu_util import to_lib
+    probs = [tall_skinny(seed=40 + q, nk=3000, nmn=12, window=6, p=0.5) for q in range(2)]
+    mats, plans, refs = [], [], []
+    for p in probs:
+        A, B = to_lib(p.A), to_lib(p.B)
+        pl = bst.multiply_plan(A, B, None, p.eps, p.transa, p.transb)
+        pl.alloc_result()
+        assert pl.stats()["flops"] >= 2 * 64 * pl.result.info[3]
+        mats.append((A, B))
+        plans.append(pl)
+        refs.append(oracle.multiply(p.A, p.B, None, 1.0, 0.0, p.eps, p.transa, p.transb))
+    single = []
+    for pl, ref in zip(plans, refs):
+        pl.execute(1.0, 0.0, bst.BST_FP64_EMU_BF16, 1)
+        torch.cuda.synchronize()
+        got = pl.result.data[:pl.result.info[3]].cpu().numpy().copy()
+        assert rel_fro(got, ref["data"]) <= 1e-11
+        single.append(got)
+    batch = bst.bst_batch_create(bst.context(), [pl.handle for pl in plans])
+    bst.bst_batch_execute(batch, np.ones(2), np.zeros(2), bst.BST_FP64_EMU_BF16)
+    torch.cuda.synchronize()
+    for pl, s in zip(plans, single):
+        assert (pl.result.data[:pl.result.info[3]].cpu().numpy() == s).all()
+    bst.bst_batch_destroy(batch)
