@@ -53,13 +53,14 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // ---- block norms -------------------------------------------------------------------
 
-// One warp per group of 32 consecutive blocks.  Each block's sum of squares is summed
-// across the warp (lane-strided FMAs, then the butterfly) and parked in the lane of the
-// block's place in the group; the 32 square roots then run as one sequence.  GB300's
-// FP64 pipe takes as long for a warp instruction with one active lane as with 32, and
-// a square root is about a dozen of them: one per block made the kernel FP64-bound
-// (175 us for the banded workload's 1.6e5 blocks of A, against 27 us to read them).
-constexpr int kNormGroup = 32;
+// One warp per group of kNormGroup consecutive blocks.  Lane j first loads the size
+// and offset of block j of the group (one coalesced round of index loads instead of a
+// dependent chain per block); then each block's sum of squares is summed across the
+// warp (lane-strided FMAs, then the butterfly) and parked in lane j, and the group's
+// square roots run as one sequence.  GB300's FP64 pipe takes as long for a warp
+// instruction with one active lane as with 32, and a square root is about a dozen of
+// them.
+constexpr int kNormGroup = 8;
 
 __global__ void k_block_norms(int64_t nblocks, const int32_t *__restrict__ row,
                               const int32_t *__restrict__ col, const int32_t *__restrict__ rsz,
@@ -69,13 +70,18 @@ __global__ void k_block_norms(int64_t nblocks, const int32_t *__restrict__ row,
   const int64_t b0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kNormGroup;
   if (b0 >= nblocks) return;
   const int nb = (int)min((int64_t)kNormGroup, nblocks - b0);
+  int my_len = 0;
+  long long my_off = 0;
+  if (lane < nb) {
+    my_len = rsz[row[b0 + lane]] * csz[col[b0 + lane]];
+    my_off = off[b0 + lane];
+  }
   double mine = 0.0;
   for (int j = 0; j < nb; ++j) {
-    const int64_t b = b0 + j;
-    const int64_t len = (int64_t)rsz[row[b]] * csz[col[b]];
-    const double *x = data + off[b];
+    const int len = __shfl_sync(0xffffffffu, my_len, j);
+    const double *x = data + __shfl_sync(0xffffffffu, my_off, j);
     double s = 0.0;
-    for (int64_t e = lane; e < len; e += 32) {
+    for (int e = lane; e < len; e += 32) {
       double v = __ldg(x + e);
       s = fma(v, v, s);
     }
