@@ -86,8 +86,10 @@ typedef struct bst_tensor bst_tensor;
 typedef struct bst_plan bst_plan;
 typedef struct bst_batch bst_batch;
 
-/* Device allocator callbacks: return a device pointer of at least `bytes` bytes
- * usable on `stream` (NULL on failure); free it.  `user` is passed through. */
+/* Device allocator callbacks: return a device pointer of at least `bytes` bytes,
+ * aligned to 256 bytes as cudaMalloc's are (the library's kernels use 16-byte vector
+ * accesses on these buffers), usable on `stream` (NULL on failure); free it.  `user` is
+ * passed through. */
 typedef void *(*bst_alloc_fn)(size_t bytes, void *user, void *stream);
 typedef void (*bst_free_fn)(void *ptr, void *user, void *stream);
 

@@ -29,6 +29,10 @@ void *Arena::alloc(size_t bytes) {
   if (ctx && ctx->alloc) {
     p = ctx->alloc(bytes, ctx->user, stream);
     if (!p) throw Error{BST_ERR_ALLOC, "allocator callback returned NULL"};
+    if (reinterpret_cast<uintptr_t>(p) & 255) {
+      ctx->free_fn(p, ctx->user, stream);
+      throw Error{BST_ERR_ALLOC, "allocator callback returned a pointer not aligned to 256 bytes"};
+    }
   } else {
     cudaError_t e = ctx && ctx->pool ? cudaMallocFromPoolAsync(&p, bytes, ctx->pool, stream)
                                      : cudaMallocAsync(&p, bytes, stream);

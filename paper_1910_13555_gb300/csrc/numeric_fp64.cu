@@ -765,6 +765,7 @@ __device__ __forceinline__ void f64_tiles_of(
     const int p0 = t * tr, mt = min(tr, m - p0);
     int64_t q = ebeg[tile];
     unsigned long long flops = 0;
+    long long w1 = 0;  // the tile's inner elements (sum of its entries' panel widths)
     for (int kc = 0; kc < S.Dk; ++kc) {
       const int len = run_len[c * S.Dk + kc];
       if (len == 0) continue;
@@ -784,6 +785,7 @@ __device__ __forceinline__ void f64_tiles_of(
             for (int l0 = 0; l0 < k; l0 += ws) {
               const int b = s_b[e] + (S.tb ? l0 : l0 * n);
               ents[q++] = make_int4((int)(ab + (int64_t)(l0 / ki) * m * ki), b, min(ws, k - l0), st);
+              w1 += min(ws, k - l0);
             }
           } else {
             for (int l0 = 0; l0 < k; l0 += ki)
@@ -791,6 +793,7 @@ __device__ __forceinline__ void f64_tiles_of(
                 const int b = s_b[e] + (S.tb ? l0 + c0 : (l0 + c0) * n);
                 ents[q++] = make_int4((int)(ab + (int64_t)(l0 / ki) * m * ki + c0), b,
                                       min(w, ki - c0), st);
+                w1 += min(w, ki - c0);
               }
           }
           continue;
@@ -800,21 +803,28 @@ __device__ __forceinline__ void f64_tiles_of(
           const int a = s_a[e] + (S.ta ? l0 * m + p0 : p0 * k + l0);
           const int b = s_b[e] + (S.tb ? l0 : l0 * n);
           ents[q++] = make_int4(a, b, wl, strides);
+          w1 += wl;
         }
       }
       flops += (unsigned long long)len * mt * n * k;
     }
+    // the descriptor as two 16-byte stores (word 7, the split, once it is known)
     int32_t *d = desc + tile * kF64Desc;
-    d[0] = (int32_t)(c_off[c] + (int64_t)p0 * n);
-    d[1] = (int32_t)ebeg[tile];
-    d[2] = (int32_t)(q - ebeg[tile]);
-    d[3] = mt | (n << 12);
-    d[4] = c_cin[c];
-    d[5] = p0 * n;
-    d[6] = (int32_t)c;
+    int4 *dv = reinterpret_cast<int4 *>(d);
+    dv[0] = make_int4((int32_t)(c_off[c] + (int64_t)p0 * n), (int32_t)ebeg[tile],
+                      (int32_t)(q - ebeg[tile]), mt | (n << 12));
     key[tile] = __clzll(flops + 1ull);
-    long long c1, saved;
-    d[7] = f64_split_of(d, ents, cls_smax[cls], slot_elems, c1, saved);
+    // a short tile never splits (the test f64_split_of starts with), decided here
+    // without reading its entries back
+    const int mn = mt * n;
+    const int smax = min(min(cls_smax[cls], kMaxSplit), min(kTile, slot_elems) / max(mn, 1));
+    long long c1, saved = 0;
+    int split = 1;
+    if (w1 < kSplitMinInner || smax < 2)
+      c1 = (long long)((mn + 31) / 32) * w1;
+    else
+      split = f64_split_of(d, ents, cls_smax[cls], slot_elems, c1, saved);
+    dv[1] = make_int4(c_cin[c], p0 * n, (int32_t)c, split);
     c1_sum += c1;
     saved_sum += saved;
   }
