@@ -478,11 +478,12 @@ __device__ __forceinline__ void slot_rc(const WarpTask &w, int nt, int h, int &r
 
 // ---- the BF16 slice kernel: one warp per C block -----------------------------------
 //
-// A warp takes C blocks in a fixed stride over the work list (C block order, so warps
-// running at the same time share op(A) digit rows in L2) and prefetches the descriptor
-// of its next block while it computes the current one.  A block's stack entries (most
-// blocks have one or two) are loaded once, one per lane, and broadcast with shuffles;
-// the warp then runs the block's 16 x 8 tiles one after another.
+// Warps take C blocks in chunks of kChunk consecutive blocks from a counter over the
+// work list (C block order, so warps running at the same time share op(A) digit rows
+// in L2) and prefetch the descriptors of their next chunk while they compute the
+// current one.  A block's stack entries (most blocks have one or two) are loaded once,
+// one per lane, and broadcast with shuffles; the warp then runs the block's 16 x 8
+// tiles one after another.
 
 constexpr unsigned kFull = 0xffffffffu;
 

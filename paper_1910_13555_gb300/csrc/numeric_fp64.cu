@@ -4,7 +4,11 @@
 // specialised per (m, n, k).  On GB300 FP64 runs at about 1 TFLOP/s on the CUDA
 // cores (FP64 DMMA measures the same), so this path is bound by the FP64 pipe, and
 // what matters is how many lanes of every FP64 FMA do useful work and that C is
-// written once.  The design:
+// written once.  Every plan whose block sizes fit its tiles runs the staged persistent
+// kernel (k_num_fp64_staged1, "staged persistent kernel" below: row tiles of C blocks
+// from a cost-ordered list, operands staged through shared memory, one runtime-size
+// product body).  The direct-load kernels described here serve the other plans and the
+// split-K path:
 //   * one warp owns one C block (the "task"); its lanes own the m*n outputs
 //     (ceil(m n / 32) accumulators per lane), so no two warps write the same C block
 //     and no atomics are needed (the paper's static assignment of whole A rows to
