@@ -39,8 +39,8 @@
  *     context's allocator callbacks (or stream-ordered cudaMallocAsync when none
  *     are given) and is released by the matching destroy call.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
- *     asynchronous on it except where documented (plans synchronise once or twice
- *     to learn output sizes).
+ *     asynchronous on it except where documented (plans synchronise the stream a few
+ *     times to learn output and schedule sizes; executes never do).
  *   - Handles are not thread-safe; use one handle per thread or lock around it.
  *   - A matrix or tensor must outlive every plan built from it.
  */
@@ -149,7 +149,8 @@ bst_status bst_matrix_filter_copy(const bst_matrix *X, bst_matrix *Y, void *stre
  * C_out = alpha * op(A) * op(B) + beta * C_in, op(X) = X ('N') or X^T ('T'), with
  * the block-norm filter eps >= 0 (see top).  C_in may be NULL.  Planning runs the
  * GPU symbolic phase on `stream`: block norms, pair matching + filter, pattern of
- * C_out, and the stacks.  It synchronises `stream` to learn the output sizes.
+ * C_out, the stacks and the numeric schedule.  It synchronises `stream` several times
+ * (about ten round trips) to learn the sizes of what it builds next.
  * The plan keeps pointers to A, B, C_in; their data are read at execute time.
  * Errors: INVALID_ARG, SHAPE_MISMATCH (inner block sizes differ, or C_in's grid
  * differs from op(A) rows x op(B) columns), OVERFLOW, UNSUPPORTED (more than 2^20
