@@ -40,7 +40,9 @@
  *     are given) and is released by the matching destroy call.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
  *     asynchronous on it except where documented (plans synchronise the stream a few
- *     times to learn output and schedule sizes; executes never do).
+ *     times to learn output and schedule sizes; the first emulated-FP64 or 3xTF32
+ *     execute of a plan and the first execute after a tuning change synchronise too,
+ *     while they build per-plan state; other executes only queue work).
  *   - Handles are not thread-safe; use one handle per thread or lock around it.
  *   - A matrix or tensor must outlive every plan built from it.
  */
