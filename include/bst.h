@@ -68,7 +68,7 @@ enum {
   BST_ERR_ALLOC = 6,            /* an allocation failed                           */
   BST_ERR_CUDA = 7,             /* a CUDA runtime call failed                     */
   BST_ERR_TIMEOUT = 8,          /* a bounded device wait gave up                  */
-  BST_ERR_UNSUPPORTED = 9,      /* valid but outside this build's limits          */
+  BST_ERR_UNSUPPORTED = 9,      /* valid but outside the library's limits         */
   BST_ERR_STATE = 10            /* wrong call order (e.g. C data not bound)       */
 };
 
