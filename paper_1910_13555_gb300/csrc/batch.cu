@@ -5,14 +5,14 @@
 // tagged with the plan's index.  For native FP64 the list is sorted by decreasing cost
 // across the batch, so one persistent grid balances products of very different sizes
 // (the staged kernel takes chunks of items from a counter after two of its own, the
-// direct-load kernel single items from a counter).  For emulated FP64 the plans are listed by
-// decreasing flops and each plan's C blocks in CSR order, and warps take a few
-// consecutive items at a time from a counter, so neighbouring warps share operand
-// digits.  bst_batch_execute only
-// queues work: a parameter copy from the batch's pinned staging buffer, the counter
-// reset and the launches (plus the per-plan slicing kernels for emulated FP64 and the
-// permutations of contraction views), so a call can be captured into a CUDA graph and
-// replayed; everything that allocates or synchronises happens in bst_batch_create.
+// direct-load kernel single items from a counter).  For emulated FP64 the plans are
+// listed by decreasing flops and each plan's C blocks in CSR order, and warps take a
+// few consecutive items at a time from a counter, so neighbouring warps share operand
+// digits.  bst_batch_execute only queues work: a parameter copy from the batch's pinned
+// staging buffer, the counter reset and the launches (plus the per-plan slicing kernels
+// for emulated FP64 and the permutations of contraction views), so a call can be
+// captured into a CUDA graph and replayed; everything that allocates or synchronises
+// happens in bst_batch_create.
 #include <algorithm>
 #include <cmath>
 #include <cstring>

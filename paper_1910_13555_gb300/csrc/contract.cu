@@ -16,7 +16,9 @@
 //   * when they are that order reversed (columns first), the view is the zero-copy
 //     transpose and the multiply takes op = 'T';
 //   * otherwise the elements of every block are permuted into a plan-owned buffer
-//     (once per execute; the inverse permutation maps gradients back).
+//     (once per execute; the inverse permutation maps gradients back) -- or, when the
+//     tensor's modes are (outer contracted, free, inner contracted), the native-FP64
+//     staged schedule reads each block in place as slabs (setup_slab_read below).
 // The result is the matrix C = op(A) op(B) with rows = the free modes of T1 and columns
 // = the free modes of T2; it is the result tensor itself when result_order is the
 // identity, and is permuted block by block into the result tensor otherwise.
