@@ -46,6 +46,17 @@ def _measured_bf16():
 
 
 BF16_PEAK_TFLOPS = _measured_bf16()
+
+
+def _measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get("hbm_gbs") or 0.0) or None
+    except (OSError, ValueError, TypeError):
+        return None
+
+
+MEASURED_HBM_GBS = _measured_hbm()
 CPU_SAMPLE_ROWS = (1000, 3000)     # cpu_baseline: block rows of A in the sample
 REF_SAMPLE_ROWS = (1800, 2200)     # --impl reference: block rows per step
 # timed-step precision -> (library constant name, numeric kernel launched by execute)
@@ -295,6 +306,27 @@ def emu_tensor_ops(plan, ctx):
         tiles = swapped if sw else plain
         total += c * 21 * 2 * tiles * 16 * 8 * 16 * -(-k // 16)
     return total
+
+
+def emu_roofline(plans, ms, ctx):
+    """Roofline of the emulated-FP64 execute of `plans` (run together in `ms`): the time
+    the slice products would take at the measured BF16 peak against the time its bytes
+    would take at the measured HBM bandwidth; fraction = the larger / measured time.
+    Executed tensor flops and bytes come from the library (bst_plan_emu_costs)."""
+    from paper_1910_13555_gb300 import bst
+    ops = byt = 0.0
+    for pl in plans:
+        c = bst.bst_plan_emu_costs(pl.handle)
+        ops += c["tensor_flops"]
+        byt += c["bytes"]
+    hbm = MEASURED_HBM_GBS
+    t_tensor = ops / (BF16_PEAK_TFLOPS * 1e12) if BF16_PEAK_TFLOPS else 0.0
+    t_hbm = byt / (hbm * 1e9) if hbm else 0.0
+    t_roof = max(t_tensor, t_hbm)
+    return {"bound": "tensor" if t_tensor >= t_hbm else "hbm",
+            "executed_bf16_tflop": ops / 1e12, "bytes": byt,
+            "t_roof_ms": t_roof * 1e3, "frac": t_roof / (ms * 1e-3) if ms > 0 else None,
+            "peaks": f"bf16 {BF16_PEAK_TFLOPS} TFLOP/s, hbm {hbm} GB/s (measured)"}
 
 
 def keep_plan_index(A, B, p, device):
@@ -562,10 +594,12 @@ def single_stacks(local_rank, stream, nb=1000):
             "aggregate_frac": tot_f / (tot_t * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
 
 
-def _median_ms(fn, stream, reps=3):
+def _median_ms(fn, stream, reps=20, warmup=3):
+    """Median of `reps` CUDA-event-timed runs of fn on `stream` after `warmup` runs."""
     import torch
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    fn()
+    for _ in range(warmup):
+        fn()
     torch.cuda.synchronize()
     times = []
     for _ in range(reps):
@@ -608,7 +642,8 @@ def _sample_err_matrix(p, plan, row_sizes, col_sizes, nsample=32, seed=0):
 
 def other_configs(local_rank, stream):
     """The other workloads of the method, measured like the headline: numeric GFLOP/s
-    (CUDA events, median of 3), fraction of the FP64 unit-count peak, and error against
+    (CUDA events, median of 20 after 3 warm-ups), fraction of the FP64 unit-count peak
+    (native rows) or the emulated path's own roofline (emulated rows), and error against
     the CPU oracle on sampled output blocks."""
     import numpy as np
     import torch
@@ -625,6 +660,14 @@ def other_configs(local_rank, stream):
     def rate(f, ms):
         return {"gflops": f / (ms * 1e-3) / 1e9, "ms": ms,
                 "frac": f / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+
+    def rate_emu(f, ms, plans):
+        """Emulated FP64: credited GFLOP/s, the ratio of that rate to the FP64 peak (a
+        speedup measure, not a roofline fraction) and the roofline fraction of the
+        emulated path itself (emu_roofline)."""
+        return {"gflops": f / (ms * 1e-3) / 1e9, "ms": ms,
+                "credited_over_fp64_peak": f / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                "roofline": emu_roofline(plans, ms, bst.context(local_rank))}
 
     out = {}
     # 40 x 40 blocks of size 5, 10 % occupancy, no filter
@@ -652,7 +695,7 @@ def other_configs(local_rank, stream):
                                               rel_err_vs_oracle_sample=_sample_err_matrix(
                                                   p, plan, p.A.col_sizes, p.B.col_sizes))
     ms = _median_ms(lambda: plan.execute(1.0, 0.0, bst.BST_FP64_EMU_BF16, 1), stream)
-    ts["emu_bf16"] = dict(rate(f, ms), rel_err_vs_oracle_sample=_sample_err_matrix(
+    ts["emu_bf16"] = dict(rate_emu(f, ms, [plan]), rel_err_vs_oracle_sample=_sample_err_matrix(
         p, plan, p.A.col_sizes, p.B.col_sizes))
     out["tall_skinny_AtB"] = ts
     del plan, A, B
@@ -691,7 +734,8 @@ def other_configs(local_rank, stream):
         blk = max(_sample_err_matrix(probs[q], plans[q], probs[q].A.row_sizes,
                                      probs[q].B.col_sizes, nsample=8, seed=q)
                   for q in (0, 7, 31, 63))
-        bt[name] = dict(rate(f, ms), rel_err_vs_oracle=full,
+        bt[name] = dict(rate(f, ms) if prec == bst.BST_FP64 else rate_emu(f, ms, plans),
+                        rel_err_vs_oracle=full,
                         max_rel_err_of_sampled_blocks=blk,
                         launch="one persistent kernel per replay (CUDA graph)")
         del g
@@ -753,7 +797,8 @@ def other_configs(local_rank, stream):
     rc = {}
     for name, prec in (("fp64", bst.BST_FP64), ("emu_bf16", bst.BST_FP64_EMU_BF16)):
         ms = _median_ms(lambda: plan.execute(1.0, 0.0, prec, 1), stream)
-        rc[name] = dict(rate(f, ms), rel_err_vs_oracle_sample=_sample_err_matrix(
+        rc[name] = dict(rate(f, ms) if prec == bst.BST_FP64 else rate_emu(f, ms, [plan]),
+                        rel_err_vs_oracle_sample=_sample_err_matrix(
             p, plan, p.A.row_sizes, p.B.col_sizes))
     out["rect_case2_small_B"] = dict(rc, flop=f)
     del plan, A, B

@@ -37,7 +37,9 @@
  *     Index arrays passed in are HOST memory and are copied; the library keeps its
  *     own device copies.  Everything the library allocates goes through the
  *     context's allocator callbacks (or stream-ordered cudaMallocAsync when none
- *     are given) and is released by the matching destroy call.
+ *     are given) and is released by the matching destroy call.  One exception: the
+ *     static split-K array of bst_multiply_execute_static, a __device__ array that
+ *     each GPU which loads the library holds until the process exits.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
  *     asynchronous on it except where documented (plans synchronise the stream a few
  *     times to learn output and schedule sizes; the first emulated-FP64 or 3xTF32
@@ -131,8 +133,10 @@ bst_status bst_matrix_bind_data(bst_matrix *m, double *data);
 bst_status bst_matrix_data_size(const bst_matrix *m, int64_t *n_elements);
 bst_status bst_matrix_destroy(bst_matrix *m);
 
-/* Block post-filter (paper Sec. 2: chained products such as the sign-matrix iteration
- * drop negligible blocks between multiplies).  bst_matrix_filter returns, in *out, a new
+/* Block post-filter.  The paper names the sign-matrix iteration among the library's
+ * operations (Sec. 2) but defines no filter on a product's result; dropping the blocks
+ * of small norm between the products of such a chain is a reading of this library,
+ * with the same Frobenius norm as the product filter.  bst_matrix_filter returns, in *out, a new
  * matrix with X's block sizes holding the blocks of X whose Frobenius norm is >= eps
  * (eps = 0 keeps every block), in canonical CSR order; its data is not bound.  It runs
  * on `stream` and synchronises it twice (to learn the kept block and element counts).
@@ -201,6 +205,14 @@ bst_status bst_plan_split_histogram(const bst_plan *plan, int64_t *hist);
  * execute or plan build; split-K executes (split_k > 1) use none of this. */
 bst_status bst_plan_schedule_info(const bst_plan *plan, int32_t *info);
 
+/* Cost model of the emulated-FP64 execute of a plan, for rooflines: out[0] = BF16
+ * tensor-core flops one execute issues (the slice products on the MMA tiles the kernel
+ * runs, padding included), out[1] = bytes its kernels move by design (FP64 operands
+ * read by the slicing passes, digit planes written and read once, C written, the
+ * schedule read; beta = 0).  Builds the plan's emulation index when it has none yet;
+ * synchronises the legacy default stream.  The paper is FP64 only: this is a reading. */
+bst_status bst_plan_emu_costs(bst_plan *plan, double *out);
+
 /* Arithmetic used by execute. */
 enum {
   BST_FP64 = 0,          /* native FP64 FMA                                        */
@@ -228,11 +240,15 @@ bst_status bst_multiply_execute(bst_plan *plan, double alpha, double beta, int32
  * bst_static_scratch_doubles() doubles (32 MiB) that every GPU loading the library
  * holds until the process exits; split_k * nelem(C_out) above that returns
  * BST_ERR_UNSUPPORTED (split_k = 1 needs no scratch).  The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the one array: calls that overlap on the
- * GPU (different streams, or different plans on one device in flight together) race.
- * Each call overwrites every scratch element it reads, so no clearing is needed.
- * Errors: as bst_multiply_execute, plus UNSUPPORTED for a too-large workspace. */
+ * looks up the array's device address (cudaGetSymbolAddress) and keeps it for the life
+ * of the process; make that first call before any stream capture, and do not reset the
+ * device (cudaDeviceReset) after it.  All calls share the one array: calls that overlap
+ * on the GPU (different streams, or different plans on one device in flight together)
+ * race.  Each call overwrites every scratch element it reads, so no clearing is needed.
+ * Every argument and size check runs before any work is queued, so a failing call
+ * queues nothing; the calling thread's current device is the same on return.
+ * Errors: as bst_multiply_execute, plus UNSUPPORTED for a too-large workspace or a
+ * device index above 63. */
 bst_status bst_multiply_execute_static(bst_plan *plan, double alpha, double beta,
                                        int32_t split_k, void *stream);
 /* Capacity of the static split-K array of bst_multiply_execute_static, in doubles. */
@@ -332,6 +348,12 @@ bst_status bst_plan_result_tensor(bst_plan *plan, bst_tensor **R);
  * library's tune table (bst_tune_*).  alpha/beta are host arrays of n values.
  * Executes of one batch must not overlap on the GPU (they share its work counter),
  * nor overlap an execute of one of its plans (they write the same C_out).
+ * alpha, beta and the plans' data pointers reach the GPU through a pinned host staging
+ * buffer of the batch: an execute first waits (on the host) until the previous
+ * execute's copy out of that buffer has run, so executes queued back to back each use
+ * their own values.  An execute captured into a CUDA graph records that copy as a
+ * graph node: a replay reads the buffer as the most recent execute call of the batch
+ * left it (the captured call's values, until another execute call rewrites them).
  * ------------------------------------------------------------------------- */
 bst_status bst_batch_create(bst_ctx *ctx, int32_t n, bst_plan *const *plans, bst_batch **out);
 bst_status bst_batch_execute(bst_batch *batch, const double *alpha, const double *beta,

@@ -319,9 +319,9 @@ class _Blocks:
 
 
 def filter_blocks(m, eps):
-    """Post-filter (paper Sec. 2, products of a chain drop negligible blocks): the blocks
-    of m, in canonical order, whose Frobenius norm (the same norm as the product filter)
-    is >= eps; their data unchanged."""
+    """Post-filter, a reading (the paper names the sign iteration, Sec. 2, but defines
+    no filter on a product's result): the blocks of m, in canonical order, whose
+    Frobenius norm (the same norm as the product filter) is >= eps; data unchanged."""
     norms = block_norms(m)
     lens = (np.asarray(m.row_sizes, np.int64)[np.asarray(m.rows)] *
             np.asarray(m.col_sizes, np.int64)[np.asarray(m.cols)])

@@ -74,6 +74,7 @@ _SIGS = {
     "bst_plan_get_stacks": ([_VP, _VP, _VP, _VP, _VP, _VP], C.c_int32),
     "bst_plan_split_histogram": ([_VP, _VP], C.c_int32),
     "bst_plan_schedule_info": ([_VP, _VP], C.c_int32),
+    "bst_plan_emu_costs": ([_VP, _VP], C.c_int32),
     "bst_multiply_execute": ([_VP, C.c_double, C.c_double, C.c_int32, C.c_int32, _VP], C.c_int32),
     "bst_multiply_execute_static": ([_VP, C.c_double, C.c_double, C.c_int32, _VP], C.c_int32),
     "bst_static_scratch_doubles": ([], C.c_size_t),
@@ -255,6 +256,12 @@ def bst_plan_schedule_info(plan) -> dict:
     v = np.zeros(4, np.int32)
     _check(load().bst_plan_schedule_info(plan, _ptr(v)), "bst_plan_schedule_info")
     return dict(staged=bool(v[0]), strided=bool(v[1]), split=bool(v[2]), slab=bool(v[3]))
+
+
+def bst_plan_emu_costs(plan) -> dict:
+    out = np.zeros(2, np.float64)
+    _check(load().bst_plan_emu_costs(plan, _ptr(out)), "bst_plan_emu_costs")
+    return {"tensor_flops": float(out[0]), "bytes": float(out[1])}
 
 
 def bst_plan_get_stacks(plan):

@@ -42,7 +42,12 @@ struct bst_batch {
   size_t epbytes = 0;
   int grid_e = 0;
   int64_t tune_version = 0;  // the context's tuning state the schedules were built for
+  // recorded after each parameter copy out of h_params / h_eparams; the next execute
+  // waits for it before it rewrites the staging buffers
+  cudaEvent_t copied = nullptr;
+  bool copy_pending = false;
   ~bst_batch() {
+    if (copied) cudaEventDestroy(copied);
     if (h_params) cudaFreeHost(h_params);
     if (h_eparams) cudaFreeHost(h_eparams);
   }
@@ -166,6 +171,7 @@ bst_status bst_batch_create(bst_ctx *ctx, int32_t n, bst_plan *const *plans, bst
       BST_CUDA(cudaMallocHost(&b->h_eparams, b->epbytes * n));
       b->grid_e = bst::emu_persist_grid(ctx->num_sms, ctx->tune_emu_row_scale);
       b->tune_version = ctx->tune_version;
+      BST_CUDA(cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming));
       BST_CUDA(cudaStreamSynchronize(s));
       scratch.release_all();
       BST_CUDA(cudaStreamSynchronize(s));
@@ -197,6 +203,18 @@ bst_status bst_batch_execute(bst_batch *b, const double *alpha, const double *be
     const int32_t n = (int32_t)b->plans.size();
     BST_REQUIRE(precision == BST_FP64 || b->tune_version == b->ctx->tune_version, BST_ERR_STATE,
                 "the context's tuning changed after the batch was created; create it again");
+    // The parameters travel through pinned host staging buffers.  An earlier execute's
+    // copy out of them may still be queued: wait for it before they are rewritten, so
+    // executes queued back to back each run with their own alpha, beta and data.  While
+    // the stream is being captured the copy becomes a graph node that reads the buffers
+    // when the graph is replayed (nothing is waited for or recorded then).
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    BST_CUDA(cudaStreamIsCapturing(s, &cap));
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    if (b->copy_pending && !capturing) {
+      BST_CUDA(cudaEventSynchronize(b->copied));
+      b->copy_pending = false;
+    }
     if (precision == BST_FP64) {
       bool split = false;
       for (int32_t q = 0; q < n; ++q) {
@@ -210,6 +228,10 @@ bst_status bst_batch_execute(bst_batch *b, const double *alpha, const double *be
                              b->stage_elems > 0);
       }
       BST_CUDA(cudaMemcpyAsync(b->d_params, b->h_params, b->pbytes * n, cudaMemcpyHostToDevice, s));
+      if (!capturing) {
+        BST_CUDA(cudaEventRecord(b->copied, s));
+        b->copy_pending = true;
+      }
       if (b->stage_elems > 0)
         bst::launch_fp64_staged(b->d_params, b->titems, b->n_titems, b->stage_elems,
                                 b->stage_strided, split, b->ctx->num_sms, b->counter, s);
@@ -225,6 +247,10 @@ bst_status bst_batch_execute(bst_batch *b, const double *alpha, const double *be
                                     static_cast<char *>(b->h_eparams) + q * b->epbytes, s);
       }
       BST_CUDA(cudaMemcpyAsync(b->d_eparams, b->h_eparams, b->epbytes * n, cudaMemcpyHostToDevice, s));
+      if (!capturing) {
+        BST_CUDA(cudaEventRecord(b->copied, s));
+        b->copy_pending = true;
+      }
       double flops = 0.0;
       int64_t nelem = 0;
       for (auto *pl : b->plans) {

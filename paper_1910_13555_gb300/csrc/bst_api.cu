@@ -59,22 +59,6 @@ void Arena::release_all() {
 
 using bst::Error;
 
-#define API_BEGIN try {
-#define API_END                                                   \
-  }                                                               \
-  catch (const bst::Error &e) {                                   \
-    bst::set_error(e.msg);                                        \
-    return e.code;                                                \
-  }                                                               \
-  catch (const std::bad_alloc &) {                                \
-    bst::set_error("host allocation failed");                     \
-    return BST_ERR_ALLOC;                                         \
-  }                                                               \
-  catch (...) {                                                   \
-    bst::set_error("unexpected internal error");                  \
-    return BST_ERR_INVALID_ARG;                                   \
-  }                                                               \
-  return BST_OK;
 
 namespace {
 
@@ -385,6 +369,16 @@ bst_status bst_plan_schedule_info(const bst_plan *plan, int32_t *info) {
   info[1] = plan->stage_elems > 0 && plan->stage_strided;
   info[2] = plan->stage_elems > 0 && plan->stage_split;
   info[3] = plan->stage_elems > 0 && plan->a_slab;
+  API_END
+}
+
+bst_status bst_plan_emu_costs(bst_plan *plan, double *out) {
+  API_BEGIN
+  BST_REQUIRE(plan && out, BST_ERR_INVALID_ARG, "NULL argument");
+  use_device(plan->ctx);
+  cudaStream_t s = nullptr;
+  bst::emu_costs(plan, s, &out[0], &out[1]);
+  BST_CUDA(cudaStreamSynchronize(s));
   API_END
 }
 

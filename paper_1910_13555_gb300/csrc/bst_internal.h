@@ -6,6 +6,7 @@
 
 #include <map>
 #include <mutex>
+#include <new>
 #include <string>
 #include <utility>
 #include <vector>
@@ -44,6 +45,26 @@ void count_launch();
   do {                                                                    \
     if (!(cond)) throw ::bst::Error{(code), std::string(msg)};            \
   } while (0)
+
+// Every extern "C" entry point wraps its body in API_BEGIN ... API_END: library errors
+// become their status code and message, a failed host allocation BST_ERR_ALLOC, and no
+// exception crosses the C boundary.
+#define API_BEGIN try {
+#define API_END                                          \
+  }                                                      \
+  catch (const ::bst::Error &e) {                        \
+    ::bst::set_error(e.msg);                             \
+    return e.code;                                       \
+  }                                                      \
+  catch (const std::bad_alloc &) {                       \
+    ::bst::set_error("host allocation failed");          \
+    return BST_ERR_ALLOC;                                \
+  }                                                      \
+  catch (...) {                                          \
+    ::bst::set_error("unexpected internal error");       \
+    return BST_ERR_INVALID_ARG;                          \
+  }                                                      \
+  return BST_OK;
 
 // ---------------------------------------------------------------------------
 // device memory through the context's allocator
@@ -338,8 +359,12 @@ void execute_fp64_workspace(bst_plan *p, const NumArgs &a, int split, double *W,
 void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s);
 void execute_tf32x3(bst_plan *p, const NumArgs &a, cudaStream_t s);
 void emu_state_free(bst_plan *p);
+void emu_costs(bst_plan *p, cudaStream_t s, double *tensor_flops, double *bytes);
 void adj_state_free(bst_plan *p);
 // contractions (contract.cu)
+// throws BST_ERR_STATE when a tensor the execute reads or writes has no data bound
+// (no device work)
+void contract_check_bound(const bst_plan *p, bool read_cin);
 void contract_prepare(bst_plan *p, bool read_cin, cudaStream_t s, bool a_copy = true);
 // the native-FP64 execute with `split` K parts reads A in place (slab schedule)
 bool fp64_reads_slabs(const bst_plan *p, int split);

@@ -445,10 +445,18 @@ void contract_free(bst_plan *p) {
 
 // Refresh the views' data before an execute: permute the inputs that are copies and
 // point the C matrix at the result data.  Returns the C data pointer to use.
-void contract_prepare(bst_plan *p, bool read_cin, cudaStream_t s, bool a_copy) {
-  Contract &K = *p->contract;
+void contract_check_bound(const bst_plan *p, bool read_cin) {
+  const Contract &K = *p->contract;
   BST_REQUIRE(K.A.T->nblocks == 0 || K.A.T->data, BST_ERR_STATE, "T1 data not bound");
   BST_REQUIRE(K.B.T->nblocks == 0 || K.B.T->data, BST_ERR_STATE, "T2 data not bound");
+  BST_REQUIRE(!(K.has_cin && read_cin) || K.Ci.T->nblocks == 0 || K.Ci.T->data, BST_ERR_STATE,
+              "R_in data not bound");
+  BST_REQUIRE(K.R->nelem == 0 || K.R->data, BST_ERR_STATE, "result tensor data not bound");
+}
+
+void contract_prepare(bst_plan *p, bool read_cin, cudaStream_t s, bool a_copy) {
+  Contract &K = *p->contract;
+  contract_check_bound(p, read_cin);
   K.A.M->data = K.A.copy ? K.A.buf : K.A.T->data;
   K.B.M->data = K.B.copy ? K.B.buf : K.B.T->data;
   p->a_slab_base = K.A.T->data;
@@ -534,22 +542,6 @@ void contract_adjoint(bst_plan *p, const double *dR, double *dT1, double *dT2, d
 
 using bst::Error;
 
-#define API_BEGIN try {
-#define API_END                                          \
-  }                                                      \
-  catch (const bst::Error &e) {                          \
-    bst::set_error(e.msg);                               \
-    return e.code;                                       \
-  }                                                      \
-  catch (const std::bad_alloc &) {                       \
-    bst::set_error("host allocation failed");            \
-    return BST_ERR_ALLOC;                                \
-  }                                                      \
-  catch (...) {                                          \
-    bst::set_error("unexpected internal error");         \
-    return BST_ERR_INVALID_ARG;                          \
-  }                                                      \
-  return BST_OK;
 
 extern "C" {
 

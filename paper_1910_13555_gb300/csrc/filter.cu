@@ -1,8 +1,9 @@
 // Block post-filter of a matrix: keep the blocks whose Frobenius norm is >= eps.
 //
-// Chains of filtered multiplies (paper Sec. 2: the sign-matrix iteration of linear-scaling
-// DFT keeps C sparse by dropping negligible blocks between products) need a filter on
-// the result blocks as well as on the block products.  bst_matrix_filter builds the kept
+// The paper names the sign-matrix iteration of linear-scaling DFT among the library's
+// operations (Sec. 2) but defines no filter; dropping the result blocks of small norm
+// between the products of such a chain is a reading of this library, beside the filter
+// on the block products.  bst_matrix_filter builds the kept
 // pattern on the GPU -- block norms (the filter's own norm kernel), a stable compaction in
 // CSR order, per-row counts, element offsets -- and returns it as a new matrix;
 // bst_matrix_filter_copy then moves the kept blocks' elements into the caller's buffer,

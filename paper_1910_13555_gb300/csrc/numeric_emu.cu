@@ -1347,6 +1347,34 @@ void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
   }
 }
 
+// Cost model of one emulated-FP64 execute (for rooflines): BF16 tensor flops issued
+// (21 slice products per 16 x 8 x 16 tile the kernel runs, padding included) and the
+// bytes its kernels move by design -- the FP64 operands read by the exponent and digit
+// passes, the digit planes written once and read once, C written, the C-major entries
+// and C block descriptors read.
+void emu_costs(bst_plan *p, cudaStream_t s, double *tensor_flops, double *bytes) {
+  *tensor_flops = 0.0;
+  *bytes = 0.0;
+  if (p->C->nblocks == 0) return;
+  EmuState &E = emu_state(p, s);
+  const auto &hb = p->h_bucket_ptr;
+  double fl = 0.0;
+  for (int32_t b = 0; b < p->nb_all; ++b) {
+    const int64_t cnt = hb[b + 1] - hb[b];
+    if (cnt == 0) continue;
+    const int kc = b % p->Dk, nc = (b / p->Dk) % p->Dn, mc = b / (p->Dk * p->Dn);
+    const int m = p->m_vals[mc], n = p->n_vals[nc], k = p->k_vals[kc];
+    const int sw = p->ctx->tune_emu_row_scale ? class_swap(p->ctx, m, n) : 0;
+    const double tiles = sw ? (double)((n + 15) / 16) * ((m + 7) / 8)
+                            : (double)((m + 15) / 16) * ((n + 7) / 8);
+    fl += (double)cnt * 21.0 * 2.0 * tiles * 16 * 8 * 16 * ((k + 15) / 16);
+  }
+  *tensor_flops = fl;
+  *bytes = 16.0 * (double)(p->A->nelem + p->B->nelem) +
+           2.0 * 2.0 * (double)(E.a_dsize + E.b_dsize) + 8.0 * (double)p->C->nelem +
+           16.0 * (double)p->T + 4.0 * kDescWords * (double)p->C->nblocks;
+}
+
 void execute_tf32x3(bst_plan *p, const NumArgs &a, cudaStream_t s) {
   if (p->C->nblocks == 0) return;
   EmuState &E = emu_state(p, s);

@@ -1300,6 +1300,24 @@ int choose_split(const bst_plan *p, int num_sms) {
   return (int)s;
 }
 
+namespace {
+
+// The direct-load kernel over every (C block, K part), then, for S > 1 parts, the
+// fixed-order reduction of the parts' partial sums (P.W) into C.
+void launch_direct_splitk(bst_plan *p, const NumParams &P, cudaStream_t s) {
+  const int64_t nc = p->C->nblocks;
+  const int wpb = 8;
+  k_num_fp64<<<nblk(nc * P.split, wpb), 32 * wpb, 0, s>>>(P);
+  BST_CHECK_LAUNCH();
+  if (P.split > 1) {
+    k_splitk_reduce<<<nblk(nc, wpb), 32 * wpb, 0, s>>>(P, nc, p->C->row, p->C->col, p->C->rsz,
+                                                       p->C->csz);
+    BST_CHECK_LAUNCH();
+  }
+}
+
+}  // namespace
+
 void execute_fp64(bst_plan *p, const NumArgs &a, int split, cudaStream_t s) {
   const int64_t nc = p->C->nblocks;
   if (nc == 0) return;
@@ -1325,36 +1343,8 @@ void execute_fp64(bst_plan *p, const NumArgs &a, int split, cudaStream_t s) {
     BST_CHECK_LAUNCH();
     return;
   }
-  NumParams P;
-  P.A = a.A;
-  P.B = a.B;
-  P.Cin = a.Cin;
-  P.C = a.C;
-  P.W = nullptr;
-  P.alpha = a.alpha;
-  P.alpha_one = a.alpha == 1.0;
-  P.has_beta = a.beta != 0.0;
-  P.beta = a.beta;
-  P.nelemC = p->C->nelem;
-  P.ntasks = nc;
-  P.split = std::max(1, split);
-  P.K = p->K;
-  P.Dk = p->Dk;
-  P.ta = p->ta;
-  P.tb = p->tb;
-  P.task_c = p->task_c;
-  P.c_cls = p->c_cls;
-  P.c_cin = p->c_cin;
-  P.c_off = p->C->off;
-  P.cin_off = p->Cin ? p->Cin->off : nullptr;
-  P.run_start = p->run_start;
-  P.run_len = p->run_len;
-  P.s_a = p->s_a;
-  P.s_b = p->s_b;
-  P.s_k = p->s_k;
-  P.cls_m = p->cls_m;
-  P.cls_n = p->cls_n;
-  P.kval = p->kval;
+  NumParams P = make_params(p, a, split);
+  P.A = a.A;  // the direct-load kernel never reads slabs in place
   if (P.split > 1) {
     const size_t need = sizeof(double) * (size_t)P.split * (size_t)P.nelemC;
     if (p->work_bytes < need) {
@@ -1366,59 +1356,17 @@ void execute_fp64(bst_plan *p, const NumArgs &a, int split, cudaStream_t s) {
     }
     P.W = static_cast<double *>(p->work.bufs.back().p);
   }
-  const int wpb = 8;
-  k_num_fp64<<<nblk(nc * P.split, wpb), 32 * wpb, 0, s>>>(P);
-  BST_CHECK_LAUNCH();
-  if (P.split > 1) {
-    k_splitk_reduce<<<nblk(nc, wpb), 32 * wpb, 0, s>>>(P, nc, p->C->row, p->C->col, p->C->rsz,
-                                                       p->C->csz);
-    BST_CHECK_LAUNCH();
-  }
+  launch_direct_splitk(p, P, s);
 }
 
-// Same launches as execute_fp64, with the split-K partial sums in a caller-provided
-// workspace W of at least split * nelem(C) doubles (no allocation here).
+// Same launches as execute_fp64's split-K path, with the partial sums in a caller-
+// provided workspace W of at least split * nelem(C) doubles (no allocation here).
 void execute_fp64_workspace(bst_plan *p, const NumArgs &a, int split, double *W, cudaStream_t s) {
-  const int64_t nc = p->C->nblocks;
-  if (nc == 0) return;
-  NumParams P;
-  P.A = a.A;
-  P.B = a.B;
-  P.Cin = a.Cin;
-  P.C = a.C;
-  P.W = W;
-  P.alpha = a.alpha;
-  P.alpha_one = a.alpha == 1.0;
-  P.has_beta = a.beta != 0.0;
-  P.beta = a.beta;
-  P.nelemC = p->C->nelem;
-  P.ntasks = nc;
-  P.split = std::max(1, split);
-  P.K = p->K;
-  P.Dk = p->Dk;
-  P.ta = p->ta;
-  P.tb = p->tb;
-  P.task_c = p->task_c;
-  P.c_cls = p->c_cls;
-  P.c_cin = p->c_cin;
-  P.c_off = p->C->off;
-  P.cin_off = p->Cin ? p->Cin->off : nullptr;
-  P.run_start = p->run_start;
-  P.run_len = p->run_len;
-  P.s_a = p->s_a;
-  P.s_b = p->s_b;
-  P.s_k = p->s_k;
-  P.cls_m = p->cls_m;
-  P.cls_n = p->cls_n;
-  P.kval = p->kval;
-  const int wpb = 8;
-  k_num_fp64<<<nblk(nc * P.split, wpb), 32 * wpb, 0, s>>>(P);
-  BST_CHECK_LAUNCH();
-  if (P.split > 1) {
-    k_splitk_reduce<<<nblk(nc, wpb), 32 * wpb, 0, s>>>(P, nc, p->C->row, p->C->col, p->C->rsz,
-                                                       p->C->csz);
-    BST_CHECK_LAUNCH();
-  }
+  if (p->C->nblocks == 0) return;
+  NumParams P = make_params(p, a, split);
+  P.A = a.A;  // the direct-load kernel never reads slabs in place
+  P.W = P.split > 1 ? W : nullptr;
+  launch_direct_splitk(p, P, s);
 }
 
 }  // namespace bst

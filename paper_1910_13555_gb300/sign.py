@@ -1,9 +1,10 @@
 """Chained filtered block-sparse products: the matrix-sign Newton-Schulz iteration.
 
-Paper Sec. 2: DBCSR serves linear-scaling DFT, where the density matrix comes from the
-matrix sign function computed by iterations made of block-sparse products; sparsity is
-kept by filtering, both the block products (eps of the multiply) and the blocks of each
-result (a post-filter).  One step here is
+Paper Sec. 2 names the sign-matrix iteration among DBCSR's operations (linear-scaling
+DFT takes the density matrix from the matrix sign function, computed by iterations made of
+block-sparse products).  The paper defines no filter; here sparsity is kept by the
+library's two readings: the block-norm filter of each product (eps of the multiply) and a
+post-filter that drops the result blocks of norm below eps_post.  One step here is
 
     T = filter(X X, eps_post)
     X <- filter(-1/2 T X + 3/2 X, eps_post)        (= (3 X - X^3) / 2)

@@ -203,6 +203,48 @@ def test_sample_matches_full():
     np.testing.assert_allclose(vals, ref, rtol=1e-14, atol=1e-14)
 
 
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T")])
+def test_sample_filter_vs_block_loop(seed, ta, tb):
+    """The sampled multiply at eps > 0 against the Python block loop under the same
+    filter, on every block of the C grid (present or not).  The sample is chosen so that
+    the filter changes values: a dropped or inverted norm test fails it."""
+    rng = np.random.default_rng(300 + seed)
+    A, B, Ci = _case(300 + seed, occ=0.5)
+    A.data *= np.repeat(10.0 ** -rng.uniform(0, 4, A.nblocks), A.block_lens)
+    B.data *= np.repeat(10.0 ** -rng.uniform(0, 4, B.nblocks), B.block_lens)
+    if ta == "T":
+        A = transpose_matrix(A)
+    if tb == "T":
+        B = transpose_matrix(B)
+    na = np.array([np.linalg.norm(block_of(A, b)) for b in range(A.nblocks)])
+    nb = np.array([np.linalg.norm(block_of(B, b)) for b in range(B.nblocks)])
+    prods = np.sort((na[:, None] * nb[None, :]).ravel())
+    eps = float(np.sqrt(prods[len(prods) // 2] * prods[len(prods) // 2 + 1]))
+    alpha, beta = -1.5, 0.25
+    ref, kept, nfilt = brute_multiply(A, B, Ci, alpha, beta, eps, ta, tb)
+    unf, _, _ = brute_multiply(A, B, Ci, alpha, beta, 0.0, ta, tb)
+    assert nfilt > 0
+    nbr, nbc = len(Ci.row_sizes), len(Ci.col_sizes)
+    bi, bj = (x.ravel().astype(np.int32) for x in np.meshgrid(np.arange(nbr), np.arange(nbc),
+                                                               indexing="ij"))
+    vals, present = oracle.multiply_sample(A, B, Ci, alpha, beta, eps, bi, bj, ta, tb,
+                                           row_sizes=Ci.row_sizes, col_sizes=Ci.col_sizes)
+    pos, changed = 0, 0
+    for e in range(len(bi)):
+        key = (int(bi[e]), int(bj[e]))
+        m, n = int(Ci.row_sizes[key[0]]), int(Ci.col_sizes[key[1]])
+        got = vals[pos:pos + m * n].reshape(m, n)
+        pos += m * n
+        assert present[e] == (key in ref), key
+        want = ref.get(key, np.zeros((m, n)))
+        scale = max(1e-300, np.abs(want).max())
+        np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-14 * scale)
+        if key in unf and np.abs(unf[key] - want).max() > 1e-6 * max(scale, np.abs(unf[key]).max()):
+            changed += 1
+    assert changed > 0  # some sampled block holds a filtered product of visible size
+
+
 def test_errors():
     A, B, Ci = _case(15)
     dup = BSMatrix(A.row_sizes, A.col_sizes, np.r_[A.rows, A.rows[:1]], np.r_[A.cols, A.cols[:1]],
