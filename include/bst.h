@@ -182,6 +182,12 @@ typedef struct {
   double bytes;           /* algorithmic bytes of execute (see bst_plan_bytes)   */
 } bst_stats;
 
+/* Counters of the plan.  Also reports device-detected errors of the plan's earlier
+ * executes: when a bounded wait inside the emulated-FP64 panel kernel ran out (the
+ * kernel then stops, leaving that execute's result incomplete, and later executes of
+ * the plan do nothing until the error is reported), it returns BST_ERR_TIMEOUT (with
+ * *out filled) and clears the error.  Synchronises when the plan has run the panel
+ * kernel. */
 bst_status bst_plan_stats(const bst_plan *plan, bst_stats *out);
 
 /* Host copies of the stacks: mnk[n_buckets*3], bucket_ptr[n_buckets+1] (int64),
@@ -209,8 +215,11 @@ bst_status bst_plan_schedule_info(const bst_plan *plan, int32_t *info);
  * tensor-core flops one execute issues (the slice products on the MMA tiles the kernel
  * runs, padding included), out[1] = bytes its kernels move by design (FP64 operands
  * read by the slicing passes, digit planes written and read once, C written, the
- * schedule read; beta = 0).  Builds the plan's emulation index when it has none yet;
- * synchronises the legacy default stream.  The paper is FP64 only: this is a reading. */
+ * schedule read; beta = 0), out[2] = bytes of intermediate partial products written
+ * and read back (the int64 slots of the panel path; 0 for the C-block kernel), out[3]
+ * = 1 when executes run the tcgen05 panel kernel, 0 for the C-block kernel.  Builds
+ * the plan's emulation schedule when it has none yet; synchronises the legacy default
+ * stream.  The paper is FP64 only: this is a reading. */
 bst_status bst_plan_emu_costs(bst_plan *plan, double *out);
 
 /* Arithmetic used by execute. */
@@ -292,6 +301,14 @@ bst_status bst_plan_destroy(bst_plan *plan);
  *     (no permuted copy is made before them) (default); 0 = always through the permuted
  *     copy.  Taken when a contraction plan is created; tune.tune_contract_slab times
  *     both on a given contraction.
+ *   BST_TUNE_EMU_PANEL (m, n ignored): 1 = emulated-FP64 executes of a plan whose
+ *     blocks fit the panel kernel (op(A) row blocks <= 128, op(B) column blocks <= 32,
+ *     inner blocks <= 32 elements) and whose inner-block panels fill at least 15 % of
+ *     its 128 x 32 tiles' multiply-adds run the tcgen05 panel kernel: per inner block k,
+ *     the op(A) blocks of column k times the op(B) blocks of row k as one dense product
+ *     on the tensor cores, digits scaled per stored block (default); 2 = the panel
+ *     kernel whenever the blocks fit; 0 = always the C-block kernel (BST_TUNE_EMU_ROW_SCALE
+ *     and BST_TUNE_EMU_SWAP apply to it).  Batches run the C-block kernel.
  * Changing a choice takes effect at the next execute of a plan; a batch built before
  * the change refuses emulated-FP64 execution (BST_ERR_STATE) and must be created again.
  * A plan or batch whose native-FP64 tiles must be split again after a change returns
@@ -302,7 +319,8 @@ enum {
   BST_TUNE_EMU_ROW_SCALE = 0,
   BST_TUNE_EMU_SWAP = 1,
   BST_TUNE_F64_SPLIT = 2,
-  BST_TUNE_CONTRACT_SLAB = 3
+  BST_TUNE_CONTRACT_SLAB = 3,
+  BST_TUNE_EMU_PANEL = 4
 };
 bst_status bst_tune_set(bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t value);
 bst_status bst_tune_get(const bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t *value);

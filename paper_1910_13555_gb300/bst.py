@@ -259,9 +259,10 @@ def bst_plan_schedule_info(plan) -> dict:
 
 
 def bst_plan_emu_costs(plan) -> dict:
-    out = np.zeros(2, np.float64)
+    out = np.zeros(4, np.float64)
     _check(load().bst_plan_emu_costs(plan, _ptr(out)), "bst_plan_emu_costs")
-    return {"tensor_flops": float(out[0]), "bytes": float(out[1])}
+    return {"tensor_flops": float(out[0]), "bytes": float(out[1]),
+            "intermediate_bytes": float(out[2]), "panel": bool(out[3])}
 
 
 def bst_plan_get_stacks(plan):
@@ -306,6 +307,7 @@ BST_TUNE_EMU_ROW_SCALE = 0
 BST_TUNE_EMU_SWAP = 1
 BST_TUNE_F64_SPLIT = 2
 BST_TUNE_CONTRACT_SLAB = 3
+BST_TUNE_EMU_PANEL = 4
 
 
 def bst_tune_set(ctx, key, value, m=0, n=0):

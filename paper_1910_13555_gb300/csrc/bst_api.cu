@@ -343,6 +343,13 @@ bst_status bst_plan_stats(const bst_plan *plan, bst_stats *out) {
   API_BEGIN
   BST_REQUIRE(plan && out, BST_ERR_INVALID_ARG, "NULL argument");
   *out = plan->stats;
+  if (plan->panel) {
+    use_device(plan->ctx);
+    const int e = bst::panel_error(const_cast<bst_plan *>(plan));
+    BST_REQUIRE(e == 0, BST_ERR_TIMEOUT,
+                "a bounded wait of the emulated-FP64 panel kernel ran out; the results of the "
+                "executes since the last check are incomplete");
+  }
   API_END
 }
 
@@ -377,7 +384,8 @@ bst_status bst_plan_emu_costs(bst_plan *plan, double *out) {
   BST_REQUIRE(plan && out, BST_ERR_INVALID_ARG, "NULL argument");
   use_device(plan->ctx);
   cudaStream_t s = nullptr;
-  bst::emu_costs(plan, s, &out[0], &out[1]);
+  bst::emu_costs(plan, s, &out[0], &out[1], &out[2]);
+  out[3] = bst::panel_usable(plan, s) ? 1.0 : 0.0;
   BST_CUDA(cudaStreamSynchronize(s));
   API_END
 }
@@ -505,6 +513,10 @@ bst_status bst_tune_set(bst_ctx *ctx, int32_t key, int32_t m, int32_t n, int32_t
       BST_REQUIRE(value == 0 || value == 1, BST_ERR_INVALID_ARG, "value must be 0 or 1");
       ctx->tune_contract_slab = value;
       break;
+    case BST_TUNE_EMU_PANEL:
+      BST_REQUIRE(value >= 0 && value <= 2, BST_ERR_INVALID_ARG, "value must be 0, 1 or 2");
+      ctx->tune_emu_panel = value;
+      break;
     case BST_TUNE_F64_SPLIT:
       BST_REQUIRE(value == -1 || (value >= 1 && value <= 16), BST_ERR_INVALID_ARG,
                   "value must be -1 or 1..16");
@@ -536,6 +548,9 @@ bst_status bst_tune_get(const bst_ctx *ctx, int32_t key, int32_t m, int32_t n, i
     case BST_TUNE_CONTRACT_SLAB:
       *value = ctx->tune_contract_slab;
       break;
+    case BST_TUNE_EMU_PANEL:
+      *value = ctx->tune_emu_panel;
+      break;
     case BST_TUNE_F64_SPLIT: {
       auto it = ctx->tune_f64_split.find({m, n});
       *value = it == ctx->tune_f64_split.end() ? -1 : it->second;
@@ -551,6 +566,7 @@ bst_status bst_plan_destroy(bst_plan *plan) {
   API_BEGIN
   if (!plan) return BST_OK;
   bst::emu_state_free(plan);
+  bst::panel_state_free(plan);
   bst::adj_state_free(plan);
   if (plan->C) {
     plan->C->owned_by_plan = false;

@@ -120,6 +120,9 @@ struct bst_ctx {
   // contractions: read an operand whose matrix view is a sequence of contiguous slabs of
   // each tensor block in place (1) or through a permuted copy (0)
   int tune_contract_slab = 1;
+  // emulated FP64: run the tcgen05 panel kernel on plans that suit it (1) or always the
+  // C-block kernel (0)
+  int tune_emu_panel = 1;
   int64_t tune_version = 0;
 };
 
@@ -271,6 +274,7 @@ OpView make_opview(const bst_matrix *m, bool trans, Arena &ar, cudaStream_t s);
 
 namespace bst {
 struct EmuState;
+struct PanelState;
 struct AdjState;
 struct Contract;
 }  // namespace bst
@@ -335,6 +339,7 @@ struct bst_plan {
   bst_stats stats{};
   // emulated-precision state (numeric_emu.cu), built on first use
   bst::EmuState *emu = nullptr;
+  bst::PanelState *panel = nullptr;  // tcgen05 panel schedule (emu_panel.cu), built on first use
   bst::AdjState *adj = nullptr;  // adjoint grouping of the stacks (adjoint.cu)
   // contraction glue (remap.cu)
   bst::Contract *contract = nullptr;
@@ -359,7 +364,14 @@ void execute_fp64_workspace(bst_plan *p, const NumArgs &a, int split, double *W,
 void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s);
 void execute_tf32x3(bst_plan *p, const NumArgs &a, cudaStream_t s);
 void emu_state_free(bst_plan *p);
-void emu_costs(bst_plan *p, cudaStream_t s, double *tensor_flops, double *bytes);
+// tcgen05 panel path of the emulated FP64 execute (emu_panel.cu)
+bool panel_usable(bst_plan *p, cudaStream_t s);  // builds the schedule on first use
+void execute_emu_panel(bst_plan *p, const NumArgs &a, cudaStream_t s);
+void panel_costs(bst_plan *p, cudaStream_t s, double *out);  // out[3]
+void panel_state_free(bst_plan *p);
+int panel_error(bst_plan *p);  // device error recorded by a panel launch (cleared)
+void emu_costs(bst_plan *p, cudaStream_t s, double *tensor_flops, double *bytes,
+               double *intermediate);
 void adj_state_free(bst_plan *p);
 // contractions (contract.cu)
 // throws BST_ERR_STATE when a tensor the execute reads or writes has no data bound

@@ -1328,6 +1328,10 @@ void launch_emu_persist(const void *params, const int64_t *items, int64_t nitems
 
 void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
   if (p->C->nblocks == 0) return;
+  if (panel_usable(p, s)) {
+    execute_emu_panel(p, a, s);
+    return;
+  }
   EmuState &E = emu_state(p, s);
   emu_alloc_digits(E);
   emu_schedule(p, E, s);  // C block descriptors, rebuilt when tuning changed
@@ -1348,14 +1352,24 @@ void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
 }
 
 // Cost model of one emulated-FP64 execute (for rooflines): BF16 tensor flops issued
-// (21 slice products per 16 x 8 x 16 tile the kernel runs, padding included) and the
-// bytes its kernels move by design -- the FP64 operands read by the exponent and digit
-// passes, the digit planes written once and read once, C written, the C-major entries
-// and C block descriptors read.
-void emu_costs(bst_plan *p, cudaStream_t s, double *tensor_flops, double *bytes) {
+// (21 slice products per MMA tile the kernel runs, padding included), the bytes its
+// kernels move by design -- the FP64 operands read by the exponent and digit passes,
+// the digit planes written once and read once, C written, the schedule read -- and the
+// intermediate bytes of partial products (the panel path's int64 slots).
+void emu_costs(bst_plan *p, cudaStream_t s, double *tensor_flops, double *bytes,
+               double *intermediate) {
   *tensor_flops = 0.0;
   *bytes = 0.0;
+  *intermediate = 0.0;
   if (p->C->nblocks == 0) return;
+  if (panel_usable(p, s)) {
+    double o[3];
+    panel_costs(p, s, o);
+    *tensor_flops = o[0];
+    *bytes = o[1];
+    *intermediate = o[2];
+    return;
+  }
   EmuState &E = emu_state(p, s);
   const auto &hb = p->h_bucket_ptr;
   double fl = 0.0;
