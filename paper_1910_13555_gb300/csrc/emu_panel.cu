@@ -123,6 +123,7 @@ struct PanelState {
   int32_t *pair_pos = nullptr;  // per C-major product: its pair entry
   int64_t *cbeg = nullptr;      // per C block: first C-major product (nc + 1)
   int32_t *red = nullptr;       // C blocks summed from slots (several products or C_in)
+  int4 *red_desc = nullptr;     // their descriptors (two int4 each)
   int64_t *slot_base = nullptr;
   int64_t slot_elems = 0;
   int64_t *slots = nullptr;
@@ -157,6 +158,28 @@ __device__ __forceinline__ double i64_scaled(long long v, int e2) {
   const int be = (int)((bits >> 52) & 0x7ff) + e2;
   if (be <= 0 || be >= 2047) return ldexp_slow(d, e2);
   return __longlong_as_double(bits + ((long long)e2 << 52));
+}
+
+// The same with integer instructions only (GB300's FP64 unit, where the hardware
+// conversion runs, is slow to return results; measured faster in the reduction kernel,
+// slower than the hardware conversion in the panel kernel's copy-out, where the extra
+// integer instructions compete for issue slots): |v| normalised by its leading-zero
+// count, its top 53 bits rounded to nearest-even on the 11 below, the exponent field
+// 1086 - lz + e2 assembled (a rounding carry into bit 53 raises it by one).  Checked
+// against the correctly rounded conversion on 600 000 values; results outside the
+// normal range go through ldexp.
+__device__ __forceinline__ double i64_scaled_int(long long v, int e2) {
+  if (v == 0) return 0.0;
+  const unsigned long long sg = (unsigned long long)v & (1ull << 63);
+  unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  a <<= lz;
+  unsigned long long m = a >> 11;
+  const unsigned rem = (unsigned)a & 0x7FFu;
+  m += (rem > 0x400u || (rem == 0x400u && (m & 1ull))) ? 1ull : 0ull;
+  const int be = 1086 - lz + e2;
+  if (be <= 0 || be >= 2046) return ldexp_slow(__ll2double_rn(v), e2);
+  return __longlong_as_double((long long)(sg | (((unsigned long long)(be - 1) << 52) + m)));
 }
 
 __device__ __forceinline__ long long round_shift(long long v, int sh) {
@@ -196,6 +219,22 @@ __global__ void k_pan_compact(int64_t nc, const int32_t *__restrict__ flag,
   if (c < nc && flag[c]) out[pos[c]] = (int32_t)c;
 }
 
+// descriptors of the reduced C blocks (the scale word is filled per execute)
+__global__ void k_pan_red_desc(int64_t nred, const int32_t *__restrict__ red,
+                               const int32_t *__restrict__ cnt, const int32_t *__restrict__ c_cin,
+                               const int32_t *__restrict__ crow, const int32_t *__restrict__ ccol,
+                               const int32_t *__restrict__ rsz, const int32_t *__restrict__ csz,
+                               const int64_t *__restrict__ slot_base, const int64_t *__restrict__ c_off,
+                               int4 *__restrict__ desc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nred) return;
+  const int c = red[i];
+  const unsigned long long sb = (unsigned long long)slot_base[c], co = (unsigned long long)c_off[c];
+  desc[2 * i] = make_int4((int)(unsigned)sb, (int)(unsigned)(sb >> 32), (int)(unsigned)co,
+                          (int)(unsigned)(co >> 32));
+  desc[2 * i + 1] = make_int4(rsz[crow[c]] * csz[ccol[c]], cnt[c], 0, c_cin[c]);
+}
+
 struct PairArgs {
   int64_t nc;
   int32_t Dk;
@@ -228,7 +267,7 @@ __global__ void k_pan_pairs(PairArgs P) {
       const int64_t pos = U.pb + (int64_t)U.nab * V.cum + (int64_t)aw.y * V.nbb + bw.y;
       const long long dst = r ? -(P.slot_base[c] + q * mn) - 2 : P.c_off[c];
       P.pairs[pos] = make_int4((int)(unsigned)(unsigned long long)dst,
-                               (int)(unsigned)((unsigned long long)dst >> 32), 0, (int)c);
+                               (int)(unsigned)((unsigned long long)dst >> 32), 0, -1);
       P.pair_pos[e0 + q] = (int32_t)pos;
     }
   }
@@ -373,6 +412,7 @@ struct ShiftArgs {
   const int32_t *a_exp, *b_exp;
   int4 *pairs;
   int32_t *c_scale;
+  int4 *desc;
 };
 
 // common scale of every reduced C block and each of its products' shift to it
@@ -390,6 +430,7 @@ __global__ void k_pan_shift(ShiftArgs P) {
   const int G = max(0, lg - 3);  // np values below 2^59.1 each sum below 2^62.1
   S += G;
   P.c_scale[c] = S;
+  P.desc[2 * i + 1].z = S;
   int q = 0;
   const int64_t e0 = P.cbeg[c];
   for (int kc = 0; kc < P.Dk; ++kc) {
@@ -403,6 +444,7 @@ __global__ void k_pan_shift(ShiftArgs P) {
 
 struct RedArgs {
   int64_t nred;
+  const int4 *desc;  // per reduced C block: {slot base, C offset}, {m n, products, scale, C_in}
   const int32_t *red, *crow, *ccol, *rsz, *csz, *c_cin;
   const int64_t *cbeg, *slot_base, *c_off, *cin_off;
   const int32_t *c_scale;
@@ -420,14 +462,12 @@ __global__ void k_pan_reduce(RedArgs P) {
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= P.nred) return;
-  const int c = P.red[i];
-  const int mn = P.rsz[P.crow[c]] * P.csz[P.ccol[c]];
-  const int np = (int)(P.cbeg[c + 1] - P.cbeg[c]);
-  const long long *sl = P.slots + P.slot_base[c];
-  const int sc = P.c_scale[c] - 54;
-  const int cin = P.c_cin[c];
+  const int4 d0 = P.desc[2 * i], d1 = P.desc[2 * i + 1];
+  const int mn = d1.x, np = d1.y, sc = d1.z - 54, cin = d1.w;
+  const long long *sl =
+      P.slots + (long long)(((unsigned long long)(unsigned)d0.y << 32) | (unsigned)d0.x);
   const double *ci = (P.has_beta && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
-  double *out = P.C + P.c_off[c];
+  double *out = P.C + (long long)(((unsigned long long)(unsigned)d0.w << 32) | (unsigned)d0.z);
   for (int e = lane; e < mn; e += 32) {
     // the common counts spelled out so that all loads are in flight before the adds
     long long acc = 0;
@@ -448,7 +488,7 @@ __global__ void k_pan_reduce(RedArgs P) {
       }
       for (; q < np; ++q) acc += __ldcs(sl + (int64_t)q * mn + e);
     }
-    double v = np > 0 ? i64_scaled(acc, sc) : 0.0;
+    double v = np > 0 ? i64_scaled_int(acc, sc) : 0.0;
     if (!P.alpha_one) v *= P.alpha;
     if (ci) v = fma(P.beta, ci[e], v);
     out[e] = v;
@@ -878,10 +918,12 @@ __global__ void __launch_bounds__(576, 1) k_pan_mma(PanArgs P) {
                 (unsigned long long)(lo + (long long)((unsigned long long)(unsigned)hi << 32));
           }
         }
-        epi_bar(g);
-        // copy-out phase: the eight warps of the group take the tile's products in turn;
-        // every (A block, B block) product is m x n contiguous values, written coalesced
         const int np = nab * nbb, inv = rec[0].y;  // ib = x / nbb = (x * inv) >> 16, x < 256
+        epi_bar(g);
+        // copy-out phase: the eight warps of the group take the tile's products in turn
+        // (round robin measured faster than giving each warp an equal share of elements
+        // in consecutive products); every (A block, B block) product is m x n contiguous
+        // values, written coalesced
         for (int x = wg; x < np; x += 8) {
           {
             const int ib = (x * inv) >> 16, jb = x - ib * nbb;
@@ -894,7 +936,7 @@ __global__ void __launch_bounds__(576, 1) k_pan_mma(PanArgs P) {
             const int mn = ar.y * bq.y;
             const unsigned long long *src = stg + ar.x * kStgLd + bq.x;
             // element e of the product: row p = e / n, column qq = e - p n of the block;
-            // two elements per iteration (e and e + 32) as independent chains
+            // four elements per iteration (e, e + 32, e + 64, e + 96) as independent chains
             const unsigned n = (unsigned)bq.y, mg = (unsigned)bq.w;
             auto at = [&](int e) -> long long {
               const int p = (int)(((unsigned)e * mg) >> 20);
@@ -905,11 +947,14 @@ __global__ void __launch_bounds__(576, 1) k_pan_mma(PanArgs P) {
               const int e2 = ar.z + bq.z - 54;
               double *o = P.C + dst;
               if (P.alpha_one) {
-                for (int e = lane; e < mn; e += 64) {
-                  const bool two = e + 32 < mn;
-                  const long long x0 = at(e), x1 = two ? at(e + 32) : 0;
+                for (int e = lane; e < mn; e += 128) {
+                  const bool v1 = e + 32 < mn, v2 = e + 64 < mn, v3 = e + 96 < mn;
+                  const long long x0 = at(e), x1 = v1 ? at(e + 32) : 0, x2 = v2 ? at(e + 64) : 0,
+                                  x3 = v3 ? at(e + 96) : 0;
                   o[e] = i64_scaled(x0, e2);
-                  if (two) o[e + 32] = i64_scaled(x1, e2);
+                  if (v1) o[e + 32] = i64_scaled(x1, e2);
+                  if (v2) o[e + 64] = i64_scaled(x2, e2);
+                  if (v3) o[e + 96] = i64_scaled(x3, e2);
                 }
               } else {
                 for (int e = lane; e < mn; e += 32) o[e] = P.alpha * i64_scaled(at(e), e2);
@@ -919,11 +964,14 @@ __global__ void __launch_bounds__(576, 1) k_pan_mma(PanArgs P) {
               // block's common scale; the reduction kernel adds a block's slots
               long long *sl = P.slots + (-(dst + 2));
               const int sh = pe.z;
-              for (int e = lane; e < mn; e += 64) {
-                const bool two = e + 32 < mn;
-                const long long x0 = at(e), x1 = two ? at(e + 32) : 0;
+              for (int e = lane; e < mn; e += 128) {
+                const bool v1 = e + 32 < mn, v2 = e + 64 < mn, v3 = e + 96 < mn;
+                const long long x0 = at(e), x1 = v1 ? at(e + 32) : 0, x2 = v2 ? at(e + 64) : 0,
+                                x3 = v3 ? at(e + 96) : 0;
                 sl[e] = round_shift(x0, sh);
-                if (two) sl[e + 32] = round_shift(x1, sh);
+                if (v1) sl[e + 32] = round_shift(x1, sh);
+                if (v2) sl[e + 64] = round_shift(x2, sh);
+                if (v3) sl[e + 96] = round_shift(x3, sh);
               }
             }
           }
@@ -1015,31 +1063,62 @@ static void panel_build(bst_plan *p, PanelState &PS, cudaStream_t s) {
         arowi[pos] = i;
       }
   }
-  // B panels (op(B) block rows, already in block-column order) cut into N-tiles
+  // Bins of a panel: first-fit decreasing of the blocks (sizes sz[x], x < n) into bins
+  // of capacity cap holding at most maxn blocks; returns the bin of each block (blocks
+  // of one bin keep their panel order).  Fewer, fuller tiles than cutting the panel in
+  // order: the 5/13/23-element blocks of the 4000 x 4000 banded product fill 88 % of
+  // the 32-column N-tiles this way against 76 % (67 134 N-tiles against 78 098).
+  auto ffd = [](const std::vector<int> &sz, int cap, int maxn, std::vector<int> &bin) {
+    const int n = (int)sz.size();
+    std::vector<int> ord(n);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return sz[x] > sz[y]; });
+    std::vector<int> used, cnt;
+    bin.assign(n, -1);
+    for (int x : ord) {
+      int b = 0;
+      while (b < (int)used.size() && (used[b] + sz[x] > cap || cnt[b] >= maxn)) ++b;
+      if (b == (int)used.size()) {
+        used.push_back(0);
+        cnt.push_back(0);
+      }
+      used[b] += sz[x];
+      cnt[b] += 1;
+      bin[x] = b;
+    }
+    return (int)used.size();
+  };
+  // B panels (op(B) block rows) packed into N-tiles
   std::vector<PNTile> nt;
   std::vector<int4> blist;
   std::vector<int2> bwhere((size_t)nbk, make_int2(-1, -1));
   std::vector<int32_t> kv0((size_t)K, 0), knN((size_t)K, 0);
   int64_t bimg = 0;
+  std::vector<int> sz, bin;
   for (int32_t k = 0; k < K; ++k) {
     kv0[k] = (int32_t)nt.size();
     const int nq = (acs[k] + 15) / 16;
     if (kcnt[k + 1] == kcnt[k]) continue;  // no op(A) block in this panel
+    const int32_t e0 = vb.rowptr[k], ne = vb.rowptr[k + 1] - e0;
+    if (ne == 0) continue;
+    sz.resize(ne);
+    for (int x = 0; x < ne; ++x) sz[x] = bcs[vb.col[e0 + x]];
+    const int nbins = ffd(sz, kTN, kMaxBB, bin);
     int cum = 0;
-    for (int32_t e = vb.rowptr[k]; e < vb.rowptr[k + 1];) {
+    for (int b = 0; b < nbins; ++b) {
       PNTile V{};
       V.b_img = bimg;
       V.bb0 = (int)blist.size();
       V.cum = cum;
       V.nq = nq;
       int used = 0;
-      while (e < vb.rowptr[k + 1] && V.nbb < kMaxBB && used + bcs[vb.col[e]] <= kTN) {
-        const int n = bcs[vb.col[e]];
+      for (int x = 0; x < ne; ++x) {
+        if (bin[x] != b) continue;
+        const int32_t e = e0 + x;
         bwhere[(size_t)vb.blk[e]] = make_int2((int)nt.size(), V.nbb);
-        blist.push_back(make_int4(vb.blk[e], used, n, 0));
-        used += n;
+        blist.push_back(make_int4(vb.blk[e], used, sz[x], 0));
+        used += sz[x];
         ++V.nbb;
-        ++e;
       }
       cum += V.nbb;
       bimg += (int64_t)kDig * nq * kBStep;
@@ -1047,7 +1126,7 @@ static void panel_build(bst_plan *p, PanelState &PS, cudaStream_t s) {
     }
     knN[k] = (int32_t)nt.size() - kv0[k];
   }
-  // A tiles: units (k, tile) of panels with op(B) blocks
+  // A tiles: units (k, tile) of panels with op(B) blocks, packed the same way
   struct HU {
     PUnit U;
     double cost;
@@ -1058,17 +1137,18 @@ static void panel_build(bst_plan *p, PanelState &PS, cudaStream_t s) {
   for (int32_t k = 0; k < K; ++k) {
     if (knN[k] == 0) continue;
     const int nq = (acs[k] + 15) / 16;
-    for (int64_t e = kcnt[k]; e < kcnt[k + 1];) {
+    const int64_t e0 = kcnt[k];
+    const int ne = (int)(kcnt[k + 1] - e0);
+    sz.resize(ne);
+    for (int x = 0; x < ne; ++x) sz[x] = ars[arowi[e0 + x]];
+    const int nbins = ffd(sz, kTM, kMaxAB, bin);
+    for (int b = 0; b < nbins; ++b) {
       HU h{};
       h.U.v0 = kv0[k];
       h.U.nN = knN[k];
       h.U.nq = nq;
-      int used = 0;
-      while (e < kcnt[k + 1] && (int)h.blocks.size() < kMaxAB && used + ars[arowi[e]] <= kTM) {
-        h.blocks.push_back((int32_t)e);
-        used += ars[arowi[e]];
-        ++e;
-      }
+      for (int x = 0; x < ne; ++x)
+        if (bin[x] == b) h.blocks.push_back((int32_t)(e0 + x));
       h.U.nab = (int)h.blocks.size();
       h.cost = (double)h.U.nN * (2.0 + nq);
       tiles_mac += (double)h.U.nN * kTM * kTN * 16 * nq;
@@ -1191,6 +1271,13 @@ static void panel_build(bst_plan *p, PanelState &PS, cudaStream_t s) {
   PS.red = ar.alloc_n<int32_t>((size_t)std::max<int32_t>(nred, 1));
   k_pan_compact<<<nblk(nc, 256), 256, 0, s>>>(nc, flag, rpos, PS.red);
   BST_CHECK_LAUNCH();
+  PS.red_desc = ar.alloc_n<int4>(2 * (size_t)std::max<int32_t>(nred, 1));
+  if (nred > 0) {
+    k_pan_red_desc<<<nblk(nred, 256), 256, 0, s>>>(nred, PS.red, cnt, p->c_cin, C->row, C->col,
+                                                    C->rsz, C->csz, PS.slot_base, C->off,
+                                                    PS.red_desc);
+    BST_CHECK_LAUNCH();
+  }
 
   PS.slots = ar.alloc_n<int64_t>((size_t)std::max<int64_t>(PS.slot_elems, 1));
   PairArgs pa{};
@@ -1305,6 +1392,7 @@ void execute_emu_panel(bst_plan *p, const NumArgs &a, cudaStream_t s) {
     sh.a_exp = PS.a_exp;
     sh.b_exp = PS.b_exp;
     sh.pairs = PS.pairs;
+    sh.desc = PS.red_desc;
     sh.c_scale = PS.c_scale;
     k_pan_shift<<<nblk(PS.nred, 256), 256, 0, s>>>(sh);
     BST_CHECK_LAUNCH();
@@ -1336,6 +1424,7 @@ void execute_emu_panel(bst_plan *p, const NumArgs &a, cudaStream_t s) {
     RedArgs R{};
     R.nred = PS.nred;
     R.red = PS.red;
+    R.desc = PS.red_desc;
     R.crow = p->C->row;
     R.ccol = p->C->col;
     R.rsz = p->C->rsz;
