@@ -284,49 +284,31 @@ def run_reference(args):
     return 0
 
 
-# measured BF16 mma.sync throughput of one GB300 (a throughput probe with 8 independent
-# chains per thread); the emulated kernel is built on mma.sync m16n8k16
-MMA_SYNC_BF16_TFLOPS = 604.0
-
-
-def emu_tensor_ops(plan, ctx):
-    """BF16 tensor flops the emulated kernel executes for a plan: per product 21 slice
-    products on 16 x 8 tiles covering the C block (rows over the block's rows, or over
-    its columns for a swapped class) and the inner size padded to 16."""
-    from paper_1910_13555_gb300 import bst
-    st = bst.bst_plan_get_stacks(plan.handle)
-    cnt = (st["bucket_ptr"][1:] - st["bucket_ptr"][:-1]).astype(float)
-    total = 0.0
-    for (m, n, k), c in zip(st["mnk"].tolist(), cnt):
-        sw = bst.bst_tune_get(ctx, bst.BST_TUNE_EMU_SWAP, m, n)
-        plain = -(-m // 16) * -(-n // 8)
-        swapped = -(-n // 16) * -(-m // 8)
-        if sw < 0:
-            sw = 1 if swapped < plain else 0
-        tiles = swapped if sw else plain
-        total += c * 21 * 2 * tiles * 16 * 8 * 16 * -(-k // 16)
-    return total
-
-
 def emu_roofline(plans, ms, ctx):
     """Roofline of the emulated-FP64 execute of `plans` (run together in `ms`): the time
     the slice products would take at the measured BF16 peak against the time its bytes
     would take at the measured HBM bandwidth; fraction = the larger / measured time.
     Executed tensor flops and bytes come from the library (bst_plan_emu_costs)."""
     from paper_1910_13555_gb300 import bst
-    ops = byt = 0.0
+    ops = byt = inter = 0.0
     for pl in plans:
         c = bst.bst_plan_emu_costs(pl.handle)
         ops += c["tensor_flops"]
         byt += c["bytes"]
+        inter += c["intermediate_bytes"]
     hbm = MEASURED_HBM_GBS
     t_tensor = ops / (BF16_PEAK_TFLOPS * 1e12) if BF16_PEAK_TFLOPS else 0.0
     t_hbm = byt / (hbm * 1e9) if hbm else 0.0
     t_roof = max(t_tensor, t_hbm)
+    t_roof2 = max(t_tensor, (byt + inter) / (hbm * 1e9) if hbm else 0.0)
     return {"bound": "tensor" if t_tensor >= t_hbm else "hbm",
-            "executed_bf16_tflop": ops / 1e12, "bytes": byt,
+            "executed_bf16_tflop": ops / 1e12, "bytes": byt, "intermediate_bytes": inter,
             "t_roof_ms": t_roof * 1e3, "frac": t_roof / (ms * 1e-3) if ms > 0 else None,
-            "peaks": f"bf16 {BF16_PEAK_TFLOPS} TFLOP/s, hbm {hbm} GB/s (measured)"}
+            "frac_with_intermediates": t_roof2 / (ms * 1e-3) if ms > 0 else None,
+            "peaks": f"bf16 {BF16_PEAK_TFLOPS} TFLOP/s, hbm {hbm} GB/s (measured)",
+            "note": "bytes: operands read by the slicing passes, digit planes written and "
+                    "read once, C written, schedule read; intermediate_bytes: partial "
+                    "products written and read back (the panel path's int64 slots)"}
 
 
 def keep_plan_index(A, B, p, device):
@@ -471,7 +453,7 @@ def run_ours(args):
     }
 
     if not args.no_e2e:
-        line["e2e"] = e2e_leg(p, local_rank, min(args.steps, 6), stream, barrier, world, dev)
+        line["e2e"] = e2e_leg(p, local_rank, max(args.steps, 20), stream, barrier, world, dev)
 
     if not args.no_extras:
         from paper_1910_13555_gb300 import tune
@@ -498,8 +480,10 @@ def run_ours(args):
                     pl2 = step(prec, ev)
                     torch.cuda.synchronize()
                     first.append(ev[0].elapsed_time(ev[1]))
+                pl2.execute(1.0, 0.0, prec, 1)  # second execute: the plan's default kernel
+                torch.cuda.synchronize()
                 times = []
-                for _ in range(5):
+                for _ in range(20):
                     ev[0].record(stream)
                     pl2.execute(1.0, 0.0, prec, 1)
                     ev[1].record(stream)
@@ -508,21 +492,15 @@ def run_ours(args):
                 t = statistics.median(times)
                 extras[name] = {"numeric_gflops": flops / (t * 1e-3) / 1e9, "ms": t,
                                 "speedup_vs_fp64_numeric": num_avg / t,
-                                "first_execute_ms": min(first),
-                                "note": "repeat executes of one plan; first_execute_ms adds "
-                                        "the per-plan slicing index"}
+                                "first_execute_ms": min(first), "repeats_timed": len(times),
+                                "note": "median of 20 repeat executes of one plan after 3 "
+                                        "(slicing of the current data + products); "
+                                        "first_execute_ms: a fresh plan's first execute"}
                 if prec == bst.BST_FP64_EMU_BF16:
-                    ops = emu_tensor_ops(pl2, bst.context(local_rank))
-                    achieved_t = ops / (t * 1e-3) / 1e12
-                    extras[name]["tensor_roofline"] = {
-                        "bound": "tensor", "executed_bf16_tflop_per_execute": ops / 1e12,
-                        "achieved": achieved_t, "unit": "TFLOP/s",
-                        "peak_mma_sync_bf16": MMA_SYNC_BF16_TFLOPS,
-                        "frac": achieved_t / MMA_SYNC_BF16_TFLOPS,
-                        "peak_measured_bf16": BF16_PEAK_TFLOPS,
-                        "frac_of_measured": achieved_t / BF16_PEAK_TFLOPS if BF16_PEAK_TFLOPS else None,
-                        "note": "whole execute (slicing + products) against the BF16 mma.sync "
-                                "rate and the measured cuBLAS BF16 rate"}
+                    c = bst.bst_plan_emu_costs(pl2.handle)
+                    extras[name]["kernel"] = "k_pan_mma (tcgen05 panels)" if c["panel"] else \
+                        "k_num_emu_bf16_persist1 (mma.sync C blocks)"
+                    extras[name]["roofline"] = emu_roofline([pl2], t, bst.context(local_rank))
                 if sample is not None:
                     extras[name]["rel_err_vs_oracle_sample"] = sample.error(pl2)
                 del pl, pl2
@@ -853,32 +831,42 @@ def e2e_leg(p, local_rank, steps, stream, barrier, world, dev):
     hcs = [None, None]
     alive = [None, None]  # objects of the step in flight on each stream
     info = {"flops": 0.0, "n": 0}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    marks = []  # per step: events after H2D, after create + plan, after execute, D2H start / end
 
     def one(i):
         slot = i % 2
         s = streams[slot]
+        m = [ev() for _ in range(6)]
         with torch.cuda.stream(s):
             sh = s.cuda_stream
+            m[0].record(s)
             da = ha.to(dev, non_blocking=True)
             db = hb.to(dev, non_blocking=True)
+            m[1].record(s)
             A = bst.Matrix(bst.bst_matrix_create(ctx, p.A.row_sizes, p.A.col_sizes, p.A.rows,
                                                  p.A.cols, da, stream=sh), da)
             B = bst.Matrix(bst.bst_matrix_create(ctx, p.B.row_sizes, p.B.col_sizes, p.B.rows,
                                                  p.B.cols, db, stream=sh), db)
-            plan = bst.multiply(A, B, None, 1.0, 0.0, p.eps, device=local_rank, stream=sh)
+            plan = bst.multiply_plan(A, B, None, p.eps, device=local_rank, stream=sh)
+            plan.alloc_result(local_rank)
+            m[2].record(s)
+            plan.execute(1.0, 0.0, bst.BST_FP64, 1, stream=sh)
+            m[3].record(s)
             n = plan.result.info[3]
             if hcs[slot] is None or hcs[slot].numel() < n:
                 hcs[slot] = torch.empty(n, dtype=torch.float64).pin_memory()
-            done = torch.cuda.Event()
-            done.record(s)
         cs = copies[slot]
-        cs.wait_event(done)
+        cs.wait_event(m[3])
         with torch.cuda.stream(cs):
+            m[4].record(cs)
             plan.result.data.record_stream(cs)
             hcs[slot][:n].copy_(plan.result.data[:n], non_blocking=True)
+            m[5].record(cs)
         alive[slot] = (plan, A, B, da, db)
         info["flops"] = plan.stats()["flops"]
         info["n"] = n
+        return m
 
     one(0)
     one(1)
@@ -886,7 +874,7 @@ def e2e_leg(p, local_rank, steps, stream, barrier, world, dev):
     barrier()
     t = time.perf_counter()
     for i in range(steps):
-        one(i)
+        marks.append(one(i))
     torch.cuda.synchronize()
     barrier()
     dt = (time.perf_counter() - t) / steps
@@ -895,9 +883,16 @@ def e2e_leg(p, local_rank, steps, stream, barrier, world, dev):
     dt, flops = reduce_over_ranks(dt, flops, world, dev)
     h2d = (p.A.data.nbytes + p.B.data.nbytes + 8 * (p.A.nblocks + p.B.nblocks) +
            4 * (len(p.A.row_sizes) + len(p.A.col_sizes) + len(p.B.row_sizes) + len(p.B.col_sizes)))
+    phase = lambda a, b: statistics.median(x[a].elapsed_time(x[b]) for x in marks)
     return {"value": flops / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(8 * info["n"]), "ms_per_step": dt * 1e3,
-            "streams": "2 compute + 2 copy"}
+            "steps_timed": steps, "streams": "2 compute + 2 copy",
+            "phases_ms_median": {"h2d": phase(0, 1), "create_and_plan": phase(1, 2),
+                                 "execute": phase(2, 3), "d2h": phase(4, 5)},
+            "phases_note": "CUDA events per step on its own streams; phases of consecutive "
+                           "steps overlap (the read-back of one step runs beside the next "
+                           "steps' uploads, plans and executes), so they do not add up to "
+                           "ms_per_step"}
 
 
 def main():

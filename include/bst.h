@@ -217,7 +217,8 @@ bst_status bst_plan_schedule_info(const bst_plan *plan, int32_t *info);
  * read by the slicing passes, digit planes written and read once, C written, the
  * schedule read; beta = 0), out[2] = bytes of intermediate partial products written
  * and read back (the int64 slots of the panel path; 0 for the C-block kernel), out[3]
- * = 1 when executes run the tcgen05 panel kernel, 0 for the C-block kernel.  Builds
+ * = 1 when the plan's next execute runs the tcgen05 panel kernel, 0 for the C-block
+ * kernel; the costs are those of that kernel.  Builds
  * the plan's emulation schedule when it has none yet; synchronises the legacy default
  * stream.  The paper is FP64 only: this is a reading. */
 bst_status bst_plan_emu_costs(bst_plan *plan, double *out);
@@ -306,9 +307,12 @@ bst_status bst_plan_destroy(bst_plan *plan);
  *     inner blocks <= 32 elements) and whose inner-block panels fill at least 15 % of
  *     its 128 x 32 tiles' multiply-adds run the tcgen05 panel kernel: per inner block k,
  *     the op(A) blocks of column k times the op(B) blocks of row k as one dense product
- *     on the tensor cores, digits scaled per stored block (default); 2 = the panel
- *     kernel whenever the blocks fit; 0 = always the C-block kernel (BST_TUNE_EMU_ROW_SCALE
- *     and BST_TUNE_EMU_SWAP apply to it).  Batches run the C-block kernel.
+ *     on the tensor cores, digits scaled per stored block -- from the plan's second
+ *     emulated execute on (the first runs the C-block kernel, so a plan executed once
+ *     does not pay for building the panel schedule) (default); 2 = the panel kernel
+ *     whenever the blocks fit, from the first execute; 0 = always the C-block kernel
+ *     (BST_TUNE_EMU_ROW_SCALE and BST_TUNE_EMU_SWAP apply to it).  Batches run the
+ *     C-block kernel.
  * Changing a choice takes effect at the next execute of a plan; a batch built before
  * the change refuses emulated-FP64 execution (BST_ERR_STATE) and must be created again.
  * A plan or batch whose native-FP64 tiles must be split again after a change returns

@@ -385,7 +385,7 @@ bst_status bst_plan_emu_costs(bst_plan *plan, double *out) {
   use_device(plan->ctx);
   cudaStream_t s = nullptr;
   bst::emu_costs(plan, s, &out[0], &out[1], &out[2]);
-  out[3] = bst::panel_usable(plan, s) ? 1.0 : 0.0;
+  out[3] = bst::panel_usable(plan, s) ? 1.0 : 0.0;  // as the next execute will run
   BST_CUDA(cudaStreamSynchronize(s));
   API_END
 }

@@ -340,6 +340,7 @@ struct bst_plan {
   // emulated-precision state (numeric_emu.cu), built on first use
   bst::EmuState *emu = nullptr;
   bst::PanelState *panel = nullptr;  // tcgen05 panel schedule (emu_panel.cu), built on first use
+  int emu_executes = 0;              // emulated executes so far (panel schedule policy)
   bst::AdjState *adj = nullptr;  // adjoint grouping of the stacks (adjoint.cu)
   // contraction glue (remap.cu)
   bst::Contract *contract = nullptr;
@@ -365,7 +366,9 @@ void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s);
 void execute_tf32x3(bst_plan *p, const NumArgs &a, cudaStream_t s);
 void emu_state_free(bst_plan *p);
 // tcgen05 panel path of the emulated FP64 execute (emu_panel.cu)
-bool panel_usable(bst_plan *p, cudaStream_t s);  // builds the schedule on first use
+// whether emulated executes run the panel kernel (builds its schedule when they do);
+// count: this call is an execute (the default mode takes the panel from a plan's second)
+bool panel_usable(bst_plan *p, cudaStream_t s, bool count = false);
 void execute_emu_panel(bst_plan *p, const NumArgs &a, cudaStream_t s);
 void panel_costs(bst_plan *p, cudaStream_t s, double *out);  // out[3]
 void panel_state_free(bst_plan *p);

@@ -1323,10 +1323,20 @@ static PanelState &panel_state(bst_plan *p, cudaStream_t s) {
   return PS;
 }
 
-bool panel_usable(bst_plan *p, cudaStream_t s) {
-  if (!p->ctx->tune_emu_panel || p->C->nblocks == 0) return false;
+// By default (BST_TUNE_EMU_PANEL = 1) a plan's first emulated execute runs the C-block
+// kernel and the panel schedule is built at its second one: building it costs host work
+// and a few synchronisations of the order of the kernel time it saves, so a plan run
+// once (a step of a chain of fresh products) never pays for it.
+bool panel_usable(bst_plan *p, cudaStream_t s, bool count) {
+  const int mode = p->ctx->tune_emu_panel;
+  if (!mode || p->C->nblocks == 0) return false;
+  if (mode == 1 && !p->panel) {
+    const int n = p->emu_executes + 1;  // the execute this call is about
+    if (count) p->emu_executes = n;
+    if (n < 2) return false;
+  }
   const PanelState &PS = panel_state(p, s);
-  return PS.eligible && (p->ctx->tune_emu_panel == 2 || PS.fill >= kMinFill);
+  return PS.eligible && (mode == 2 || PS.fill >= kMinFill);
 }
 
 void panel_state_free(bst_plan *p) {

@@ -1328,7 +1328,7 @@ void launch_emu_persist(const void *params, const int64_t *items, int64_t nitems
 
 void execute_emu_bf16(bst_plan *p, const NumArgs &a, cudaStream_t s) {
   if (p->C->nblocks == 0) return;
-  if (panel_usable(p, s)) {
+  if (panel_usable(p, s, true)) {
     execute_emu_panel(p, a, s);
     return;
   }

@@ -2,10 +2,12 @@
 profilers and quick timings).
 
     python -m paper_1910_13555_gb300.run_workload <name> [--reps N] [--precision P] [--nb N] [--np P]
-                                                        [--adjoint]
+                                                        [--adjoint] [--emu-kernel K]
 
 name: banded | tall_skinny | rect_case2 | batched | rank3 | rank4 | sign
 precision: fp64 | emu | tf32x3
+emu-kernel (emulated FP64): auto (default choice) | panel (the tcgen05 panel kernel when the
+blocks fit) | block (the C-block kernel)
 
 Each run builds the plan once and executes it `reps` times (a batch for `batched`,
 one Newton-Schulz step for `sign`, the adjoint dT, dU with --adjoint for `rank3` and
@@ -36,8 +38,11 @@ def main(argv=None) -> int:
                     help="rank3 / rank4: P blocks (fewer products per C block, same C pattern)")
     ap.add_argument("--adjoint", action="store_true",
                     help="rank3 / rank4: time the adjoint (dT, dU from dR = R) instead")
+    ap.add_argument("--emu-kernel", default="auto", choices=["auto", "panel", "block"])
     a = ap.parse_args(argv)
     prec = getattr(bst, PRECISIONS[a.precision])
+    bst.bst_tune_set(bst.context(), bst.BST_TUNE_EMU_PANEL,
+                     {"auto": 1, "panel": 2, "block": 0}[a.emu_kernel])
 
     def mk(m):
         return bst.Matrix.from_host(m.row_sizes, m.col_sizes, m.rows, m.cols, m.data)

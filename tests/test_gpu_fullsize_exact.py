@@ -57,13 +57,17 @@ def test_banded_full_size_exact():
     _assert_exact(got, ref)
     assert 0 < ref["nfiltered"] < ref["ncandidates"]
     assert rel_fro(got["data"], ref["data"]) <= 1e-12
-    # emulated FP64 on the same plan: whole C within 1e-11
+    # emulated FP64 on the same plan, whole C within 1e-11: the first emulated execute
+    # runs the C-block kernel, the second the tcgen05 panel kernel (default policy)
     plan = got["plan"]
-    plan.execute(1.0, 0.0, bst.BST_FP64_EMU_BF16, 1)
-    torch.cuda.synchronize()
     ne = plan.result.info[3]
-    emu = plan.result.data[:ne].cpu().numpy()
-    assert rel_fro(emu, ref["data"]) <= 1e-11
+    for panel in (False, True):
+        assert bst.bst_plan_emu_costs(plan.handle)["panel"] == panel
+        plan.execute(1.0, 0.0, bst.BST_FP64_EMU_BF16, 1)
+        torch.cuda.synchronize()
+        emu = plan.result.data[:ne].cpu().numpy()
+        assert rel_fro(emu, ref["data"]) <= 1e-11, panel
+    plan.stats()  # reports a timeout of the panel kernel, if any
 
 
 def test_tall_skinny_full_size_exact():
