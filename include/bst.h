@@ -311,8 +311,11 @@ bst_status bst_plan_destroy(bst_plan *plan);
  *     emulated execute on (the first runs the C-block kernel, so a plan executed once
  *     does not pay for building the panel schedule) (default); 2 = the panel kernel
  *     whenever the blocks fit, from the first execute; 0 = always the C-block kernel
- *     (BST_TUNE_EMU_ROW_SCALE and BST_TUNE_EMU_SWAP apply to it).  Batches run the
- *     C-block kernel.
+ *     (BST_TUNE_EMU_ROW_SCALE and BST_TUNE_EMU_SWAP apply to it).  A batch decides
+ *     when it is created: with 1 or 2 every matrix plan the panel kernel takes (as
+ *     above, at 1 only with the 15 % fill) runs in one panel launch over all those
+ *     plans, its schedule built by bst_batch_create; the others run the C-block
+ *     kernel.
  * Changing a choice takes effect at the next execute of a plan; a batch built before
  * the change refuses emulated-FP64 execution (BST_ERR_STATE) and must be created again.
  * A plan or batch whose native-FP64 tiles must be split again after a change returns
@@ -376,6 +379,11 @@ bst_status bst_plan_result_tensor(bst_plan *plan, bst_tensor **R);
  * their own values.  An execute captured into a CUDA graph records that copy as a
  * graph node: a replay reads the buffer as the most recent execute call of the batch
  * left it (the captured call's values, until another execute call rewrites them).
+ * Emulated-FP64 executes also write per-plan scratch of the plans on the panel kernel
+ * (digit images and partial-sum slots, shared with the plans' own executes): executes
+ * of such a plan, alone or in batches, must be ordered on the GPU (one stream).  A
+ * device-side timeout of that batch launch is reported by bst_plan_stats of the
+ * first plan on the panel kernel (in the batch's flops order) as BST_ERR_TIMEOUT.
  * ------------------------------------------------------------------------- */
 bst_status bst_batch_create(bst_ctx *ctx, int32_t n, bst_plan *const *plans, bst_batch **out);
 bst_status bst_batch_execute(bst_batch *batch, const double *alpha, const double *beta,

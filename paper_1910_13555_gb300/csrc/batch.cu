@@ -5,14 +5,18 @@
 // tagged with the plan's index.  For native FP64 the list is sorted by decreasing cost
 // across the batch, so one persistent grid balances products of very different sizes
 // (the staged kernel takes chunks of items from a counter after two of its own, the
-// direct-load kernel single items from a counter).  For emulated FP64 the plans are
-// listed by decreasing flops and each plan's C blocks in CSR order, and warps take a
-// few consecutive items at a time from a counter, so neighbouring warps share operand
-// digits.  bst_batch_execute only queues work: a parameter copy from the batch's pinned
-// staging buffer, the counter reset and the launches (plus the per-plan slicing kernels
-// for emulated FP64 and the permutations of contraction views), so a call can be
-// captured into a CUDA graph and replayed; everything that allocates or synchronises
-// happens in bst_batch_create.
+// direct-load kernel single items from a counter).  For emulated FP64, the plans whose
+// blocks fit the tensor-core panel kernel (and, unless that kernel is forced, whose
+// panels are full enough) run together in one launch of it: the units (one inner block
+// of one plan each) of every such plan, by decreasing cost, with each plan's pointers
+// in a small device table; their schedules are built here, at creation.  The other
+// plans run on the C-block kernel: plans listed by decreasing flops and each plan's C
+// blocks in CSR order, warps taking a few consecutive items at a time from a counter,
+// so neighbouring warps share operand digits.  bst_batch_execute only queues work:
+// parameter copies from the batch's pinned staging buffers, the counter reset and the
+// launches (plus the per-plan slicing and reduction kernels for emulated FP64 and the
+// permutations of contraction views), so a call can be captured into a CUDA graph and
+// replayed; everything that allocates or synchronises happens in bst_batch_create.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -41,6 +45,15 @@ struct bst_batch {
   void *d_eparams = nullptr, *h_eparams = nullptr;
   size_t epbytes = 0;
   int grid_e = 0;
+  // emulated FP64 on the panel kernel: the plans it runs, their (plan, unit) list and
+  // the per-plan pointer table (staged like the parameters)
+  std::vector<int32_t> panel_plans;
+  std::vector<char> on_panel;
+  int2 *ulist = nullptr;
+  int64_t n_units = 0;
+  void *d_pplans = nullptr, *h_pplans = nullptr;
+  size_t ppbytes = 0;
+  int *panel_err = nullptr;
   int64_t tune_version = 0;  // the context's tuning state the schedules were built for
   // recorded after each parameter copy out of h_params / h_eparams; the next execute
   // waits for it before it rewrites the staging buffers
@@ -50,6 +63,7 @@ struct bst_batch {
     if (copied) cudaEventDestroy(copied);
     if (h_params) cudaFreeHost(h_params);
     if (h_eparams) cudaFreeHost(h_eparams);
+    if (h_pplans) cudaFreeHost(h_pplans);
   }
 };
 
@@ -154,13 +168,32 @@ bst_status bst_batch_create(bst_ctx *ctx, int32_t n, bst_plan *const *plans, bst
         b->titems = b->ar.alloc_n<int64_t>((size_t)b->n_titems);
         bst::sort_items(t0, tk, b->n_titems, b->titems, scratch, s);
       }
-      // emulated FP64: every C block (slicing state built per plan here)
+      // emulated FP64: plans on the panel kernel (schedule built here), every C block of
+      // the others (slicing state built per plan here)
+      b->on_panel.assign(n, 0);
+      {
+        std::vector<bst_plan *> pp;
+        for (int32_t q : order) {
+          bst_plan *p = b->plans[q];
+          if (p->contract || p->C->nblocks == 0 || !bst::panel_batch_eligible(p, s)) continue;
+          b->on_panel[q] = 1;
+          b->panel_plans.push_back(q);
+          pp.push_back(p);
+        }
+        if (!pp.empty()) {
+          b->n_units = bst::panel_batch_units(pp, b->ar, &b->ulist, s);
+          b->ppbytes = bst::panel_plan_bytes();
+          b->d_pplans = b->ar.alloc(b->ppbytes * pp.size());
+          BST_CUDA(cudaMallocHost(&b->h_pplans, b->ppbytes * pp.size()));
+          b->panel_err = bst::panel_err_flag(pp[0]);
+        }
+      }
       std::vector<int64_t> cnt(n);
       for (int32_t q = 0; q < n; ++q) {
-        cnt[q] = b->plans[q]->contract ? 0 : bst::emu_item_count(b->plans[q], s);
+        cnt[q] = b->plans[q]->contract || b->on_panel[q] ? 0 : bst::emu_item_count(b->plans[q], s);
         b->n_items_e += cnt[q];
       }
-      b->items_e = b->ar.alloc_n<int64_t>((size_t)b->n_items_e);
+      b->items_e = b->ar.alloc_n<int64_t>((size_t)std::max<int64_t>(b->n_items_e, 1));
       off = 0;
       for (int32_t q : order) {
         if (cnt[q]) bst::emu_build_items(b->plans[q], (int64_t)q << 32, b->items_e + off, s);
@@ -238,27 +271,50 @@ bst_status bst_batch_execute(bst_batch *b, const double *alpha, const double *be
       else
         bst::launch_fp64_persist(b->d_params, b->items, b->n_items, b->counter, b->grid, s);
     } else {
-      for (int32_t q = 0; q < n; ++q) {
+      for (int32_t q = 0; q < n; ++q)
         BST_REQUIRE(!b->plans[q]->contract, BST_ERR_UNSUPPORTED,
                     "emulated FP64 batches take matrix plans only");
+      std::vector<bst::NumArgs> pargs(b->panel_plans.size());
+      for (size_t i = 0; i < b->panel_plans.size(); ++i) {
+        bst_plan *p = b->plans[b->panel_plans[i]];
+        pargs[i] = plan_args(p, alpha[b->panel_plans[i]], beta[b->panel_plans[i]], s).a;
+        bst::panel_prepare(p, pargs[i], s);
+        bst::panel_fill_plan(p, pargs[i], static_cast<char *>(b->h_pplans) + i * b->ppbytes);
+      }
+      for (int32_t q = 0; q < n; ++q) {
+        if (b->on_panel[q]) continue;
         Args r = plan_args(b->plans[q], alpha[q], beta[q], s);
         if (b->plans[q]->C->nblocks > 0)
           bst::emu_prepare_and_fill(b->plans[q], r.a,
                                     static_cast<char *>(b->h_eparams) + q * b->epbytes, s);
       }
-      BST_CUDA(cudaMemcpyAsync(b->d_eparams, b->h_eparams, b->epbytes * n, cudaMemcpyHostToDevice, s));
+      if (b->n_items_e > 0)
+        BST_CUDA(cudaMemcpyAsync(b->d_eparams, b->h_eparams, b->epbytes * n,
+                                 cudaMemcpyHostToDevice, s));
+      if (!b->panel_plans.empty())
+        BST_CUDA(cudaMemcpyAsync(b->d_pplans, b->h_pplans, b->ppbytes * b->panel_plans.size(),
+                                 cudaMemcpyHostToDevice, s));
       if (!capturing) {
         BST_CUDA(cudaEventRecord(b->copied, s));
         b->copy_pending = true;
       }
-      double flops = 0.0;
-      int64_t nelem = 0;
-      for (auto *pl : b->plans) {
-        flops += pl->stats.flops;
-        nelem += pl->C->nelem;
+      if (b->n_items_e > 0) {
+        double flops = 0.0;
+        int64_t nelem = 0;
+        for (int32_t q = 0; q < n; ++q) {
+          if (b->on_panel[q]) continue;
+          flops += b->plans[q]->stats.flops;
+          nelem += b->plans[q]->C->nelem;
+        }
+        bst::launch_emu_persist(b->d_eparams, b->items_e, b->n_items_e, b->counter, b->grid_e,
+                                b->ctx->tune_emu_row_scale, bst::emu_pipelined(flops, nelem), s);
       }
-      bst::launch_emu_persist(b->d_eparams, b->items_e, b->n_items_e, b->counter, b->grid_e,
-                              b->ctx->tune_emu_row_scale, bst::emu_pipelined(flops, nelem), s);
+      if (!b->panel_plans.empty()) {
+        bst::launch_panel_batch(b->d_pplans, b->ulist, b->n_units, b->panel_err,
+                                b->ctx->num_sms, s);
+        for (size_t i = 0; i < b->panel_plans.size(); ++i)
+          bst::panel_finish(b->plans[b->panel_plans[i]], pargs[i], s);
+      }
     }
     for (int32_t q = 0; q < n; ++q) {
       if (b->plans[q]->contract) bst::contract_finish(b->plans[q], s);

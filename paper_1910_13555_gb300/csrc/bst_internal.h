@@ -373,6 +373,17 @@ void execute_emu_panel(bst_plan *p, const NumArgs &a, cudaStream_t s);
 void panel_costs(bst_plan *p, cudaStream_t s, double *out);  // out[3]
 void panel_state_free(bst_plan *p);
 int panel_error(bst_plan *p);  // device error recorded by a panel launch (cleared)
+// batches of panel plans (emu_panel.cu): one k_pan_mma launch over every plan's units
+bool panel_batch_eligible(bst_plan *p, cudaStream_t s);  // builds the schedule now
+size_t panel_plan_bytes();
+void panel_fill_plan(bst_plan *p, const NumArgs &a, void *out);
+int64_t panel_batch_units(const std::vector<bst_plan *> &plans, Arena &ar, int2 **out,
+                          cudaStream_t s);
+void panel_prepare(bst_plan *p, const NumArgs &a, cudaStream_t s);
+void panel_finish(bst_plan *p, const NumArgs &a, cudaStream_t s);
+void launch_panel_batch(const void *d_plans, const int2 *ulist, int64_t n, int *err, int num_sms,
+                        cudaStream_t s);
+int *panel_err_flag(bst_plan *p);
 void emu_costs(bst_plan *p, cudaStream_t s, double *tensor_flops, double *bytes,
                double *intermediate);
 void adj_state_free(bst_plan *p);

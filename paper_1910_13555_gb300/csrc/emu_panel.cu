@@ -670,20 +670,38 @@ __device__ __forceinline__ bool elect_one() {
   return pred != 0;
 }
 
-struct PanArgs {
+// One plan's panel schedule and this execute's output.
+struct PanPlan {
   const PUnit *units;
-  int64_t nunits;
   const PNTile *ntiles;
   const char *a_img, *b_img;
   const int4 *urec;   // per unit: kURec int4 {row offset, m, exponent, stored block}
   const int4 *ntrec;  // per N-tile: kNTRec int4 (header, column table, B blocks)
-  const int4 *pairs;  // per (unit, N-tile) pair: {dst lo, dst hi, shift, C block}
+  const int4 *pairs;  // per (unit, N-tile) pair: {dst lo, dst hi, shift, -1}
   double *C;
   long long *slots;
   double alpha;
-  int alpha_one;
+  int alpha_one, pad;
+};
+
+struct PanArgs {
+  PanPlan one;           // the plan of a single execute
+  const PanPlan *plans;  // a batch: its plans (null: `one`)
+  const int2 *ulist;     // a batch: (plan, unit) in decreasing cost (null: units of `one`)
+  int64_t nunits;
   int *err;
 };
+
+// unit u of the launch: its plan and its index in that plan's schedule
+__device__ __forceinline__ const PanPlan &unit_plan(const PanArgs &P, int64_t u, int &lu) {
+  if (!P.ulist) {
+    lu = (int)u;
+    return P.one;
+  }
+  const int2 w = P.ulist[u];
+  lu = w.y;
+  return P.plans[w.x];
+}
 
 // the units of this CTA: snake order over the cost-sorted list
 __device__ __forceinline__ int64_t unit_at(int64_t r, int G, int b) {
@@ -763,38 +781,40 @@ __global__ void __launch_bounds__(576, 1) k_pan_mma(PanArgs P) {
       for (int64_t r = 0; ok; ++r) {
         const int64_t u = unit_at(r, G, cta);
         if (u >= P.nunits) break;
-        const PUnit U = P.units[u];
+        int lu;
+        const PanPlan &Q = unit_plan(P, u, lu);
+        const PUnit U = Q.units[lu];
         const int ab = (int)(q & 1);
         if (q >= 2) {
           if (!(ok = mbar_wait(&S.empty_u[ab], (uint32_t)(((q >> 1) - 1) & 1), P.err))) break;
           if (!(ok = mbar_wait(&S.empty_a[ab], (uint32_t)(((q >> 1) - 1) & 1), P.err))) break;
         }
         mbar_expect_tx(&S.full_u[ab], 16 * kURec);
-        bulk_g2s(surec + ab * kURec, P.urec + u * kURec, 16 * kURec, &S.full_u[ab]);
+        bulk_g2s(surec + ab * kURec, Q.urec + (int64_t)lu * kURec, 16 * kURec, &S.full_u[ab]);
         const uint32_t abytes = (uint32_t)(kDig * U.nq * kAStep);
         mbar_expect_tx(&S.full_a[ab], abytes);
-        bulk_g2s(sA + ab * kABuf, P.a_img + U.a_img, abytes, &S.full_a[ab]);
+        bulk_g2s(sA + ab * kABuf, Q.a_img + U.a_img, abytes, &S.full_a[ab]);
         ++q;
         long long pb = U.pb;
-        PNTile Vn = P.ntiles[U.v0];  // descriptors loaded one N-tile ahead
+        PNTile Vn = Q.ntiles[U.v0];  // descriptors loaded one N-tile ahead
         for (int nt = 0; nt < U.nN; ++nt) {
           const PNTile V = Vn;
-          if (nt + 1 < U.nN) Vn = P.ntiles[U.v0 + nt + 1];
+          if (nt + 1 < U.nN) Vn = Q.ntiles[U.v0 + nt + 1];
           const int st = (int)(t % kStages), rs = (int)(t % kRecStages);
           if (t >= kStages &&
               !(ok = mbar_wait(&S.empty_b[st], (uint32_t)(((t / kStages) - 1) & 1), P.err)))
             break;
           const uint32_t bbytes = (uint32_t)(kDig * V.nq * kBStep);
           mbar_expect_tx(&S.full_b[st], bbytes);
-          bulk_g2s(sB + st * kBBuf, P.b_img + V.b_img, bbytes, &S.full_b[st]);
+          bulk_g2s(sB + st * kBBuf, Q.b_img + V.b_img, bbytes, &S.full_b[st]);
           if (t >= kRecStages &&
               !(ok = mbar_wait(&S.empty_r[rs], (uint32_t)(((t / kRecStages) - 1) & 1), P.err)))
             break;
           const int np = U.nab * V.nbb;
           int4 *rec = srec + rs * (kRecBytes / 16);
           mbar_expect_tx(&S.full_r[rs], (uint32_t)(16 * (kNTRec + np)));
-          bulk_g2s(rec, P.ntrec + (int64_t)(U.v0 + nt) * kNTRec, 16 * kNTRec, &S.full_r[rs]);
-          bulk_g2s(rec + kNTRec, P.pairs + pb, (uint32_t)(16 * np), &S.full_r[rs]);
+          bulk_g2s(rec, Q.ntrec + (int64_t)(U.v0 + nt) * kNTRec, 16 * kNTRec, &S.full_r[rs]);
+          bulk_g2s(rec + kNTRec, Q.pairs + pb, (uint32_t)(16 * np), &S.full_r[rs]);
           pb += np;
           ++t;
         }
@@ -826,7 +846,8 @@ __global__ void __launch_bounds__(576, 1) k_pan_mma(PanArgs P) {
     for (int64_t r = 0; ok; ++r) {
       const int64_t u = unit_at(r, G, cta);
       if (u >= P.nunits) break;
-      const PUnit U = P.units[u];
+      int lu;
+      const PUnit U = unit_plan(P, u, lu).units[lu];
       const int ab = (int)(q & 1);
       ok = __shfl_sync(0xffffffffu, lane != 0 || mbar_wait(&S.full_a[ab], (uint32_t)((q >> 1) & 1), P.err), 0);
       if (!ok) break;
@@ -873,7 +894,13 @@ __global__ void __launch_bounds__(576, 1) k_pan_mma(PanArgs P) {
     for (int64_t r = 0; ok; ++r) {
       const int64_t u = unit_at(r, G, cta);
       if (u >= P.nunits) break;
-      const int nN = P.units[u].nN, nab = P.units[u].nab;
+      int lu;
+      const PanPlan &Q = unit_plan(P, u, lu);
+      const int nN = Q.units[lu].nN, nab = Q.units[lu].nab;
+      double *const QC = Q.C;
+      long long *const Qslots = Q.slots;
+      const double Qalpha = Q.alpha;
+      const int Qalpha_one = Q.alpha_one;
       const int us = (int)(q & 1);
       if (!(ok = epi_bar_and(g, gt != 0 || mbar_wait(&S.full_u[us], (uint32_t)((q >> 1) & 1), P.err))))
         break;
@@ -945,8 +972,8 @@ __global__ void __launch_bounds__(576, 1) k_pan_mma(PanArgs P) {
             if (dst >= 0) {
               // the C block's only product: converted and written
               const int e2 = ar.z + bq.z - 54;
-              double *o = P.C + dst;
-              if (P.alpha_one) {
+              double *o = QC + dst;
+              if (Qalpha_one) {
                 for (int e = lane; e < mn; e += 128) {
                   const bool v1 = e + 32 < mn, v2 = e + 64 < mn, v3 = e + 96 < mn;
                   const long long x0 = at(e), x1 = v1 ? at(e + 32) : 0, x2 = v2 ? at(e + 64) : 0,
@@ -957,12 +984,12 @@ __global__ void __launch_bounds__(576, 1) k_pan_mma(PanArgs P) {
                   if (v3) o[e + 96] = i64_scaled(x3, e2);
                 }
               } else {
-                for (int e = lane; e < mn; e += 32) o[e] = P.alpha * i64_scaled(at(e), e2);
+                for (int e = lane; e < mn; e += 32) o[e] = Qalpha * i64_scaled(at(e), e2);
               }
             } else {
               // one of several products (or a block with C_in): its slot, at the C
               // block's common scale; the reduction kernel adds a block's slots
-              long long *sl = P.slots + (-(dst + 2));
+              long long *sl = Qslots + (-(dst + 2));
               const int sh = pe.z;
               for (int e = lane; e < mn; e += 128) {
                 const bool v1 = e + 32 < mn, v2 = e + 64 < mn, v3 = e + 96 < mn;
@@ -1364,7 +1391,41 @@ int panel_error(bst_plan *p) {
   return e;
 }
 
-void execute_emu_panel(bst_plan *p, const NumArgs &a, cudaStream_t s) {
+namespace {
+
+PanPlan pan_plan(const PanelState &PS, const NumArgs &a) {
+  PanPlan Q{};
+  Q.units = PS.units;
+  Q.ntiles = PS.ntiles;
+  Q.a_img = PS.a_img;
+  Q.b_img = PS.b_img;
+  Q.urec = PS.urec;
+  Q.ntrec = PS.ntrec;
+  Q.pairs = PS.pairs;
+  Q.C = a.C;
+  Q.slots = reinterpret_cast<long long *>(PS.slots);
+  Q.alpha = a.alpha;
+  Q.alpha_one = a.alpha == 1.0;
+  return Q;
+}
+
+void launch_pan_mma(const PanArgs &P, int num_sms, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    BST_CUDA(cudaFuncSetAttribute(k_pan_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmemBytes));
+    attr_set = true;
+  }
+  if (P.nunits == 0) return;
+  const int grid = (int)std::min<int64_t>(num_sms, P.nunits);
+  k_pan_mma<<<grid, 576, kSmemBytes, s>>>(P);
+  BST_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+// slicing of the current operand data, record exponents and slot shifts (launches only)
+void panel_prepare(bst_plan *p, const NumArgs &a, cudaStream_t s) {
   PanelState &PS = panel_state(p, s);
   const int wpb = 8;
   for (int side = 0; side < 2; ++side) {
@@ -1407,54 +1468,107 @@ void execute_emu_panel(bst_plan *p, const NumArgs &a, cudaStream_t s) {
     k_pan_shift<<<nblk(PS.nred, 256), 256, 0, s>>>(sh);
     BST_CHECK_LAUNCH();
   }
-  static bool attr_set = false;
-  if (!attr_set) {
-    BST_CUDA(cudaFuncSetAttribute(k_pan_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kSmemBytes));
-    attr_set = true;
-  }
-  PanArgs P{};
-  P.units = PS.units;
-  P.nunits = PS.nunits;
-  P.ntiles = PS.ntiles;
-  P.a_img = PS.a_img;
-  P.b_img = PS.b_img;
-  P.urec = PS.urec;
-  P.ntrec = PS.ntrec;
-  P.pairs = PS.pairs;
-  P.C = a.C;
-  P.slots = reinterpret_cast<long long *>(PS.slots);
-  P.alpha = a.alpha;
-  P.alpha_one = a.alpha == 1.0;
-  P.err = PS.err;
-  const int grid = (int)std::min<int64_t>(p->ctx->num_sms, PS.nunits);
-  k_pan_mma<<<grid, 576, kSmemBytes, s>>>(P);
-  BST_CHECK_LAUNCH();
-  if (PS.nred > 0) {
-    RedArgs R{};
-    R.nred = PS.nred;
-    R.red = PS.red;
-    R.desc = PS.red_desc;
-    R.crow = p->C->row;
-    R.ccol = p->C->col;
-    R.rsz = p->C->rsz;
-    R.csz = p->C->csz;
-    R.c_cin = p->c_cin;
-    R.cbeg = PS.cbeg;
-    R.slot_base = PS.slot_base;
-    R.c_off = p->C->off;
-    R.cin_off = p->Cin ? p->Cin->off : nullptr;
-    R.c_scale = PS.c_scale;
-    R.slots = reinterpret_cast<const long long *>(PS.slots);
-    R.Cin = a.Cin;
-    R.C = a.C;
-    R.alpha = a.alpha;
-    R.beta = a.beta;
-    R.alpha_one = a.alpha == 1.0;
-    R.has_beta = a.beta != 0.0 && a.Cin != nullptr;
-    k_pan_reduce<<<nblk(PS.nred, wpb), 32 * wpb, 0, s>>>(R);
-    BST_CHECK_LAUNCH();
-  }
 }
+
+// the C blocks summed from slots (launch only)
+void panel_finish(bst_plan *p, const NumArgs &a, cudaStream_t s) {
+  PanelState &PS = *p->panel;
+  if (PS.nred == 0) return;
+  RedArgs R{};
+  R.nred = PS.nred;
+  R.red = PS.red;
+  R.desc = PS.red_desc;
+  R.crow = p->C->row;
+  R.ccol = p->C->col;
+  R.rsz = p->C->rsz;
+  R.csz = p->C->csz;
+  R.c_cin = p->c_cin;
+  R.cbeg = PS.cbeg;
+  R.slot_base = PS.slot_base;
+  R.c_off = p->C->off;
+  R.cin_off = p->Cin ? p->Cin->off : nullptr;
+  R.c_scale = PS.c_scale;
+  R.slots = reinterpret_cast<const long long *>(PS.slots);
+  R.Cin = a.Cin;
+  R.C = a.C;
+  R.alpha = a.alpha;
+  R.beta = a.beta;
+  R.alpha_one = a.alpha == 1.0;
+  R.has_beta = a.beta != 0.0 && a.Cin != nullptr;
+  const int wpb = 8;
+  k_pan_reduce<<<nblk(PS.nred, wpb), 32 * wpb, 0, s>>>(R);
+  BST_CHECK_LAUNCH();
+}
+
+void execute_emu_panel(bst_plan *p, const NumArgs &a, cudaStream_t s) {
+  PanelState &PS = panel_state(p, s);
+  panel_prepare(p, a, s);
+  PanArgs P{};
+  P.one = pan_plan(PS, a);
+  P.plans = nullptr;
+  P.ulist = nullptr;
+  P.nunits = PS.nunits;
+  P.err = PS.err;
+  launch_pan_mma(P, p->ctx->num_sms, s);
+  panel_finish(p, a, s);
+}
+
+// ---- batches -------------------------------------------------------------------
+
+// whether a batch runs this plan's emulated products on the panel kernel (the schedule is
+// built now: batch executes must not synchronise)
+bool panel_batch_eligible(bst_plan *p, cudaStream_t s) {
+  const int mode = p->ctx->tune_emu_panel;
+  if (!mode || p->C->nblocks == 0) return false;
+  const PanelState &PS = panel_state(p, s);
+  return PS.eligible && (mode == 2 || PS.fill >= kMinFill);
+}
+
+size_t panel_plan_bytes() { return sizeof(PanPlan); }
+
+void panel_fill_plan(bst_plan *p, const NumArgs &a, void *out) {
+  const PanPlan Q = pan_plan(*p->panel, a);
+  std::memcpy(out, &Q, sizeof(Q));
+}
+
+// the (plan, unit) list of a batch: every unit of the given plans, by decreasing cost
+int64_t panel_batch_units(const std::vector<bst_plan *> &plans, Arena &ar, int2 **out,
+                          cudaStream_t s) {
+  std::vector<std::pair<double, int2>> all;
+  for (size_t q = 0; q < plans.size(); ++q) {
+    const PanelState &PS = *plans[q]->panel;
+    std::vector<PUnit> u((size_t)PS.nunits);
+    {
+      ReadBack rb(plans[q]->ctx, s);
+      rb.add(u.data(), PS.units, sizeof(PUnit) * u.size());
+      rb.done();
+    }
+    for (size_t x = 0; x < u.size(); ++x)
+      all.push_back({(double)u[x].nN * (2.0 + u[x].nq), make_int2((int)q, (int)x)});
+  }
+  std::stable_sort(all.begin(), all.end(),
+                   [](const std::pair<double, int2> &x, const std::pair<double, int2> &y) {
+                     return x.first > y.first;
+                   });
+  std::vector<int2> list(all.size());
+  for (size_t i = 0; i < all.size(); ++i) list[i] = all[i].second;
+  if (list.empty()) list.push_back(make_int2(0, 0));
+  Upload up(plans.empty() ? nullptr : plans[0]->ctx, s);
+  *out = up.add_vector(ar, list);
+  up.done();
+  return (int64_t)all.size();
+}
+
+void launch_panel_batch(const void *d_plans, const int2 *ulist, int64_t n, int *err, int num_sms,
+                        cudaStream_t s) {
+  PanArgs P{};
+  P.plans = static_cast<const PanPlan *>(d_plans);
+  P.ulist = ulist;
+  P.nunits = n;
+  P.err = err;
+  launch_pan_mma(P, num_sms, s);
+}
+
+int *panel_err_flag(bst_plan *p) { return p->panel ? p->panel->err : nullptr; }
 
 }  // namespace bst

@@ -176,3 +176,90 @@ def test_panel_empty_and_filtered_everything():
 def test_panel_not_taken_for_large_blocks():
     """n = 40 exceeds the kernel's 32-column tiles: the C-block kernel runs instead."""
     check(_mixed(38, sizes=(5, 13, 40), nb=(20, 20, 20)), expect_panel=False)
+
+
+def _lib_plans(probs):
+    mats, plans = [], []
+    for p in probs:
+        A, B = to_lib(p.A), to_lib(p.B)
+        Ci = to_lib(p.C_in) if p.C_in is not None else None
+        plan = bst.multiply_plan(A, B, Ci, p.eps, p.transa, p.transb)
+        plan.alloc_result()
+        mats.append((A, B, Ci))
+        plans.append(plan)
+    return mats, plans
+
+
+def _plan_data(plan):
+    n = plan.result.info[3]
+    return plan.result.data[:n].cpu().numpy().copy()
+
+
+def test_panel_batch_mixed_plans_against_oracle_and_single():
+    """A batch whose plans are partly on the panel kernel (one launch over all their
+    units) and partly not (blocks of 40 > 32): every plan within 1e-11 of the oracle
+    per C block, bitwise equal to the same plan executed alone (each unit's digit
+    products and slot sums do not depend on which other units share the launch)."""
+    import torch
+    probs = batched(nprob=5, nmin=300, nmax=900, occ_min=0.02, occ_max=0.06, seed=41)
+    probs.append(_mixed(42, sizes=(5, 13, 40), nb=(20, 20, 20), cin=True, beta=0.5))
+    probs.append(_mixed(43, ta="T", tb="T", cin=True, alpha=-0.5, beta=2.0))
+    with panel_mode(2):
+        mats, plans = _lib_plans(probs)
+        alphas = np.array([p.alpha for p in probs])
+        betas = np.array([p.beta for p in probs])
+        batch = bst.bst_batch_create(bst.context(), [pl.handle for pl in plans])
+        on_panel = [bst.bst_plan_emu_costs(pl.handle)["panel"] for pl in plans]
+        assert on_panel[-2] is False and sum(on_panel) == len(plans) - 1
+        for pl in plans:
+            pl.result.data.fill_(float("nan"))
+        bst.bst_batch_execute(batch, alphas, betas, bst.BST_FP64_EMU_BF16)
+        torch.cuda.synchronize()
+        for pl in plans:
+            assert pl.stats()["n_stack"] >= 0  # raises on a device-side timeout
+        got = [_plan_data(pl) for pl in plans]
+        for q, pl in enumerate(plans):
+            pl.execute(alphas[q], betas[q], bst.BST_FP64_EMU_BF16, 1)
+        torch.cuda.synchronize()
+        single = [_plan_data(pl) for pl in plans]
+        bst.bst_batch_destroy(batch)
+    for q, p in enumerate(probs):
+        assert (got[q] == single[q]).all(), q
+        ref = oracle.multiply(p.A, p.B, p.C_in, p.alpha, p.beta, p.eps, p.transa, p.transb)
+        assert rel_fro(got[q], ref["data"]) <= TOL
+        if p.transa == "N" and p.transb == "N":
+            g = dict(data=got[q])
+            assert per_block_max_err(g, ref, p.A.row_sizes, p.B.col_sizes) <= TOL, q
+
+
+def test_panel_batch_graph_replay_with_new_values():
+    """The batch's panel launch captured into a CUDA graph: a replay after the operands
+    changed in place reads the current data (slicing, launch and reduction are all
+    graph nodes)."""
+    import torch
+    probs = batched(nprob=4, nmin=300, nmax=700, occ_min=0.03, occ_max=0.06, seed=44)
+    with panel_mode(2):
+        mats, plans = _lib_plans(probs)
+        ones, zeros = np.ones(len(plans)), np.zeros(len(plans))
+        batch = bst.bst_batch_create(bst.context(), [pl.handle for pl in plans])
+        assert all(bst.bst_plan_emu_costs(pl.handle)["panel"] for pl in plans)
+        bst.bst_batch_execute(batch, ones, zeros, bst.BST_FP64_EMU_BF16)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream()
+        with torch.cuda.graph(g, stream=cs):
+            bst.bst_batch_execute(batch, ones, zeros, bst.BST_FP64_EMU_BF16, stream=cs)
+        for (A, B, _), p in zip(mats, probs):
+            A.data.mul_(-2.0)  # scales every block norm alike: the filter keeps its choices
+            p.A.data *= -2.0
+            B.data.mul_(0.25)
+            p.B.data *= 0.25
+        for pl in plans:
+            pl.result.data.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        got = [_plan_data(pl) for pl in plans]
+        bst.bst_batch_destroy(batch)
+    for q, p in enumerate(probs):
+        ref = oracle.multiply(p.A, p.B, None, 1.0, 0.0, p.eps * 0.5)
+        assert rel_fro(got[q], ref["data"]) <= TOL
