@@ -693,12 +693,14 @@ def other_configs(local_rank, stream):
     refs = {q: oracle.multiply(probs[q].A, probs[q].B, None, 1.0, 0.0, probs[q].eps)["data"]
             for q in small}
     ctx = bst.context(local_rank)
-    old_rs = bst.bst_tune_get(ctx, bst.BST_TUNE_EMU_ROW_SCALE)
+    old_pan = bst.bst_tune_get(ctx, bst.BST_TUNE_EMU_PANEL)
     bt = {}
-    for name, prec, rs in (("fp64", bst.BST_FP64, old_rs),
-                           ("emu_bf16", bst.BST_FP64_EMU_BF16, 1),
-                           ("emu_bf16_block_scaled", bst.BST_FP64_EMU_BF16, 0)):
-        bst.bst_tune_set(ctx, bst.BST_TUNE_EMU_ROW_SCALE, rs)
+    # emulated rows: the default (every plan on the tcgen05 panel kernel) and the
+    # C-block kernel with row-scaled digits
+    for name, prec, pan in (("fp64", bst.BST_FP64, old_pan),
+                            ("emu_bf16", bst.BST_FP64_EMU_BF16, old_pan),
+                            ("emu_bf16_c_block_kernel", bst.BST_FP64_EMU_BF16, 0)):
+        bst.bst_tune_set(ctx, bst.BST_TUNE_EMU_PANEL, pan)
         batch = bst.bst_batch_create(ctx, [pl.handle for pl in plans])
         bst.bst_batch_execute(batch, ones, zeros, prec)
         torch.cuda.synchronize()
@@ -712,13 +714,17 @@ def other_configs(local_rank, stream):
         blk = max(_sample_err_matrix(probs[q], plans[q], probs[q].A.row_sizes,
                                      probs[q].B.col_sizes, nsample=8, seed=q)
                   for q in (0, 7, 31, 63))
-        bt[name] = dict(rate(f, ms) if prec == bst.BST_FP64 else rate_emu(f, ms, plans),
-                        rel_err_vs_oracle=full,
-                        max_rel_err_of_sampled_blocks=blk,
-                        launch="one persistent kernel per replay (CUDA graph)")
+        row = dict(rate(f, ms) if prec == bst.BST_FP64 else rate_emu(f, ms, plans),
+                   rel_err_vs_oracle=full,
+                   max_rel_err_of_sampled_blocks=blk,
+                   launch="one persistent kernel per replay (CUDA graph)")
+        if prec != bst.BST_FP64:
+            row["plans_on_panel_kernel"] = int(sum(
+                bst.bst_plan_emu_costs(pl.handle)["panel"] for pl in plans)) if pan else 0
+        bt[name] = row
         del g
         bst.bst_batch_destroy(batch)
-    bst.bst_tune_set(ctx, bst.BST_TUNE_EMU_ROW_SCALE, old_rs)
+    bst.bst_tune_set(ctx, bst.BST_TUNE_EMU_PANEL, old_pan)
     out["batched_64"] = dict(bt, flop=f,
                              error_note="rel_err_vs_oracle: relative Frobenius error over all "
                                         "of C, worst of the 4 smallest problems; sampled "

@@ -304,18 +304,17 @@ bst_status bst_plan_destroy(bst_plan *plan);
  *     both on a given contraction.
  *   BST_TUNE_EMU_PANEL (m, n ignored): 1 = emulated-FP64 executes of a plan whose
  *     blocks fit the panel kernel (op(A) row blocks <= 128, op(B) column blocks <= 32,
- *     inner blocks <= 32 elements) and whose inner-block panels fill at least 15 % of
- *     its 128 x 32 tiles' multiply-adds run the tcgen05 panel kernel: per inner block k,
+ *     inner blocks <= 32 elements) run the tcgen05 panel kernel: per inner block k,
  *     the op(A) blocks of column k times the op(B) blocks of row k as one dense product
  *     on the tensor cores, digits scaled per stored block -- from the plan's second
  *     emulated execute on (the first runs the C-block kernel, so a plan executed once
  *     does not pay for building the panel schedule) (default); 2 = the panel kernel
  *     whenever the blocks fit, from the first execute; 0 = always the C-block kernel
  *     (BST_TUNE_EMU_ROW_SCALE and BST_TUNE_EMU_SWAP apply to it).  A batch decides
- *     when it is created: with 1 or 2 every matrix plan the panel kernel takes (as
- *     above, at 1 only with the 15 % fill) runs in one panel launch over all those
- *     plans, its schedule built by bst_batch_create; the others run the C-block
- *     kernel.
+ *     when it is created: with 1 or 2 every matrix plan whose blocks fit runs in one
+ *     panel launch over all those plans, its schedule built by bst_batch_create; the
+ *     others run the C-block kernel.  A plan whose schedule exists (built by an
+ *     execute or a batch) keeps the panel kernel at 1 and 2.
  * Changing a choice takes effect at the next execute of a plan; a batch built before
  * the change refuses emulated-FP64 execution (BST_ERR_STATE) and must be created again.
  * A plan or batch whose native-FP64 tiles must be split again after a change returns

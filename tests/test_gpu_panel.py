@@ -263,3 +263,39 @@ def test_panel_batch_graph_replay_with_new_values():
     for q, p in enumerate(probs):
         ref = oracle.multiply(p.A, p.B, None, 1.0, 0.0, p.eps * 0.5)
         assert rel_fro(got[q], ref["data"]) <= TOL
+
+
+def test_default_mode_batch_and_second_execute_per_block_accuracy():
+    """The default choice (BST_TUNE_EMU_PANEL = 1) on the batched generator: a batch puts
+    every plan on the panel kernel and holds 1e-11 on every C block; a plan executed on
+    its own runs the C-block kernel first and the panel kernel from its second execute
+    on, which then holds the same per-block bound."""
+    import torch
+    probs = batched(nprob=6, nmin=200, nmax=800, occ_min=0.01, occ_max=0.06, seed=45)
+    with panel_mode(1):
+        mats, plans = _lib_plans(probs)
+        batch = bst.bst_batch_create(bst.context(), [pl.handle for pl in plans])
+        assert all(bst.bst_plan_emu_costs(pl.handle)["panel"] for pl in plans)
+        ones, zeros = np.ones(len(plans)), np.zeros(len(plans))
+        bst.bst_batch_execute(batch, ones, zeros, bst.BST_FP64_EMU_BF16)
+        torch.cuda.synchronize()
+        got = [_plan_data(pl) for pl in plans]
+        bst.bst_batch_destroy(batch)
+        p = probs[-1]
+        A, B = to_lib(p.A), to_lib(p.B)
+        plan = bst.multiply_plan(A, B, None, p.eps)
+        plan.alloc_result()
+        # the costs describe the next execute: here the first one
+        first_on_panel = bst.bst_plan_emu_costs(plan.handle)["panel"]
+        plan.execute(1.0, 0.0, bst.BST_FP64_EMU_BF16, 1)
+        torch.cuda.synchronize()
+        assert bst.bst_plan_emu_costs(plan.handle)["panel"]
+        plan.execute(1.0, 0.0, bst.BST_FP64_EMU_BF16, 1)
+        torch.cuda.synchronize()
+        second = _plan_data(plan)
+        assert bst.bst_plan_emu_costs(plan.handle)["panel"]
+    assert not first_on_panel
+    for q, p in enumerate(probs):
+        ref = oracle.multiply(p.A, p.B, None, 1.0, 0.0, p.eps)
+        assert per_block_max_err(dict(data=got[q]), ref, p.A.row_sizes, p.B.col_sizes) <= TOL
+    assert (second == got[-1]).all()
