@@ -389,6 +389,26 @@ bst_status bst_batch_execute(bst_batch *batch, const double *alpha, const double
                              int32_t precision, void *stream);
 bst_status bst_batch_destroy(bst_batch *batch);
 
+/* ---------------------------------------------------------------------------
+ * K-split reduction (paper Sec. 3.1, the case S_C << S_A, S_B: the inner dimension K is
+ * divided among P processes, process i computes the partial product C~_i = op(A_i)
+ * op(B_i) over its share of K, and C is the sum of the C~_i).
+ *
+ * bst_sum_parts adds up parts of C: for every output block u < nblocks, whose elements
+ * are dst[dst_off[u] .. dst_off[u+1]-1], and every part i < nparts in increasing i, the
+ * same number of elements of src starting at src_off[i * nblocks + u] (-1: part i has
+ * no block u).  dst = ((first part present + next) + ...) in that fixed order, so the
+ * bits do not depend on the launch; a block no part has is written as 0.
+ * dst_off: device int64[nblocks + 1] (increasing), src_off: device int64[nparts *
+ * nblocks], src and dst: device FP64, not overlapping, all owned by the caller.  Only
+ * queues one kernel on `stream` (no allocation, no synchronisation).  The exchange
+ * that brings each process its parts (an all-to-all over the processes, e.g. NCCL) and
+ * the layout tables are the caller's; the package's ksplit module builds both.
+ * Errors: INVALID_ARG for a NULL pointer (when nblocks > 0), nparts < 1 or nblocks < 0.
+ * ------------------------------------------------------------------------- */
+bst_status bst_sum_parts(bst_ctx *ctx, int32_t nparts, int64_t nblocks, const int64_t *dst_off,
+                         const int64_t *src_off, const double *src, double *dst, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,7 @@ _SIGS = {
     "bst_batch_create": ([_VP, C.c_int32, _VP, C.POINTER(_VP)], C.c_int32),
     "bst_batch_execute": ([_VP, _VP, _VP, C.c_int32, _VP], C.c_int32),
     "bst_batch_destroy": ([_VP], C.c_int32),
+    "bst_sum_parts": ([_VP, C.c_int32, C.c_int64, _VP, _VP, _VP, _VP, _VP], C.c_int32),
 }
 
 
@@ -389,6 +390,13 @@ def bst_batch_execute(batch, alpha, beta, precision=BST_FP64, stream=None):
 
 def bst_batch_destroy(batch):
     _check(load().bst_batch_destroy(batch), "bst_batch_destroy")
+
+
+def bst_sum_parts(ctx, nparts, nblocks, dst_off, src_off, src, dst, stream=None):
+    """dst_off (int64, nblocks + 1), src_off (int64, nparts * nblocks), src, dst: device
+    tensors (FP64 for src and dst)."""
+    _check(load().bst_sum_parts(ctx, int(nparts), int(nblocks), _ptr(dst_off), _ptr(src_off),
+                                _ptr(src), _ptr(dst), _stream(stream)), "bst_sum_parts")
 
 
 # ---- convenience wrappers -----------------------------------------------------------
