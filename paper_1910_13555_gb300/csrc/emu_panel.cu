@@ -35,21 +35,26 @@
 // depend on scheduling; each C block keeps its own scale, so a block many decades below
 // the other blocks of its rows keeps full relative accuracy.
 //
-// The MMA kernel is persistent, one CTA per SM, warp-specialised: warp 4 loads each
-// unit's A tile image and each N-tile's B image with cp.async.bulk (completion on
-// mbarriers), warp 5 allocates 512 TMEM columns and one of its threads issues the
-// tcgen05.mma instructions into two accumulator buffers (6 levels x 32 columns each),
-// warps 0-3 (TMEM lanes 0-127) read the levels back with tcgen05.ld, fold them, stage
-// the tile's results in shared memory and write whole C-block rows with coalesced
-// stores.  Every wait is bounded: a wait that runs out (2 s) records an error flag,
-// and the kernel's roles stop, drain their copies and MMAs, free TMEM and return.
+// The MMA kernel is persistent, one CTA of 18 warps per SM, warp-specialised: warp 16
+// loads each unit's A tile image, each N-tile's B image and the epilogue's records with
+// cp.async.bulk (completion on mbarriers); warp 17 allocates 512 TMEM columns and one
+// elected lane of it issues the tcgen05.mma instructions into two accumulator buffers
+// (6 levels x 32 columns each); warps 0-15 are two epilogue groups of 8 warps, group g
+// draining buffer g: they read the levels back with tcgen05.ld (thread t of a group:
+// TMEM lane t mod 128, half of the columns), fold them, stage the tile in shared memory
+// and write whole C-block rows with coalesced stores.  Units, in decreasing cost, are
+// dealt to the CTAs in serpentine order (odd rounds backwards); one grid serves the
+// units of one plan or of a whole batch of plans (per-plan pointers in a table).
+// Every wait is bounded: a wait that runs out (2 s) records an error flag, and the
+// kernel's roles stop, drain their copies and MMAs, free TMEM and return.
 //
 // Operand images.  The digits are written once per execute directly in the layout the
 // tensor core reads from shared memory (K-major; each row's inner values contiguous, 32
 // or 64 bytes for nq = 1 or 2 K-steps of 16, in 8-row atoms with the 32- or 64-byte
 // swizzle), per unit (panel k, 128-row tile) slice by slice, so a unit's A operand is
-// one contiguous bulk copy of 6 * nq * 4 KB and an N-tile's B operand 6 * nq * 1 KB.  Tiles are cut at block boundaries (at most 32 blocks per
-// A tile, 8 per N-tile), so each (A block, B block) pair of a tile is one whole product.
+// one contiguous bulk copy of 6 * nq * 4 KB and an N-tile's B operand 6 * nq * 1 KB.
+// Tiles are cut at block boundaries (at most 32 blocks per A tile, 8 per N-tile, packed
+// first-fit decreasing), so each (A block, B block) pair of a tile is one whole product.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -82,9 +87,6 @@ constexpr int kNoExp = -4000;                      // exponent of an all-zero bl
 constexpr int kAccCols = 256;                      // TMEM columns per accumulator buffer
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every wait
 constexpr int kErrWait = 1;                        // error code: a wait ran out
-// useful share of the tiles' multiply-adds (inner padding and empty tile rows and
-// columns excluded) from which the panel kernel is chosen by default: below it the
-// panels are thin (tall-skinny products) and the C-block kernel suits them better
 
 // unit = (panel k, 128-row tile); sorted by decreasing cost on the host
 struct PUnit {
