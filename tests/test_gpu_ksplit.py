@@ -161,4 +161,5 @@ def test_multiply_ksplit_one_process_group(backend):
     pr = subprocess.run([sys.executable, "-c", _WORKER.format(root=ROOT)], env=env, cwd=ROOT,
                         capture_output=True, text=True, timeout=300)
     assert pr.returncode == 0, pr.stderr[-3000:]
-    assert pr.stdout.strip().splitlines()[-1].startswith("ok")
+    # the communication libraries print their own lines too
+    assert any(line.startswith("ok ") for line in pr.stdout.splitlines()), pr.stdout
