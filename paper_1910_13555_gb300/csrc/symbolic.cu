@@ -53,21 +53,24 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // ---- block norms -------------------------------------------------------------------
 
-// One warp per group of kNormGroup consecutive blocks.  Lane j first loads the size
-// and offset of block j of the group (one coalesced round of index loads instead of a
-// dependent chain per block); then each block's sum of squares is summed across the
-// warp (lane-strided FMAs, then the butterfly) and parked in lane j, and the group's
-// square roots run as one sequence.  GB300's FP64 pipe takes as long for a warp
-// instruction with one active lane as with 32, and a square root is about a dozen of
-// them.
-constexpr int kNormGroup = 8;
+// One warp per group of 32 consecutive blocks.  Lane j first loads the size and offset
+// of block j of the group (one coalesced round of index loads).  For each block the
+// lanes accumulate lane-strided squares and park their 32 partial sums in a row of
+// shared memory; then lane j adds row j (the partials of block j) in lane order and
+// takes its square root.  GB300's FP64 pipe takes as long for a warp instruction with
+// one active lane as with 32: a butterfly costs five full FP64 instructions per block,
+// the transposed sum one per block, and the group's 32 square roots run together.
+constexpr int kNormGroup = 32;
+constexpr int kNormWarps = 4;
 
-__global__ void k_block_norms(int64_t nblocks, const int32_t *__restrict__ row,
-                              const int32_t *__restrict__ col, const int32_t *__restrict__ rsz,
-                              const int32_t *__restrict__ csz, const int64_t *__restrict__ off,
-                              const double *__restrict__ data, double *__restrict__ norms) {
-  const int lane = threadIdx.x & 31;
-  const int64_t b0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kNormGroup;
+__global__ void __launch_bounds__(32 * kNormWarps)
+    k_block_norms(int64_t nblocks, const int32_t *__restrict__ row,
+                  const int32_t *__restrict__ col, const int32_t *__restrict__ rsz,
+                  const int32_t *__restrict__ csz, const int64_t *__restrict__ off,
+                  const double *__restrict__ data, double *__restrict__ norms) {
+  __shared__ double part[kNormWarps][kNormGroup][33];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int64_t b0 = ((int64_t)blockIdx.x * kNormWarps + wl) * kNormGroup;
   if (b0 >= nblocks) return;
   const int nb = (int)min((int64_t)kNormGroup, nblocks - b0);
   int my_len = 0;
@@ -76,19 +79,23 @@ __global__ void k_block_norms(int64_t nblocks, const int32_t *__restrict__ row,
     my_len = rsz[row[b0 + lane]] * csz[col[b0 + lane]];
     my_off = off[b0 + lane];
   }
-  double mine = 0.0;
+  double(*P)[33] = part[wl];
   for (int j = 0; j < nb; ++j) {
     const int len = __shfl_sync(0xffffffffu, my_len, j);
     const double *x = data + __shfl_sync(0xffffffffu, my_off, j);
     double s = 0.0;
     for (int e = lane; e < len; e += 32) {
-      double v = __ldg(x + e);
+      const double v = __ldg(x + e);
       s = fma(v, v, s);
     }
-    s = warp_sum_d(s);
-    if (lane == j) mine = s;
+    P[j][lane] = s;
   }
-  if (lane < nb) norms[b0 + lane] = sqrt(mine);
+  __syncwarp();
+  if (lane < nb) {
+    double t = P[lane][0];
+    for (int q = 1; q < 32; ++q) t += P[lane][q];
+    norms[b0 + lane] = sqrt(t);
+  }
 }
 
 // ---- operand views -----------------------------------------------------------------
@@ -372,10 +379,9 @@ __global__ void k_ref_elems(int64_t nblocks, const int32_t *__restrict__ flag,
 void block_norms(const bst_matrix *m, double *norms, cudaStream_t s) {
   if (m->nblocks == 0) return;
   BST_REQUIRE(m->data != nullptr, BST_ERR_STATE, "matrix data not bound");
-  const int wpb = 8;
   const int64_t groups = (m->nblocks + kNormGroup - 1) / kNormGroup;
-  k_block_norms<<<nblk(groups, wpb), 32 * wpb, 0, s>>>(m->nblocks, m->row, m->col, m->rsz,
-                                                       m->csz, m->off, m->data, norms);
+  k_block_norms<<<nblk(groups, kNormWarps), 32 * kNormWarps, 0, s>>>(
+      m->nblocks, m->row, m->col, m->rsz, m->csz, m->off, m->data, norms);
   BST_CHECK_LAUNCH();
 }
 
