@@ -120,3 +120,30 @@ def test_multiply_adjoint_equals_plan_adjoint_without_cin():
     bst.bst_multiply_adjoint(plan.handle, g, dA2, dB2, p.alpha)
     torch.cuda.synchronize()
     assert torch.equal(dA1, dA2) and torch.equal(dB1, dB2)
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
+def test_adjoint_tall_b_blocks(ta, tb):
+    """op(B) blocks of 70 and 130 rows take the stripe kernel for dop(B) (those with at
+    most 32 columns; the 40-column ones and the 20-row ones stay on the general kernel):
+    every layout against the oracle's adjoint, and repeat runs bitwise equal."""
+    rng = np.random.default_rng(7)
+    m = rng.choice(np.array([5, 13], np.int32), 12).astype(np.int32)
+    k = rng.choice(np.array([20, 70, 130], np.int32), 10).astype(np.int32)
+    n = rng.choice(np.array([5, 13, 40], np.int32), 9).astype(np.int32)
+    A = random_matrix(rng, m, k, 0.4)
+    B = random_matrix(rng, k, n, 0.4)
+    Ci = random_matrix(rng, m, n, 0.3)
+    if ta == "T":
+        A = transpose_matrix(A)
+    if tb == "T":
+        B = transpose_matrix(B)
+    p = Problem(A, B, Ci, 0.75, 2.0, 0.0, ta, tb)
+    ref = oracle.multiply(p.A, p.B, p.C_in, p.alpha, p.beta, p.eps, ta, tb)
+    G = rng.standard_normal(len(ref["data"]))
+    rA, rB, rC = oracle.multiply_adjoint(p.A, p.B, p.C_in, p.alpha, p.beta, p.eps, G, ta, tb)
+    dA, dB, dC, _ = gpu_adjoint(p, G)
+    assert rel_fro(dA, rA) <= 1e-12 and rel_fro(dB, rB) <= 1e-12
+    assert (dC == rC).all()
+    dA2, dB2, _, _ = gpu_adjoint(p, G)
+    assert (dB2 == dB).all() and (dA2 == dA).all()
