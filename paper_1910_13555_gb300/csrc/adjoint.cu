@@ -44,8 +44,6 @@ struct AdjArgs {
   // several warps
   int64_t nblocks;
   int32_t nch, span;
-  int32_t tall_k;   // dop(B) blocks with k >= tall_k and n <= 32 go to k_adj_b_tall (0: none)
-  int32_t nstripe;  // k_adj_b_tall: 32-row stripes per block (of the tallest block)
   const int32_t *row, *col, *rsz, *csz;
   const int64_t *off;
 };
@@ -111,7 +109,6 @@ __global__ void k_adj_b(AdjArgs P) {
   if (b >= P.nblocks) return;
   const int R = P.rsz[P.row[b]], Cc = P.csz[P.col[b]];
   const int k = P.tb ? Cc : R, n = P.tb ? R : Cc;
-  if (P.tall_k && k >= P.tall_k && n <= 32) return;  // k_adj_b_tall's block
   const int64_t ob = (w - b * P.nch) * (int64_t)P.span;
   if (ob >= k * n) return;
   const int o1 = (int)min((int64_t)k * n, ob + P.span);
@@ -150,58 +147,6 @@ __global__ void k_adj_b(AdjArgs P) {
   }
 }
 
-// dop(B) for a tall stored B block (k >= tall_k rows of op(B), n <= 32 columns), e.g.
-// the 390 x 13 blocks of U in the rank-4 contraction: one warp per 32-row stripe, lane
-// l owns row l of the stripe and every column q (16 accumulators per round).  Per inner
-// index p a lane loads one op(A) element (the lanes' loads of a row are consecutive) and
-// the stripe's dC row p, the same for all lanes, and issues up to 16 FMAs; in k_adj_b's
-// numbering the lanes of a pass would walk a 169-row panel of a 0.5 MB op(A) block
-// through L1 once per 256 outputs.  Every output sums its entries, then p, in the same
-// order as k_adj_b, so both kernels give the same bits.
-__global__ void k_adj_b_tall(AdjArgs P) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int64_t b = w / P.nstripe;
-  if (b >= P.nblocks) return;
-  const int R = P.rsz[P.row[b]], Cc = P.csz[P.col[b]];
-  const int k = P.tb ? Cc : R, n = P.tb ? R : Cc;
-  const int l0 = (int)(w - b * P.nstripe) * 32;
-  if (k < P.tall_k || n > 32 || l0 >= k) return;
-  const int l = l0 + lane;
-  const bool mine = l < k;
-  const int e0 = P.ptr[b], e1 = P.ptr[b + 1];
-  double *out = P.dB + P.off[b];
-  for (int q0 = 0; q0 < n; q0 += 16) {
-    double acc[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) acc[j] = 0.0;
-    for (int x = e0; x < e1; ++x) {
-      const int e = P.grp[x];
-      const int c = P.s_cb[e];
-      const int m = P.c_rsz[P.c_row[c]];
-      const double *g = P.dC + P.s_c[e] + q0;  // m x n, from column q0
-      const double *aa = P.A + P.s_a[e];       // op(A): m x k
-      const int a_sp = P.ta ? 1 : k, a_sl = P.ta ? m : 1;
-      const double *ap = aa + (mine ? l : 0) * a_sl;
-#pragma unroll 2
-      for (int p = 0; p < m; ++p) {
-        const double a = mine ? __ldg(ap + p * a_sp) : 0.0;
-        const double *gr = g + p * n;
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (q0 + j < n) acc[j] = fma(a, __ldg(gr + j), acc[j]);
-      }
-    }
-    if (mine) {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int q = q0 + j;
-        if (q < n) out[P.tb ? q * k + l : l * n + q] = P.alpha * acc[j];
-      }
-    }
-  }
-}
-
 // dC_in = beta dC on the C_in blocks (one warp per C block that carries a C_in block)
 __global__ void k_adj_cin(int64_t nc, const int32_t *c_cin, const int64_t *c_off,
                           const int64_t *cin_off, const int32_t *c_row, const int32_t *c_col,
@@ -220,8 +165,6 @@ __global__ void k_adj_cin(int64_t nc, const int32_t *c_cin, const int64_t *c_off
 // the largest stored block of the output side needs; a warp whose chunk lies past its
 // block's end returns at once.  Without host block sizes: one chunk per block.
 constexpr int kAdjChunkPasses = 4;
-// op(B) blocks with at least this many rows (and at most 32 columns) take k_adj_b_tall
-constexpr int kTallK = 64;
 
 void chunking(AdjArgs &P, const bst_matrix &M) {
   int32_t r = 0, c = 0;
@@ -308,17 +251,8 @@ void adjoint_fp64(bst_plan *p, const double *A, const double *B, const double *d
     P.csz = Bm->csz;
     P.off = Bm->off;
     chunking(P, *Bm);
-    // tall op(B) blocks (at least kTallK rows) to the stripe kernel
-    int32_t kmax = 0;
-    for (int32_t v : (p->tb ? Bm->h_csz : Bm->h_rsz)) kmax = std::max(kmax, v);
-    P.tall_k = kmax >= kTallK ? kTallK : 0;
-    P.nstripe = (kmax + 31) / 32;
     k_adj_b<<<nblk(Bm->nblocks * P.nch, wpb), 32 * wpb, 0, s>>>(P);
     BST_CHECK_LAUNCH();
-    if (P.tall_k) {
-      k_adj_b_tall<<<nblk(Bm->nblocks * P.nstripe, wpb), 32 * wpb, 0, s>>>(P);
-      BST_CHECK_LAUNCH();
-    }
   }
 }
 

@@ -124,9 +124,9 @@ def test_multiply_adjoint_equals_plan_adjoint_without_cin():
 
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
 def test_adjoint_tall_b_blocks(ta, tb):
-    """op(B) blocks of 70 and 130 rows take the stripe kernel for dop(B) (those with at
-    most 32 columns; the 40-column ones and the 20-row ones stay on the general kernel):
-    every layout against the oracle's adjoint, and repeat runs bitwise equal."""
+    """op(B) blocks of 20, 70 and 130 rows with 5 to 40 columns (outputs spread over
+    several warps): every layout against the oracle's adjoint, repeat runs bitwise
+    equal."""
     rng = np.random.default_rng(7)
     m = rng.choice(np.array([5, 13], np.int32), 12).astype(np.int32)
     k = rng.choice(np.array([20, 70, 130], np.int32), 10).astype(np.int32)
