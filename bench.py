@@ -618,6 +618,90 @@ def _sample_err_matrix(p, plan, row_sizes, col_sizes, nsample=32, seed=0):
     return _rel(_gather(plan.result.data, offs[sel], lens), ref)
 
 
+def ksplit_simulated(p, nproc, whole, local_rank, stream):
+    """The K-split product of a tall-skinny workload with `nproc` processes run one after
+    another on one GPU: median times of all partial multiplies and of all owner sums
+    (CUDA events, 20 after 3 warm-ups), the owner-sum kernel's HBM roofline (bytes read
+    and written by bst_sum_parts over its time) and the error against the undivided
+    product `whole` (device data in its C layout)."""
+    import numpy as np
+    import torch
+
+    from paper_1910_13555_gb300 import bst, ksplit
+    A, B = p.A, p.B
+    ka = ksplit.k_index(A.rows, A.cols, p.transa, "A")
+    kb = ksplit.k_index(B.rows, B.cols, p.transb, "B")
+    ea = A.row_sizes[A.rows].astype(np.int64) * A.col_sizes[A.cols]
+    eb = B.row_sizes[B.rows].astype(np.int64) * B.col_sizes[B.cols]
+    r = ksplit.k_ranges(ka, ea, kb, eb, A.row_sizes if p.transa == "T" else A.col_sizes, nproc)
+    plans, mats, pats = [], [], []
+    for i in range(nproc):
+        ra, ca, da = ksplit.select_k_range(A.row_sizes, A.col_sizes, A.rows, A.cols, A.data,
+                                           p.transa, "A", r[i], r[i + 1])
+        rb, cb, db = ksplit.select_k_range(B.row_sizes, B.col_sizes, B.rows, B.cols, B.data,
+                                           p.transb, "B", r[i], r[i + 1])
+        Ai = bst.Matrix.from_host(A.row_sizes, A.col_sizes, ra, ca, da, device=local_rank)
+        Bi = bst.Matrix.from_host(B.row_sizes, B.col_sizes, rb, cb, db, device=local_rank)
+        pl = bst.multiply_plan(Ai, Bi, None, p.eps, p.transa, p.transb, device=local_rank)
+        pl.alloc_result(local_rank)
+        plans.append(pl)
+        mats.append((Ai, Bi))
+    f = sum(pl.stats()["flops"] for pl in plans)
+
+    def partials():
+        for pl in plans:
+            pl.execute(1.0, 0.0, bst.BST_FP64, 1)
+    ms_part = _median_ms(partials, stream)
+    parts = []
+    for pl in plans:
+        rows, cols, _ = pl.result.index()
+        pats.append((rows, cols))
+        parts.append(pl.result.data[:pl.result.info[3]])
+    rs = A.col_sizes if p.transa == "T" else A.row_sizes
+    cs = B.row_sizes if p.transb == "T" else B.col_sizes
+    lay = ksplit.exchange_layout(pats, rs, cs)
+    dev = torch.device("cuda", local_rank)
+    bufs, tabs, outs, nbytes = [], [], [], 0
+    for q in range(nproc):
+        chunks = [parts[i][int(lay.send[i, :q].sum()):int(lay.send[i, :q + 1].sum())]
+                  for i in range(nproc)]
+        bufs.append(torch.cat(chunks))
+        _, _, offs = lay.owned(q)
+        tabs.append((torch.as_tensor(np.ascontiguousarray(offs, np.int64)).to(dev),
+                     torch.as_tensor(np.ascontiguousarray(lay.src_off[q], np.int64)).to(dev)))
+        outs.append(torch.empty(int(offs[-1]), dtype=torch.float64, device=dev))
+        nbytes += 8 * (bufs[-1].numel() + int(offs[-1]))
+
+    def sums():
+        for q in range(nproc):
+            n = len(tabs[q][0]) - 1
+            if n:
+                bst.bst_sum_parts(bst.context(local_rank), nproc, n, tabs[q][0], tabs[q][1],
+                                  bufs[q], outs[q])
+    # the owners' sums replayed from a CUDA graph: one launch each, back to back on the
+    # device, so the time is the kernels' and not the host's launch overhead
+    sums()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=cs):
+        sums()
+    ms_sum = _median_ms(g.replay, stream)
+    got = torch.cat(outs)
+    err = float(torch.linalg.norm(got - whole) / torch.linalg.norm(whole))
+    achieved = nbytes / (ms_sum * 1e-3) / 1e9
+    return {"processes": nproc, "k_ranges": [int(x) for x in r], "flop": f,
+            "partials_ms": ms_part, "partials_gflops": f / (ms_part * 1e-3) / 1e9,
+            "sum_ms": ms_sum, "sum_bytes": nbytes,
+            "sum_roofline": {"bound": "hbm", "kernel": "k_sum_parts", "achieved": achieved,
+                             "peak": MEASURED_HBM_GBS, "unit": "GB/s",
+                             "frac": achieved / MEASURED_HBM_GBS if MEASURED_HBM_GBS else None},
+            "rel_err_vs_undivided": err,
+            "note": "processes simulated one after another on one GPU; the owners' sums "
+                    "timed as one graph replay; the all-to-all between partial products and "
+                    "owners is not timed"}
+
+
 def other_configs(local_rank, stream):
     """The other workloads of the method, measured like the headline: numeric GFLOP/s
     (CUDA events, median of 20 after 3 warm-ups), fraction of the FP64 unit-count peak
@@ -675,8 +759,15 @@ def other_configs(local_rank, stream):
     ms = _median_ms(lambda: plan.execute(1.0, 0.0, bst.BST_FP64_EMU_BF16, 1), stream)
     ts["emu_bf16"] = dict(rate_emu(f, ms, [plan]), rel_err_vs_oracle_sample=_sample_err_matrix(
         p, plan, p.A.col_sizes, p.B.col_sizes))
+    # the K split of the same product over 4 processes (paper Sec. 3.1), the processes
+    # simulated one after another on this GPU: partial products, then every owner's
+    # fixed-order sum (bst_sum_parts); the all-to-all between them is not timed here
+    plan.execute(1.0, 0.0, bst.BST_FP64, 1)
+    torch.cuda.synchronize()
+    whole = plan.result.data[:plan.result.info[3]].clone()
+    ts["ksplit_4_simulated"] = ksplit_simulated(p, 4, whole, local_rank, stream)
     out["tall_skinny_AtB"] = ts
-    del plan, A, B
+    del plan, A, B, whole
     # 64 independent products in one persistent launch, replayed from a CUDA graph
     probs = batched()
     mats, plans = [], []

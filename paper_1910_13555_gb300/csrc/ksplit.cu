@@ -10,7 +10,8 @@
 // part i, located through src_off[i * nblocks + u] (-1: part i has no such block).  The
 // order of the additions is the part order whatever the launch shape, so every process
 // gets the same bits for the same inputs.  One warp per block, lanes over its elements
-// (C blocks of a few hundred elements), read once and written once: bound by HBM.
+// (C blocks of a few hundred elements), read once and written once: bound by HBM, or by
+// load latency when C is small.
 #include "bst_internal.h"
 
 namespace bst {
@@ -18,6 +19,9 @@ namespace {
 
 constexpr int kWarps = 8;
 
+// The block's part offsets are loaded once, 32 parts per round (lane i holds part i of
+// the round), and the element loop issues the loads of up to 8 present parts before
+// adding them in part order, so a warp keeps several loads in flight.
 __global__ void __launch_bounds__(32 * kWarps)
     k_sum_parts(int32_t nparts, int64_t nblocks, const int64_t *__restrict__ dst_off,
                 const int64_t *__restrict__ src_off, const double *__restrict__ src,
@@ -26,17 +30,42 @@ __global__ void __launch_bounds__(32 * kWarps)
   const int64_t nwarps = (int64_t)gridDim.x * kWarps;
   for (int64_t u = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); u < nblocks; u += nwarps) {
     const int64_t d0 = dst_off[u], len = dst_off[u + 1] - d0;
-    for (int64_t e = lane; e < len; e += 32) {
+    for (int64_t e0 = 0; e0 < len; e0 += 32) {
+      const int64_t e = e0 + lane;
+      const bool live = e < len;
       double acc = 0.0;
       bool any = false;
-      for (int32_t i = 0; i < nparts; ++i) {
-        const int64_t o = src_off[(int64_t)i * nblocks + u];
-        if (o < 0) continue;
-        const double v = __ldcs(src + o + e);  // streamed: read once
-        acc = any ? acc + v : v;
-        any = true;
+      for (int32_t r0 = 0; r0 < nparts; r0 += 32) {
+        const int64_t my = r0 + lane < nparts ? src_off[(int64_t)(r0 + lane) * nblocks + u] : -1;
+        unsigned present = __ballot_sync(0xffffffffu, my >= 0);
+        while (present) {
+          // the next (up to) 8 present parts of this round, in part order
+          int idx[8];
+          int cnt = 0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            idx[k] = present ? __ffs(present) - 1 : -1;
+            if (present) {
+              present &= present - 1u;
+              ++cnt;
+            }
+          }
+          double v[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const long long o = __shfl_sync(0xffffffffu, (long long)my, idx[k] < 0 ? 0 : idx[k]);
+            v[k] = (k < cnt && live) ? __ldcs(src + o + e) : 0.0;
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            if (k < cnt) {
+              acc = any ? acc + v[k] : v[k];
+              any = true;
+            }
+          }
+        }
       }
-      dst[d0 + e] = acc;
+      if (live) dst[d0 + e] = acc;
     }
   }
 }
