@@ -43,8 +43,10 @@
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
  *     asynchronous on it except where documented (plans synchronise the stream a few
  *     times to learn output and schedule sizes; the first emulated-FP64 or 3xTF32
- *     execute of a plan and the first execute after a tuning change synchronise too,
- *     while they build per-plan state; other executes only queue work).
+ *     execute of a plan, the emulated execute that builds its panel schedule (the
+ *     second by default, see BST_TUNE_EMU_PANEL) and the first execute after a tuning
+ *     change synchronise too, while they build per-plan state; other executes only
+ *     queue work).
  *   - Handles are not thread-safe; use one handle per thread or lock around it.
  *   - A matrix or tensor must outlive every plan built from it.
  */
