@@ -1350,6 +1350,8 @@ static PanelState &panel_state(bst_plan *p, cudaStream_t s) {
 // kernel and the panel schedule is built at its second one: building it costs host work
 // and a few synchronisations of the order of the kernel time it saves, so a plan run
 // once (a step of a chain of fresh products) never pays for it.
+// An execute captured into a CUDA graph never builds the schedule (that synchronises):
+// it runs the C-block kernel, whose state the plan's first emulated execute built.
 bool panel_usable(bst_plan *p, cudaStream_t s, bool count) {
   const int mode = p->ctx->tune_emu_panel;
   if (!mode || p->C->nblocks == 0) return false;
@@ -1357,6 +1359,11 @@ bool panel_usable(bst_plan *p, cudaStream_t s, bool count) {
     const int n = p->emu_executes + 1;  // the execute this call is about
     if (count) p->emu_executes = n;
     if (n < 2) return false;
+  }
+  if (!p->panel || !p->panel->built) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    BST_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return false;
   }
   const PanelState &PS = panel_state(p, s);
   return PS.eligible;

@@ -299,3 +299,38 @@ def test_default_mode_batch_and_second_execute_per_block_accuracy():
         ref = oracle.multiply(p.A, p.B, None, 1.0, 0.0, p.eps)
         assert per_block_max_err(dict(data=got[q]), ref, p.A.row_sizes, p.B.col_sizes) <= TOL
     assert (second == got[-1]).all()
+
+
+def test_graph_capture_before_and_after_the_schedule_exists():
+    """Default choice: an emulated execute captured into a CUDA graph before the panel
+    schedule exists runs the C-block kernel (building the schedule would synchronise);
+    once a plain execute has built it, a captured execute runs the panel kernel.  Both
+    replays against the oracle."""
+    import torch
+    p = banded(seed=46, nb=300, eps=1e-8)
+    ref = oracle.multiply(p.A, p.B, None, 1.0, 0.0, p.eps)
+    with panel_mode(1):
+        A, B = to_lib(p.A), to_lib(p.B)
+        plan = bst.multiply_plan(A, B, None, p.eps)
+        C = plan.alloc_result()
+        n = C.info[3]
+        plan.execute(1.0, 0.0, bst.BST_FP64_EMU_BF16, 1)  # first: C-block kernel state
+        torch.cuda.synchronize()
+        graphs = []
+        for _ in range(2):
+            g = torch.cuda.CUDAGraph()
+            cs = torch.cuda.Stream()
+            with torch.cuda.graph(g, stream=cs):
+                plan.execute(1.0, 0.0, bst.BST_FP64_EMU_BF16, 1, stream=cs)
+            C.data.fill_(float("nan"))
+            g.replay()
+            torch.cuda.synchronize()
+            got = C.data[:n].cpu().numpy()
+            assert np.isfinite(got).all()
+            assert rel_fro(got, ref["data"]) <= TOL
+            graphs.append(g)
+            # a plain execute: builds the schedule (after the first graph)
+            plan.execute(1.0, 0.0, bst.BST_FP64_EMU_BF16, 1)
+            torch.cuda.synchronize()
+        assert bst.bst_plan_emu_costs(plan.handle)["panel"]
+        assert plan.stats()["n_stack"] > 0
