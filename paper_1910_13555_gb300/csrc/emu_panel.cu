@@ -457,7 +457,8 @@ struct RedArgs {
 
 // C blocks with several products or a C_in block: their slots added in product order
 // (exact integer sums), converted once, alpha and beta C_in applied.  One warp per C
-// block, each lane summing its elements' slots with the loads issued before the adds.
+// block, each lane summing two elements' slots at a time with the loads issued before
+// the adds.
 __global__ void k_pan_reduce(RedArgs P) {
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -468,30 +469,48 @@ __global__ void k_pan_reduce(RedArgs P) {
       P.slots + (long long)(((unsigned long long)(unsigned)d0.y << 32) | (unsigned)d0.x);
   const double *ci = (P.has_beta && cin >= 0) ? P.Cin + P.cin_off[cin] : nullptr;
   double *out = P.C + (long long)(((unsigned long long)(unsigned)d0.w << 32) | (unsigned)d0.z);
-  for (int e = lane; e < mn; e += 32) {
-    // the common counts spelled out so that all loads are in flight before the adds
+  // two elements per lane and iteration (e, e + 32); the common product counts spelled
+  // out so that all loads of both are in flight before the adds
+  auto sum_at = [&](int e) -> long long {
     long long acc = 0;
-    if (np == 1) {
-      acc = __ldcs(sl + e);
-    } else if (np == 2) {
-      const long long x0 = __ldcs(sl + e), x1 = __ldcs(sl + mn + e);
-      acc = x0 + x1;
-    } else if (np == 3) {
-      const long long x0 = __ldcs(sl + e), x1 = __ldcs(sl + mn + e), x2 = __ldcs(sl + 2 * mn + e);
-      acc = x0 + x1 + x2;
-    } else {
-      int q = 0;
-      for (; q + 4 <= np; q += 4) {
-        const long long x0 = __ldcs(sl + (int64_t)q * mn + e), x1 = __ldcs(sl + (int64_t)(q + 1) * mn + e);
-        const long long x2 = __ldcs(sl + (int64_t)(q + 2) * mn + e), x3 = __ldcs(sl + (int64_t)(q + 3) * mn + e);
-        acc += (x0 + x1) + (x2 + x3);
-      }
-      for (; q < np; ++q) acc += __ldcs(sl + (int64_t)q * mn + e);
+    int q = 0;
+    for (; q + 4 <= np; q += 4) {
+      const long long x0 = __ldcs(sl + (int64_t)q * mn + e), x1 = __ldcs(sl + (int64_t)(q + 1) * mn + e);
+      const long long x2 = __ldcs(sl + (int64_t)(q + 2) * mn + e), x3 = __ldcs(sl + (int64_t)(q + 3) * mn + e);
+      acc += (x0 + x1) + (x2 + x3);
     }
+    for (; q < np; ++q) acc += __ldcs(sl + (int64_t)q * mn + e);
+    return acc;
+  };
+  auto finish = [&](long long acc, int e) {
     double v = np > 0 ? i64_scaled_int(acc, sc) : 0.0;
     if (!P.alpha_one) v *= P.alpha;
     if (ci) v = fma(P.beta, ci[e], v);
     out[e] = v;
+  };
+  for (int e = lane; e < mn; e += 64) {
+    const bool v1 = e + 32 < mn;
+    const int e1 = v1 ? e + 32 : e;  // a valid index for the second element's loads
+    long long a0 = 0, a1 = 0;
+    if (np == 1) {
+      a0 = __ldcs(sl + e);
+      a1 = __ldcs(sl + e1);
+    } else if (np == 2) {
+      const long long x0 = __ldcs(sl + e), x1 = __ldcs(sl + mn + e);
+      const long long y0 = __ldcs(sl + e1), y1 = __ldcs(sl + mn + e1);
+      a0 = x0 + x1;
+      a1 = y0 + y1;
+    } else if (np == 3) {
+      const long long x0 = __ldcs(sl + e), x1 = __ldcs(sl + mn + e), x2 = __ldcs(sl + 2 * mn + e);
+      const long long y0 = __ldcs(sl + e1), y1 = __ldcs(sl + mn + e1), y2 = __ldcs(sl + 2 * mn + e1);
+      a0 = x0 + x1 + x2;
+      a1 = y0 + y1 + y2;
+    } else if (np > 0) {
+      a0 = sum_at(e);
+      if (v1) a1 = sum_at(e1);
+    }
+    finish(a0, e);
+    if (v1) finish(a1, e1);
   }
 }
 
