@@ -289,21 +289,9 @@ struct SideP {
   char *img;
 };
 
-// largest exponent of every stored block (one warp per block)
-__global__ void k_pan_exps(SideP S) {
-  const int lane = threadIdx.x & 31;
-  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (b >= S.nblocks) return;
-  const int n = S.rsz[S.row[b]] * S.csz[S.col[b]];
-  const double *x = S.data + S.off[b];
-  int E = kNoExp;
-  for (int e = lane; e < n; e += 32) E = max(E, exp_of(x[e]));
-#pragma unroll
-  for (int o = 16; o; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
-  if (lane == 0) S.bexp[b] = E;
-}
-
-// Digits of every stored block of a panel into its tile image.  Item (outer row r of
+// Digits of every stored block of a panel into its tile image, after its largest
+// exponent (one warp per stored block; blocks no kept product uses are skipped, their
+// exponent is never read).  Item (outer row r of
 // the tile, 8-group g of the inner index): 8 consecutive inner values -> six 16-byte
 // core-matrix rows, one per slice (inner positions at and above the inner size are
 // written as zeros).
@@ -331,8 +319,16 @@ __global__ void k_pan_digits(SideP S) {
     first = S.list[U.ab0 + wh.y].y;
   }
   const int stepb = S.is_b ? kBStep : kAStep;
-  const int E = S.bexp[b];
   const double *x = S.data + S.off[b];
+  // the block's largest exponent (also kept for the records and the slot shifts)
+  int E = kNoExp;
+  {
+    const int n = R * Cc;
+    for (int e = lane; e < n; e += 32) E = max(E, exp_of(x[e]));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+    if (lane == 0) S.bexp[b] = E;
+  }
   const int ng = 2 * nq;
   const int total = nouter * ng;
   for (int it = lane; it < total; it += 32) {
@@ -1460,8 +1456,6 @@ void panel_prepare(bst_plan *p, const NumArgs &a, cudaStream_t s) {
     S.ntiles = PS.ntiles;
     S.list = side ? PS.blist : PS.alist;
     S.img = side ? PS.b_img : PS.a_img;
-    k_pan_exps<<<nblk(X->nblocks, wpb), 32 * wpb, 0, s>>>(S);
-    BST_CHECK_LAUNCH();
     k_pan_digits<<<nblk(X->nblocks, wpb), 32 * wpb, 0, s>>>(S);
     BST_CHECK_LAUNCH();
   }
