@@ -58,6 +58,7 @@ def _measured_hbm():
 
 MEASURED_HBM_GBS = _measured_hbm()
 CPU_SAMPLE_ROWS = (1000, 3000)     # cpu_baseline: block rows of A in the sample
+D2H_SPLIT = 4                      # e2e: parts of C's read-back, one copy stream each
 REF_SAMPLE_ROWS = (1800, 2200)     # --impl reference: block rows per step
 # timed-step precision -> (library constant name, numeric kernel launched by execute)
 PRECISIONS = {"fp64": ("BST_FP64", "k_num_fp64_staged1"),
@@ -911,11 +912,11 @@ def e2e_leg(p, local_rank, steps, stream, barrier, world, dev):
     """The same metric through the public API from host buffers: each step copies A's
     and B's data from pinned host memory (H2D), creates the matrices from the host index
     arrays, plans, executes and reads all of C_out back into pinned host memory (D2H).
-    Steps alternate between two compute streams, and each step's D2H runs on a copy
-    stream of its own that waits for the execute, so one step's D2H overlaps the next
-    steps' uploads, plans and executes (on one stream, the next upload two steps later
-    queued behind the 4 GB read-back and the SMs waited for it), as a caller streaming
-    independent products would run them."""
+    Steps alternate between two compute streams, and each step's D2H runs on copy
+    streams of its own (the read-back in D2H_SPLIT parts) that wait for the execute, so
+    one step's D2H overlaps the next steps' uploads, plans and executes (on one stream,
+    the next upload two steps later queued behind the 4 GB read-back and the SMs waited
+    for it), as a caller streaming independent products would run them."""
     import torch
 
     from paper_1910_13555_gb300 import bst
@@ -924,7 +925,9 @@ def e2e_leg(p, local_rank, steps, stream, barrier, world, dev):
     hb = torch.from_numpy(p.B.data).pin_memory()
     ctx = bst.context(local_rank)
     streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
-    copies = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+    # the read-back of C in D2H_SPLIT parts, each on a copy stream of its own, so that
+    # several copy engines move it at once
+    copies = [[torch.cuda.Stream(device=dev) for _ in range(D2H_SPLIT)] for _ in range(2)]
     hcs = [None, None]
     alive = [None, None]  # objects of the step in flight on each stream
     info = {"flops": 0.0, "n": 0}
@@ -934,7 +937,7 @@ def e2e_leg(p, local_rank, steps, stream, barrier, world, dev):
     def one(i):
         slot = i % 2
         s = streams[slot]
-        m = [ev() for _ in range(6)]
+        m = [ev() for _ in range(5 + D2H_SPLIT)]
         with torch.cuda.stream(s):
             sh = s.cuda_stream
             m[0].record(s)
@@ -953,13 +956,16 @@ def e2e_leg(p, local_rank, steps, stream, barrier, world, dev):
             n = plan.result.info[3]
             if hcs[slot] is None or hcs[slot].numel() < n:
                 hcs[slot] = torch.empty(n, dtype=torch.float64).pin_memory()
-        cs = copies[slot]
-        cs.wait_event(m[3])
-        with torch.cuda.stream(cs):
-            m[4].record(cs)
-            plan.result.data.record_stream(cs)
-            hcs[slot][:n].copy_(plan.result.data[:n], non_blocking=True)
-            m[5].record(cs)
+        cut = [n * j // D2H_SPLIT for j in range(D2H_SPLIT + 1)]
+        for j, cs in enumerate(copies[slot]):
+            cs.wait_event(m[3])
+            with torch.cuda.stream(cs):
+                if j == 0:
+                    m[4].record(cs)
+                plan.result.data.record_stream(cs)
+                hcs[slot][cut[j]:cut[j + 1]].copy_(plan.result.data[cut[j]:cut[j + 1]],
+                                                   non_blocking=True)
+                m[5 + j].record(cs)
         alive[slot] = (plan, A, B, da, db)
         info["flops"] = plan.stats()["flops"]
         info["n"] = n
@@ -981,11 +987,14 @@ def e2e_leg(p, local_rank, steps, stream, barrier, world, dev):
     h2d = (p.A.data.nbytes + p.B.data.nbytes + 8 * (p.A.nblocks + p.B.nblocks) +
            4 * (len(p.A.row_sizes) + len(p.A.col_sizes) + len(p.B.row_sizes) + len(p.B.col_sizes)))
     phase = lambda a, b: statistics.median(x[a].elapsed_time(x[b]) for x in marks)
+    d2h = statistics.median(max(x[4].elapsed_time(x[5 + j]) for j in range(D2H_SPLIT))
+                            for x in marks)
     return {"value": flops / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(8 * info["n"]), "ms_per_step": dt * 1e3,
-            "steps_timed": steps, "streams": "2 compute + 2 copy",
+            "steps_timed": steps,
+            "streams": f"2 compute + 2 x {D2H_SPLIT} copy (the read-back in {D2H_SPLIT} parts)",
             "phases_ms_median": {"h2d": phase(0, 1), "create_and_plan": phase(1, 2),
-                                 "execute": phase(2, 3), "d2h": phase(4, 5)},
+                                 "execute": phase(2, 3), "d2h": d2h},
             "phases_note": "CUDA events per step on its own streams; phases of consecutive "
                            "steps overlap (the read-back of one step runs beside the next "
                            "steps' uploads, plans and executes), so they do not add up to "
