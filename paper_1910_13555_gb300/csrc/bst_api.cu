@@ -149,6 +149,7 @@ bst_status bst_context_destroy(bst_ctx *ctx) {
   }
   if (ctx && ctx->rb_host) cudaFreeHost(ctx->rb_host);
   if (ctx && ctx->up_host) cudaFreeHost(ctx->up_host);
+  if (ctx && ctx->up_event) cudaEventDestroy(ctx->up_event);
   delete static_cast<bst::Ctx *>(ctx);
   API_END
 }

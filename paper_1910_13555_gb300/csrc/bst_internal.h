@@ -108,6 +108,10 @@ struct bst_ctx {
   void *up_host = nullptr;
   size_t up_cap = 0;
   std::mutex up_mutex;
+  // recorded after the copies of an Upload finished with done_async(); the next Upload
+  // waits for it before it writes the staging buffer again
+  cudaEvent_t up_event = nullptr;
+  bool up_pending = false;
   // kernel choices (bst_tune_set): emulated-FP64 digit scaling per whole op row /
   // column (1) or per block row / column (0); per (m, n) C block class, the tile
   // orientation of the emulated kernel (1 = MMA rows run over the C block's columns);
@@ -240,6 +244,11 @@ struct Upload {
   }
   void flush();  // launch the copies staged so far and wait for them
   void done();   // flush() and release the staging buffer to other threads
+  // launch the copies without waiting (the next Upload waits before it reuses the
+  // buffer): only for data the same stream consumes, before a later synchronisation of
+  // that stream hands the result to the caller
+  void done_async();
+  void launch();  // the copy kernels of the items staged so far
 };
 void gather_i32(const int32_t *src, const int32_t *idx, int32_t *dst, int64_t n, cudaStream_t s);
 

@@ -1057,7 +1057,7 @@ static bool build_staged(bst_plan *p, cudaStream_t s) {
     d_wp = up.add_vector(scratch, wpanel);
     d_smax = up.add_vector(scratch, class_split_bounds(p));
     if (slab) d_kin = up.add_vector(scratch, p->a_slab_kin);
-    up.done();
+    up.done_async();  // read by this stream's kernels below; the plan synchronises later
   }
   unsigned long long *d_sums = scratch.alloc_n<unsigned long long>(2);
   BST_CUDA(cudaMemsetAsync(d_sums, 0, 2 * sizeof(unsigned long long), s));

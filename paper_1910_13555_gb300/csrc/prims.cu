@@ -305,8 +305,27 @@ void Upload::done() {
   }
 }
 
+void Upload::done_async() {
+  if (!items.empty()) {
+    launch();
+    if (!ctx->up_event) BST_CUDA(cudaEventCreateWithFlags(&ctx->up_event, cudaEventDisableTiming));
+    BST_CUDA(cudaEventRecord(ctx->up_event, s));
+    ctx->up_pending = true;
+    items.clear();
+    used = 0;
+  }
+  if (locked) {
+    locked = false;
+    ctx->up_mutex.unlock();
+  }
+}
+
 void Upload::add(void *dev_dst, const void *host_src, size_t bytes) {
   if (bytes == 0) return;
+  if (ctx->up_pending) {  // an earlier Upload's copies may still read the buffer
+    BST_CUDA(cudaEventSynchronize(ctx->up_event));
+    ctx->up_pending = false;
+  }
   const size_t off = (used + 15) & ~(size_t)15;
   if (off + bytes > ctx->up_cap) {
     // grow (geometrically, never shrinking: freeing pinned memory synchronises the whole
@@ -327,6 +346,13 @@ void Upload::add(void *dev_dst, const void *host_src, size_t bytes) {
 
 void Upload::flush() {
   if (items.empty()) return;
+  launch();
+  BST_CUDA(cudaStreamSynchronize(s));
+  items.clear();
+  used = 0;
+}
+
+void Upload::launch() {
   void *dev_view = nullptr;
   BST_CUDA(cudaHostGetDevicePointer(&dev_view, ctx->up_host, 0));
   for (const Item &it : items) {
@@ -342,9 +368,6 @@ void Upload::flush() {
     }
     BST_CHECK_LAUNCH();
   }
-  BST_CUDA(cudaStreamSynchronize(s));
-  items.clear();
-  used = 0;
 }
 
 void fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s) {

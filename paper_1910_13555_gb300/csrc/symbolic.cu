@@ -305,6 +305,10 @@ __global__ void k_sym_fill(SymArgs S, FillOut O) {
   });
 }
 
+__global__ void k_i64_to_i32_one(const int64_t *__restrict__ in, int32_t *__restrict__ out) {
+  *out = (int32_t)*in;
+}
+
 __global__ void k_rowptr_i64_to_i32(const int64_t *__restrict__ in, int32_t *__restrict__ out,
                                     int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -462,7 +466,7 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
     p->cls_m = up.add_vector(ar, cm);
     p->cls_n = up.add_vector(ar, cn);
     p->kval = up.add_vector(ar, kv);
-    up.done();  // host vectors go out of scope
+    up.done_async();  // staged on the host already; the plan synchronises later
   }
 
   // block norms (filter input)
@@ -565,12 +569,9 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
     k_sym_fill<<<nblk(M, wpc), 32 * wpc, smem_fill, s>>>(S, O);
     BST_CHECK_LAUNCH();
   }
-  {
-    const int32_t tv = (int32_t)T;
-    Upload up(p->ctx, s);
-    up.add(p->t_start + nnzC, &tv, 4);
-    up.done();  // tv lives on this frame
-  }
+  // t_start[nnzC] = T, from the device's own count (no host round trip)
+  k_i64_to_i32_one<<<1, 1, 0, s>>>(t_rowptr + M, p->t_start + nnzC);
+  BST_CHECK_LAUNCH();
 
   // element offsets and (m,n) class of every C block
   int64_t *csize = scratch.alloc_n<int64_t>((size_t)nnzC);
@@ -580,14 +581,7 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
     BST_CHECK_LAUNCH();
   }
   exscan_i64(csize, C->off, nnzC, scratch, s);
-  int64_t nelemC = 0;
-  {
-    ReadBack rb(p->ctx, s);
-    rb.add(&nelemC, C->off + nnzC, 8);
-    rb.done();
-  }
-  BST_REQUIRE(nelemC < INT32_MAX, BST_ERR_OVERFLOW, "C_out has more than 2^31-1 elements");
-  C->nelem = nelemC;
+  int64_t nelemC = 0;  // read back with the class and bucket pointers below
 
   // numeric task list: C blocks grouped by (m, n) class, CSR order inside a class
   const int32_t ncls = p->Dm * p->Dn;
@@ -668,8 +662,11 @@ void symbolic_phase(bst_plan *p, cudaStream_t s) {
   }
   unsigned long long hrefel[2];
   rb_ptrs.add(hrefel, refel, 16);
+  rb_ptrs.add(&nelemC, C->off + nnzC, 8);
   rb_ptrs.done();
   scratch.release_all();
+  BST_REQUIRE(nelemC < INT32_MAX, BST_ERR_OVERFLOW, "C_out has more than 2^31-1 elements");
+  C->nelem = nelemC;
 
   p->h_bucket_ptr.assign(hb.begin(), hb.end());
   // statistics

@@ -163,3 +163,51 @@ def test_multiply_ksplit_one_process_group(backend):
     assert pr.returncode == 0, pr.stderr[-3000:]
     # the communication libraries print their own lines too
     assert any(line.startswith("ok ") for line in pr.stdout.splitlines()), pr.stdout
+
+
+def test_simulated_ksplit_with_cin_alpha_beta():
+    """alpha on every partial product, beta C_in on process 0's only (C_in has blocks no
+    product reaches), 3 processes simulated on one GPU, against the undivided oracle."""
+    import torch
+    rng = np.random.default_rng(22)
+    p = _problem(eps=30.0)
+    A, B = p.A, p.B
+    rs, cs = A.col_sizes, B.col_sizes
+    full0 = oracle.multiply(A, B, None, 1.0, 0.0, p.eps, "T", "N")
+    keep = rng.random(len(full0["rows"])) < 0.3
+    pairs = sorted(set(zip(full0["rows"][keep].tolist(), full0["cols"][keep].tolist())) |
+                   set(zip(rng.integers(0, len(rs), 25).tolist(),
+                           rng.integers(0, len(cs), 25).tolist())))
+    ci_r = np.array([a for a, _ in pairs], np.int32)
+    ci_c = np.array([b for _, b in pairs], np.int32)
+    ci_d = rng.uniform(-1, 1, int((rs[ci_r].astype(np.int64) * cs[ci_c]).sum()))
+    Ci = BSMatrix(rs, cs, ci_r, ci_c, ci_d)
+    alpha, beta = -0.75, 1.5
+    full = oracle.multiply(A, B, Ci, alpha, beta, p.eps, "T", "N")
+    ka = ksplit.k_index(A.rows, A.cols, "T", "A")
+    kb = ksplit.k_index(B.rows, B.cols, "N", "B")
+    ea = A.row_sizes[A.rows].astype(np.int64) * A.col_sizes[A.cols]
+    eb = B.row_sizes[B.rows].astype(np.int64) * B.col_sizes[B.cols]
+    P = 3
+    r = ksplit.k_ranges(ka, ea, kb, eb, A.row_sizes, P)
+    mk = lambda m: bst.Matrix.from_host(m.row_sizes, m.col_sizes, m.rows, m.cols, m.data)
+    parts, pats, keep_alive = [], [], []
+    for i in range(P):
+        Ai, Bi = mk(_cut(A, "T", "A", r[i], r[i + 1])), mk(_cut(B, "N", "B", r[i], r[i + 1]))
+        Cii = mk(Ci) if i == 0 else None
+        plan = bst.multiply(Ai, Bi, Cii, alpha, beta if i == 0 else 0.0, p.eps, "T", "N")
+        rows, cols, _ = plan.result.index()
+        pats.append((rows, cols))
+        parts.append(plan.result.data[:plan.result.info[3]])
+        keep_alive.append((plan, Ai, Bi, Cii))
+    lay = ksplit.exchange_layout(pats, rs, cs)
+    assert np.array_equal(lay.rows, full["rows"]) and np.array_equal(lay.cols, full["cols"])
+    out = []
+    for q in range(P):
+        recv = torch.cat([parts[i][int(lay.send[i, :q].sum()):int(lay.send[i, :q + 1].sum())]
+                          for i in range(P)])
+        _, _, _, data, _ = ksplit.sum_owned(lay, q, recv)
+        torch.cuda.synchronize()
+        out.append(data.cpu().numpy())
+    got = np.concatenate(out)
+    assert np.linalg.norm(got - full["data"]) / np.linalg.norm(full["data"]) <= 1e-12
