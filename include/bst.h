@@ -158,7 +158,7 @@ bst_status bst_matrix_filter_copy(const bst_matrix *X, bst_matrix *Y, void *stre
  * the block-norm filter eps >= 0 (see top).  C_in may be NULL.  Planning runs the
  * GPU symbolic phase on `stream`: block norms, pair matching + filter, pattern of
  * C_out, the stacks and the numeric schedule.  It synchronises `stream` several times
- * (about ten round trips) to learn the sizes of what it builds next.
+ * (about seven round trips) to learn the sizes of what it builds next.
  * The plan keeps pointers to A, B, C_in; their data are read at execute time.
  * Errors: INVALID_ARG, SHAPE_MISMATCH (inner block sizes differ, or C_in's grid
  * differs from op(A) rows x op(B) columns), OVERFLOW, UNSUPPORTED (more than 2^20
