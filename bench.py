@@ -744,6 +744,11 @@ def other_configs(local_rank, stream):
     out["plain_40x40_size5"] = dict(rate(plan.stats()["flops"], ms),
                                     rel_err_vs_oracle=_rel(plan.result.data[:n].cpu().numpy(),
                                                            ref["data"]))
+    # the no-allocation execute (CTA-level K split into the static array), split 2
+    ms = _median_ms(lambda: bst.bst_multiply_execute_static(plan.handle, 1.0, 0.0, 2), stream)
+    out["plain_40x40_size5"]["static_split_2"] = dict(
+        rate(plan.stats()["flops"], ms),
+        rel_err_vs_oracle=_rel(plan.result.data[:n].cpu().numpy(), ref["data"]))
     del plan, A, B
     # tall-skinny C = A^T B (100000 x 400 blocks), split-K
     p = tall_skinny()
@@ -752,7 +757,9 @@ def other_configs(local_rank, stream):
     plan.alloc_result(local_rank)
     f = plan.stats()["flops"]
     ts = {}
-    for split in (1, 0):
+    # split 1 and the automatic choice run the staged kernel; split 4 the CTA-level K
+    # split (k_num_fp64 into 4 partial copies of C, then k_splitk_reduce)
+    for split in (1, 0, 4):
         ms = _median_ms(lambda: plan.execute(1.0, 0.0, bst.BST_FP64, split), stream)
         ts[f"split_{split or 'auto'}"] = dict(rate(f, ms), split_k=plan.stats()["split_k"],
                                               rel_err_vs_oracle_sample=_sample_err_matrix(

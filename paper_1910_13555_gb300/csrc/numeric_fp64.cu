@@ -509,16 +509,43 @@ __device__ __forceinline__ void store_block(const NumParams &P, const F64Blk &b,
   }
 }
 
+// A K split (ksplit > 1, single plans only): item i is part i % ksplit of tile
+// items[i / ksplit]; the part takes its share of the tile's entries (contiguous, in
+// entry order) and writes its partial sums, without alpha, to W + part * nelem(C), which
+// k_splitk_reduce adds in part order.
+__device__ __forceinline__ void store_part(const NumParams &P, const F64Blk &b, int part,
+                                           const double (&acc)[kMaxR]) {
+  const int lane = threadIdx.x & 31, mn = b.m * b.n;
+  double *W = P.W + (int64_t)part * P.nelemC + b.off;
+#pragma unroll
+  for (int r = 0; r < kMaxR; ++r)
+    if (lane + 32 * r < mn) W[lane + 32 * r] = acc[r];
+}
+
 template <bool STRIDED, bool SPLIT, class GetP>
 __device__ __forceinline__ void staged_loop(const int64_t *__restrict__ items, int64_t nitems,
                                             int slot_elems, unsigned long long *__restrict__ counter,
-                                            int chunk, GetP get) {
+                                            int chunk, int ksplit, GetP get) {
   extern __shared__ double smem_stage[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double *slots = smem_stage + (size_t)wid * 2 * slot_elems;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
-  auto item = [&](int64_t i) -> int64_t { return i < nitems ? items[i] : -1; };
+  auto item = [&](int64_t i) -> int64_t {
+    if (i >= nitems) return -1;
+    if (ksplit <= 1) return items[i];
+    return items[i / ksplit] | ((i % ksplit) << 32);
+  };
+  // a K part's share of its tile's entries
+  auto part_of = [&](F64Blk b, int64_t v) -> F64Blk {
+    if (ksplit > 1 && v >= 0) {
+      const int q = (int)(v >> 32);
+      const int e0 = (int)((int64_t)b.ne * q / ksplit), e1 = (int)((int64_t)b.ne * (q + 1) / ksplit);
+      b.eb += e0;
+      b.ne = e1 - e0;
+    }
+    return b;
+  };
   // item positions [pos, end) left of the current chunk.  Chunks w and W + w are the
   // warp's own; on opening a chunk lane 0 requests the next one from the counter
   // (`ticket`, chunk 2 W + ticket), whose value is first read when that chunk opens.
@@ -550,13 +577,13 @@ __device__ __forceinline__ void staged_loop(const int64_t *__restrict__ items, i
   if (v < 0) return;
   int64_t vn = item(next_pos());
   int dw = word(v), dwn = word(vn);
-  F64Blk b = f64_blk(dw);
+  F64Blk b = part_of(f64_blk(dw), v);
   int4 ent = group(v, b, 0);
   int slot = 0;
   bool staged = false;  // slot holds the first product of the current block
   for (;;) {
     const NumParams &P = get(v >> 32);
-    const F64Blk bn = f64_blk(dwn);
+    const F64Blk bn = part_of(f64_blk(dwn), vn);
     const int4 entn = group(vn, bn, 0);
     const int64_t vnn = vn >= 0 ? item(next_pos()) : -1;
     const int dwnn = word(vnn);
@@ -611,7 +638,10 @@ __device__ __forceinline__ void staged_loop(const int64_t *__restrict__ items, i
     staged = b.ne > 0 && vn >= 0 && bn.ne > 0;
     // the slot of the tile's last job is free: the next tile's first job went to the other
     if (SPLIT && b.s > 1 && b.ne > 0) split_reduce(slots + (slot ^ 1) * slot_elems, b.m * b.n, b.s, acc);
-    store_block(P, b, acc);
+    if (ksplit > 1)
+      store_part(P, b, (int)(v >> 32), acc);
+    else
+      store_block(P, b, acc);
     if (vn < 0) break;
     v = vn;
     vn = vnn;
@@ -630,16 +660,17 @@ __device__ __forceinline__ void staged_loop(const int64_t *__restrict__ items, i
 template <bool STRIDED, bool SPLIT>
 __global__ void __launch_bounds__(32 * kStageWarps, 3)
     k_num_fp64_staged1(NumParams P, const int64_t *__restrict__ items, int64_t nitems,
-                       int slot_elems, unsigned long long *counter, int chunk) {
-  staged_loop<STRIDED, SPLIT>(items, nitems, slot_elems, counter, chunk,
+                       int slot_elems, unsigned long long *counter, int chunk, int ksplit) {
+  staged_loop<STRIDED, SPLIT>(items, nitems, slot_elems, counter, chunk, ksplit,
                               [&](int64_t) -> const NumParams & { return P; });
 }
 
 template <bool STRIDED, bool SPLIT>
 __global__ void __launch_bounds__(32 * kStageWarps, 3)
     k_num_fp64_staged(const NumParams *__restrict__ plans, const int64_t *__restrict__ items,
-                      int64_t nitems, int slot_elems, unsigned long long *counter, int chunk) {
-  staged_loop<STRIDED, SPLIT>(items, nitems, slot_elems, counter, chunk,
+                      int64_t nitems, int slot_elems, unsigned long long *counter, int chunk,
+                      int ksplit) {
+  staged_loop<STRIDED, SPLIT>(items, nitems, slot_elems, counter, chunk, 1,
                               [&](int64_t pl) -> const NumParams & { return plans[pl]; });
 }
 
@@ -930,7 +961,7 @@ __global__ void k_splitk_reduce(NumParams P, int64_t nc, const int32_t *__restri
 
 NumParams make_params(bst_plan *p, const NumArgs &a, int split) {
   NumParams P;
-  P.A = (p->a_slab && p->stage_elems > 0 && split <= 1) ? p->a_slab_base : a.A;
+  P.A = (p->a_slab && p->stage_elems > 0) ? p->a_slab_base : a.A;
   P.B = a.B;
   P.Cin = a.Cin;
   P.C = a.C;
@@ -966,8 +997,11 @@ NumParams make_params(bst_plan *p, const NumArgs &a, int split) {
 
 }  // namespace
 
+// every native-FP64 execute of a plan with a staged schedule runs the staged kernel (a
+// K split too), which reads a slab plan's first tensor in place
 bool fp64_reads_slabs(const bst_plan *p, int split) {
-  return p->a_slab && p->stage_elems > 0 && split <= 1;
+  (void)split;
+  return p->a_slab && p->stage_elems > 0;
 }
 
 size_t num_params_bytes() { return sizeof(NumParams); }
@@ -1235,7 +1269,7 @@ static int staged_ctas_per_sm(K kernel, bool &attr_set, int slot_elems, size_t &
 template <class K, class Arg>
 static void staged_launch(K kernel, bool &attr_set, Arg params, const int64_t *items,
                           int64_t nitems, int slot_elems, int num_sms,
-                          unsigned long long *counter, cudaStream_t s) {
+                          unsigned long long *counter, cudaStream_t s, int ksplit = 1) {
   BST_REQUIRE(counter, BST_ERR_STATE, "staged kernel without a work counter");
   size_t smem = 0;
   const int per = staged_ctas_per_sm(kernel, attr_set, slot_elems, smem);
@@ -1245,7 +1279,8 @@ static void staged_launch(K kernel, bool &attr_set, Arg params, const int64_t *i
   const int g = (int)std::min<int64_t>((int64_t)per * num_sms,
                                        (nchunks + kStageWarps - 1) / kStageWarps);
   BST_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
-  kernel<<<g, 32 * kStageWarps, smem, s>>>(params, items, nitems, slot_elems, counter, chunk);
+  kernel<<<g, 32 * kStageWarps, smem, s>>>(params, items, nitems, slot_elems, counter, chunk,
+                                           ksplit);
   BST_CHECK_LAUNCH();
 }
 
@@ -1318,21 +1353,45 @@ void launch_direct_splitk(bst_plan *p, const NumParams &P, cudaStream_t s) {
 
 }  // namespace
 
+// The staged kernel over every tile (split = 1: into C), or over every (tile, K part)
+// into W followed by the fixed-order reduction of the parts (split > 1).
+static void staged_single(bst_plan *p, const NumParams &P, int split, cudaStream_t s) {
+  const int v = (p->stage_strided ? 1 : 0) | (p->stage_split ? 2 : 0);
+  const int ns = p->ctx->num_sms, se = p->stage_elems;
+  const int64_t nt = p->n_tiles * split;
+  switch (v) {
+    case 0: staged_launch(k_num_fp64_staged1<false, false>, g_attr[1][v], P, p->titems, nt, se, ns, p->items_counter, s, split); break;
+    case 1: staged_launch(k_num_fp64_staged1<true, false>, g_attr[1][v], P, p->titems, nt, se, ns, p->items_counter, s, split); break;
+    case 2: staged_launch(k_num_fp64_staged1<false, true>, g_attr[1][v], P, p->titems, nt, se, ns, p->items_counter, s, split); break;
+    default: staged_launch(k_num_fp64_staged1<true, true>, g_attr[1][v], P, p->titems, nt, se, ns, p->items_counter, s, split); break;
+  }
+  if (split > 1) {
+    const int wpb = 8;
+    const int64_t nc = p->C->nblocks;
+    k_splitk_reduce<<<nblk(nc, wpb), 32 * wpb, 0, s>>>(P, nc, p->C->row, p->C->col, p->C->rsz,
+                                                       p->C->csz);
+    BST_CHECK_LAUNCH();
+  }
+}
+
 void execute_fp64(bst_plan *p, const NumArgs &a, int split, cudaStream_t s) {
   const int64_t nc = p->C->nblocks;
   if (nc == 0) return;
-  if (split <= 1 && p->stage_elems > 0) {
+  if (p->stage_elems > 0) {
     refresh_f64_split(p, s);
-    const NumParams P = make_params(p, a, 1);
-    const int v = (p->stage_strided ? 1 : 0) | (p->stage_split ? 2 : 0);
-    const int ns = p->ctx->num_sms, se = p->stage_elems;
-    const int64_t nt = p->n_tiles;
-    switch (v) {
-      case 0: staged_launch(k_num_fp64_staged1<false, false>, g_attr[1][v], P, p->titems, nt, se, ns, p->items_counter, s); break;
-      case 1: staged_launch(k_num_fp64_staged1<true, false>, g_attr[1][v], P, p->titems, nt, se, ns, p->items_counter, s); break;
-      case 2: staged_launch(k_num_fp64_staged1<false, true>, g_attr[1][v], P, p->titems, nt, se, ns, p->items_counter, s); break;
-      default: staged_launch(k_num_fp64_staged1<true, true>, g_attr[1][v], P, p->titems, nt, se, ns, p->items_counter, s); break;
+    NumParams P = make_params(p, a, std::max(split, 1));
+    if (P.split > 1) {
+      const size_t need = sizeof(double) * (size_t)P.split * (size_t)P.nelemC;
+      if (p->work_bytes < need) {
+        p->work.release_all();
+        p->work.ctx = static_cast<Ctx *>(p->ctx);
+        p->work.stream = s;
+        p->work.alloc(need);
+        p->work_bytes = need;
+      }
+      P.W = static_cast<double *>(p->work.bufs.back().p);
     }
+    staged_single(p, P, P.split, s);
     return;
   }
   if (split <= 1 && p->items) {
@@ -1363,6 +1422,14 @@ void execute_fp64(bst_plan *p, const NumArgs &a, int split, cudaStream_t s) {
 // provided workspace W of at least split * nelem(C) doubles (no allocation here).
 void execute_fp64_workspace(bst_plan *p, const NumArgs &a, int split, double *W, cudaStream_t s) {
   if (p->C->nblocks == 0) return;
+  if (p->stage_elems > 0) {
+    // the tiles' inner splits were chosen when the plan was built (a later tuning change
+    // is taken by the next bst_multiply_execute, which may synchronise)
+    NumParams P = make_params(p, a, std::max(split, 1));
+    P.W = P.split > 1 ? W : nullptr;
+    staged_single(p, P, P.split, s);
+    return;
+  }
   NumParams P = make_params(p, a, split);
   P.A = a.A;  // the direct-load kernel never reads slabs in place
   P.W = P.split > 1 ? W : nullptr;

@@ -130,7 +130,7 @@ def test_slab_plan_split_k_and_adjoint(ctx):
     ref = oracle.contract(w.T1, w.T2, w.c1, w.c2, w.f1, w.f2, w.result_order)
     plan, (t1, t2, _) = _plan(ctx, w, 1)
     assert plan.schedule_info()["slab"]
-    plan.execute(1.0, 0.0, bst.BST_FP64, 3)  # split-K reads the permuted copy
+    plan.execute(1.0, 0.0, bst.BST_FP64, 3)  # the K split reads the slabs in place too
     idx, data = _result(plan)
     assert rel_fro(data, ref["data"]) <= 1e-12
     plan.execute(1.0, 0.0, bst.BST_FP64, 1)
