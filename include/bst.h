@@ -210,7 +210,7 @@ bst_status bst_plan_split_histogram(const bst_plan *plan, int64_t *hist);
  * staging copies strided rows (row tiles, inner panels or slabs), info[2] = 1 when some
  * tile splits its inner dimension (BST_TUNE_F64_SPLIT), info[3] = 1 when A is read in
  * place as slabs of a contraction operand (BST_TUNE_CONTRACT_SLAB).  As of the last
- * execute or plan build; split-K executes (split_k > 1) use none of this. */
+ * execute or plan build; split-K executes (split_k > 1) run the same staged tiles. */
 bst_status bst_plan_schedule_info(const bst_plan *plan, int32_t *info);
 
 /* Cost model of the emulated-FP64 execute of a plan, for rooflines: out[0] = BF16
@@ -233,9 +233,10 @@ enum {
 };
 
 /* Numeric phase into C_out's bound data.  split_k: 1 = each C block summed by one
- * warp; S > 1 = the K block range is cut into S equal parts whose partial sums go
- * to a workspace and are added in the fixed order 0..S-1 (paper Sec. 3.1);
- * 0 = choose S from the plan's shape.  With beta == 0 C_in is not read.
+ * warp; S > 1 = every C tile's products are cut into S contiguous parts (in product
+ * order, so along K) whose partial sums go to a workspace and are added in the fixed
+ * order 0..S-1 (paper Sec. 3.1: the K split with one reduction); 0 = choose S from
+ * the plan's shape.  With beta == 0 C_in is not read.
  * Executes of one plan must not overlap on the GPU (e.g. on two streams at once):
  * they write the same C_out and share the plan's work counter, from which the
  * persistent kernels take their tiles; order them on one stream or with events.
