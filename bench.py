@@ -776,6 +776,21 @@ def other_configs(local_rank, stream):
     ts["ksplit_4_simulated"] = ksplit_simulated(p, 4, whole, local_rank, stream)
     out["tall_skinny_AtB"] = ts
     del plan, A, B, whole
+    # the same shape with a small C (40 x 40 blocks, 1600 tiles for about 1800 resident
+    # warps): the case the K split is for
+    p = tall_skinny(nmn=40, window=40)
+    A, B = mk(p.A), mk(p.B)
+    plan = bst.multiply_plan(A, B, None, p.eps, "T", "N", device=local_rank)
+    plan.alloc_result(local_rank)
+    f = plan.stats()["flops"]
+    sc = {"flop": f, "c_blocks": plan.stats()["n_c_blocks"]}
+    for split in (1, 2, 4, 8, 0):
+        ms = _median_ms(lambda: plan.execute(1.0, 0.0, bst.BST_FP64, split), stream)
+        sc[f"split_{split or 'auto'}"] = dict(rate(f, ms), split_k=plan.stats()["split_k"],
+                                              rel_err_vs_oracle_sample=_sample_err_matrix(
+                                                  p, plan, p.A.col_sizes, p.B.col_sizes))
+    out["tall_skinny_small_C"] = sc
+    del plan, A, B
     # 64 independent products in one persistent launch, replayed from a CUDA graph
     probs = batched()
     mats, plans = [], []
