@@ -412,6 +412,17 @@ bst_status bst_batch_destroy(bst_batch *batch);
 bst_status bst_sum_parts(bst_ctx *ctx, int32_t nparts, int64_t nblocks, const int64_t *dst_off,
                          const int64_t *src_off, const double *src, double *dst, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Test of the bounded device waits.  Every spin-wait of the library's kernels (the
+ * panel kernel's mbarrier waits) gives up after a bound, records an error flag that the
+ * host reads (bst_plan_stats reports it as BST_ERR_TIMEOUT) and lets the kernel drain
+ * and return, so the context stays usable.  bst_debug_wait_probe runs a kernel whose
+ * one wait, on an mbarrier nothing arrives at, is bounded by bound_ns (1e3 .. 1e9 ns),
+ * and returns what that wait reports: BST_ERR_TIMEOUT.  Synchronises `stream`.
+ * Errors: INVALID_ARG for a NULL context or a bound outside the range.
+ * ------------------------------------------------------------------------- */
+bst_status bst_debug_wait_probe(bst_ctx *ctx, int64_t bound_ns, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

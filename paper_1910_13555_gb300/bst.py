@@ -95,6 +95,7 @@ _SIGS = {
     "bst_batch_execute": ([_VP, _VP, _VP, C.c_int32, _VP], C.c_int32),
     "bst_batch_destroy": ([_VP], C.c_int32),
     "bst_sum_parts": ([_VP, C.c_int32, C.c_int64, _VP, _VP, _VP, _VP, _VP], C.c_int32),
+    "bst_debug_wait_probe": ([_VP, C.c_int64, _VP], C.c_int32),
 }
 
 
@@ -390,6 +391,11 @@ def bst_batch_execute(batch, alpha, beta, precision=BST_FP64, stream=None):
 
 def bst_batch_destroy(batch):
     _check(load().bst_batch_destroy(batch), "bst_batch_destroy")
+
+
+def bst_debug_wait_probe(ctx, bound_ns, stream=None):
+    _check(load().bst_debug_wait_probe(ctx, int(bound_ns), _stream(stream)),
+           "bst_debug_wait_probe")
 
 
 def bst_sum_parts(ctx, nparts, nblocks, dst_off, src_off, src, dst, stream=None):

@@ -555,7 +555,8 @@ __device__ __forceinline__ unsigned long long gtimer() {
 // kWaitNs; gives up early once another role has recorded an error.  Returns false
 // (and records kErrWait) when it gives up.
 __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err,
-                                       bool drain = false) {
+                                       bool drain = false,
+                                       unsigned long long bound = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
   for (uint32_t i = 1;; ++i) {
@@ -563,7 +564,7 @@ __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err,
     {
       // a drain (copies or MMAs in flight) waits out its bound even after an error
       if (!drain && *reinterpret_cast<volatile int *>(err) != 0) return false;
-      if (gtimer() - t0 > kWaitNs) {
+      if (gtimer() - t0 > bound) {
         atomicCAS(err, 0, kErrWait);
         return false;
       }
@@ -584,6 +585,18 @@ __device__ __forceinline__ void tc_fence_before() {
 }
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// A wait that cannot complete (an mbarrier nothing arrives at), bounded by bound_ns: lets
+// a test check on the GPU that a wait which runs out is reported the way every bounded
+// wait of the panel kernel reports it, and that the context stays usable afterwards.
+__global__ void k_pan_wait_probe(int *err, unsigned long long bound_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait(&bar, 0, err, false, bound_ns);
+  }
 }
 
 // shared-memory matrix descriptor, K-major and swizzled: rows of 32 B (one K-step of 16
@@ -1588,3 +1601,28 @@ void launch_panel_batch(const void *d_plans, const int2 *ulist, int64_t n, int *
 int *panel_err_flag(bst_plan *p) { return p->panel ? p->panel->err : nullptr; }
 
 }  // namespace bst
+
+extern "C" bst_status bst_debug_wait_probe(bst_ctx *ctx, int64_t bound_ns, void *stream) {
+  API_BEGIN
+  BST_REQUIRE(ctx, BST_ERR_INVALID_ARG, "NULL context");
+  BST_REQUIRE(bound_ns >= 1000 && bound_ns <= 1000000000, BST_ERR_INVALID_ARG,
+              "bound_ns outside [1e3, 1e9]");
+  int cur = -1;
+  BST_CUDA(cudaGetDevice(&cur));
+  if (cur != ctx->device) BST_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  bst::Arena scratch;
+  scratch.ctx = static_cast<bst::Ctx *>(ctx);
+  scratch.stream = s;
+  int *err = scratch.alloc_n<int>(1);
+  BST_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  bst::k_pan_wait_probe<<<1, 32, 0, s>>>(err, (unsigned long long)bound_ns);
+  BST_CHECK_LAUNCH();
+  int e = 0;
+  BST_CUDA(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BST_CUDA(cudaStreamSynchronize(s));
+  scratch.release_all();
+  if (cur != ctx->device) BST_CUDA(cudaSetDevice(cur));
+  BST_REQUIRE(e == 0, BST_ERR_TIMEOUT, "a bounded device wait gave up");
+  API_END
+}

@@ -334,3 +334,24 @@ def test_graph_capture_before_and_after_the_schedule_exists():
             torch.cuda.synchronize()
         assert bst.bst_plan_emu_costs(plan.handle)["panel"]
         assert plan.stats()["n_stack"] > 0
+
+
+def test_bounded_wait_reports_timeout_and_context_stays_usable():
+    """A device wait that cannot complete (an mbarrier nothing arrives at) gives up after
+    its bound and is reported as BST_ERR_TIMEOUT; the next product on the same context
+    still runs and matches the oracle.  No GPU fault is involved: the kernel returns."""
+    import time
+
+    import torch
+    ctx = bst.context()
+    t0 = time.perf_counter()
+    with pytest.raises(bst.BstError) as e:
+        bst.bst_debug_wait_probe(ctx, 20_000_000)  # 20 ms
+    assert e.value.name == "BST_ERR_TIMEOUT"
+    assert time.perf_counter() - t0 < 5.0
+    with pytest.raises(bst.BstError) as e:
+        bst.bst_debug_wait_probe(ctx, 10)  # below the accepted range
+    assert e.value.name == "BST_ERR_INVALID_ARG"
+    got, ref = check(_mixed(47), mode=2)
+    assert got["stats"]["n_stack"] > 0
+    torch.cuda.synchronize()
