@@ -53,15 +53,40 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // ---- block norms -------------------------------------------------------------------
 
-// One warp per group of 32 consecutive blocks.  Lane j first loads the size and offset
-// of block j of the group (one coalesced round of index loads).  For each block the
-// lanes accumulate lane-strided squares and park their 32 partial sums in a row of
-// shared memory; then lane j adds row j (the partials of block j) in lane order and
-// takes its square root.  GB300's FP64 pipe takes as long for a warp instruction with
-// one active lane as with 32: a butterfly costs five full FP64 instructions per block,
-// the transposed sum one per block, and the group's 32 square roots run together.
+// Matrices of small blocks (at most kNormSmall elements): one warp per group of 32
+// consecutive blocks.  Lane j first loads the size and offset of block j of the group
+// (one coalesced round of index loads).  For each block the lanes accumulate
+// lane-strided squares and park their 32 partial sums in a row of shared memory; then
+// lane j adds row j (the partials of block j) in lane order and takes its square root.
+// GB300's FP64 pipe takes as long for a warp instruction with one active lane as with
+// 32: a butterfly costs five full FP64 instructions per block, the transposed sum one
+// per block, and the group's 32 square roots run together.  Matrices with larger blocks
+// (a contraction's folded views, up to hundreds of thousands of elements a block): one
+// warp per block, a butterfly at the end (grouping them left a few hundred warps
+// streaming 32 large blocks each: 4.6 ms for the rank-4 operand against a few tens of
+// microseconds).
 constexpr int kNormGroup = 32;
 constexpr int kNormWarps = 4;
+constexpr int64_t kNormSmall = 1024;
+
+__global__ void __launch_bounds__(32 * kNormWarps)
+    k_block_norms1(int64_t nblocks, const int32_t *__restrict__ row,
+                   const int32_t *__restrict__ col, const int32_t *__restrict__ rsz,
+                   const int32_t *__restrict__ csz, const int64_t *__restrict__ off,
+                   const double *__restrict__ data, double *__restrict__ norms) {
+  const int lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * kNormWarps + (threadIdx.x >> 5);
+  if (b >= nblocks) return;
+  const int64_t len = (int64_t)rsz[row[b]] * csz[col[b]];
+  const double *x = data + off[b];
+  double s = 0.0;
+  for (int64_t e = lane; e < len; e += 32) {
+    const double v = __ldg(x + e);
+    s = fma(v, v, s);
+  }
+  s = warp_sum_d(s);
+  if (lane == 0) norms[b] = sqrt(s);
+}
 
 __global__ void __launch_bounds__(32 * kNormWarps)
     k_block_norms(int64_t nblocks, const int32_t *__restrict__ row,
@@ -383,9 +408,17 @@ __global__ void k_ref_elems(int64_t nblocks, const int32_t *__restrict__ flag,
 void block_norms(const bst_matrix *m, double *norms, cudaStream_t s) {
   if (m->nblocks == 0) return;
   BST_REQUIRE(m->data != nullptr, BST_ERR_STATE, "matrix data not bound");
-  const int64_t groups = (m->nblocks + kNormGroup - 1) / kNormGroup;
-  k_block_norms<<<nblk(groups, kNormWarps), 32 * kNormWarps, 0, s>>>(
-      m->nblocks, m->row, m->col, m->rsz, m->csz, m->off, m->data, norms);
+  int64_t rmax = 0, cmax = 0;
+  for (int32_t v : m->h_rsz) rmax = std::max<int64_t>(rmax, v);
+  for (int32_t v : m->h_csz) cmax = std::max<int64_t>(cmax, v);
+  if (m->h_rsz.empty() || m->h_csz.empty() || rmax * cmax > kNormSmall) {
+    k_block_norms1<<<nblk(m->nblocks, kNormWarps), 32 * kNormWarps, 0, s>>>(
+        m->nblocks, m->row, m->col, m->rsz, m->csz, m->off, m->data, norms);
+  } else {
+    const int64_t groups = (m->nblocks + kNormGroup - 1) / kNormGroup;
+    k_block_norms<<<nblk(groups, kNormWarps), 32 * kNormWarps, 0, s>>>(
+        m->nblocks, m->row, m->col, m->rsz, m->csz, m->off, m->data, norms);
+  }
   BST_CHECK_LAUNCH();
 }
 
