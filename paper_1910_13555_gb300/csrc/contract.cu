@@ -154,18 +154,43 @@ __global__ void k_permute(PermArgs P) {
     len *= s[d];
   }
   const int64_t to = P.toff[tb], vo = P.voff[q];
-  for (int32_t e = threadIdx.x; e < len; e += blockDim.x) {
-    int32_t rem = e, src = 0;
-    for (int j = P.rank - 1; j >= 0; --j) {
-      const int d = P.ord[j];
-      const int32_t qd = rem / s[d];
-      src += (rem - qd * s[d]) * st[d];
-      rem = qd;
+  if ((int32_t)threadIdx.x >= len) return;
+  // the thread's elements e = threadIdx.x + i * blockDim.x in view order, as mixed-radix
+  // digits over the view's modes (slowest first): decoded once by division, then
+  // advanced by the step's own digits with one carry per mode (an element costs a few
+  // adds instead of one division per mode)
+  // (loops over all kMaxRank modes with the unused ones as size-1 modes, so that the
+  // digit arrays live in registers)
+  int32_t dig[kMaxRank], inc[kMaxRank], sv[kMaxRank], tv[kMaxRank];
+  {
+    int32_t rem = (int32_t)threadIdx.x, stp = (int32_t)blockDim.x;
+#pragma unroll
+    for (int j = kMaxRank - 1; j >= 0; --j) {
+      const bool used = j < P.rank;
+      const int d = used ? P.ord[j] : 0;
+      sv[j] = used ? s[d] : 1;
+      tv[j] = used ? st[d] : 0;
+      dig[j] = rem % sv[j];
+      rem /= sv[j];
+      inc[j] = stp % sv[j];
+      stp /= sv[j];
     }
+  }
+  for (int32_t e = threadIdx.x; e < len; e += blockDim.x) {
+    int32_t src = 0;
+#pragma unroll
+    for (int j = 0; j < kMaxRank; ++j) src += dig[j] * tv[j];
     if (P.to_view)
       P.dst[vo + e] = P.src[to + src];
     else
       P.dst[to + src] = P.src[vo + e];
+    int32_t carry = 0;
+#pragma unroll
+    for (int j = kMaxRank - 1; j >= 0; --j) {
+      const int32_t v = dig[j] + inc[j] + carry;
+      carry = v >= sv[j];
+      dig[j] = carry ? v - sv[j] : v;
+    }
   }
 }
 
