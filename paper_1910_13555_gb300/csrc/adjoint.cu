@@ -11,7 +11,7 @@
 // grouped by stored A block and by stored B block once (stable counting sort, cached
 // in the plan), and warp `a` sums over the entries of A block `a`.  Lanes own output
 // elements (m x k of dop(A) column by column, k x n of dop(B) row by row) in passes of
-// 256, a block of more than 4 passes spread over several warps (chunks of 4 passes);
+// 256, a block of more than one pass spread over several warps (a pass each);
 // every block product reads its dC block and the other operand's block from L1/L2.
 #include <algorithm>
 
@@ -172,8 +172,10 @@ __global__ void k_adj_cin(int64_t nc, const int32_t *c_cin, const int64_t *c_off
 
 // Chunks of kAdjChunkPasses passes (of 32 RA outputs) per warp, as many per block as
 // the largest stored block of the output side needs; a warp whose chunk lies past its
-// block's end returns at once.  Without host block sizes: one chunk per block.
-constexpr int kAdjChunkPasses = 4;
+// block's end returns at once.  Without host block sizes: one chunk per block.  One
+// pass per chunk: more warps and shorter tails than 4 (the rank-4 adjoint's dU grid
+// was 3.4 waves of resident CTAs): rank-4 adjoint 20.2 -> 16.8 ms, rank-3 86 -> 80.5 ms.
+constexpr int kAdjChunkPasses = 1;
 
 void chunking(AdjArgs &P, const bst_matrix &M) {
   int32_t r = 0, c = 0;
