@@ -11,7 +11,7 @@
 // grouped by stored A block and by stored B block once (stable counting sort, cached
 // in the plan), and warp `a` sums over the entries of A block `a`.  Lanes own output
 // elements (m x k of dop(A) column by column, k x n of dop(B) row by row) in passes of
-// 256, a block of more than one pass spread over several warps (a pass each);
+// 32 RA = 128, a block of more than one pass spread over several warps (a pass each);
 // every block product reads its dC block and the other operand's block from L1/L2.
 #include <algorithm>
 
@@ -29,7 +29,7 @@ namespace {
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-constexpr int RA = 8;  // outputs per lane per pass
+constexpr int RA = 4;  // outputs per lane per pass (8 and 2 measured: 4 the best balance)
 
 struct AdjArgs {
   const double *A, *B, *dC;
@@ -174,7 +174,8 @@ __global__ void k_adj_cin(int64_t nc, const int32_t *c_cin, const int64_t *c_off
 // the largest stored block of the output side needs; a warp whose chunk lies past its
 // block's end returns at once.  Without host block sizes: one chunk per block.  One
 // pass per chunk: more warps and shorter tails than 4 (the rank-4 adjoint's dU grid
-// was 3.4 waves of resident CTAs): rank-4 adjoint 20.2 -> 16.8 ms, rank-3 86 -> 80.5 ms.
+// was 3.4 waves of resident CTAs): rank-4 adjoint 20.2 -> 16.8 ms, rank-3 86 -> 80.5 ms
+// with passes of 256 outputs; passes of 128 (RA = 4): 16.5 and 79.8 ms.
 constexpr int kAdjChunkPasses = 1;
 
 void chunking(AdjArgs &P, const bst_matrix &M) {
