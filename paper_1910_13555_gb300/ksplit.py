@@ -28,7 +28,9 @@ from dataclasses import dataclass
 import numpy as np
 
 __all__ = ["k_index", "k_ranges", "select_k_range", "Layout", "exchange_layout",
-           "gather_patterns", "exchange", "multiply_ksplit", "KSplitResult"]
+           "gather_patterns", "exchange", "multiply_ksplit", "KSplitResult",
+           "select_tensor_range", "tensor_fold", "tensor_unfold", "result_block_sizes",
+           "contract_ksplit"]
 
 
 def k_index(rows, cols, trans, side):
@@ -250,5 +252,97 @@ def multiply_ksplit(A, B, row_sizes, col_sizes, C_in=None, alpha=1.0, beta=0.0, 
     if pdev == "cpu":  # a host transport: the runs travel through host memory
         part = part.cpu()
     recv = exchange(part, layout, group).to(C.data.device)
+    r, c, o, data, tables = sum_owned(layout, q, recv, device)
+    return KSplitResult(r, c, o, data, layout, plan, tables)
+
+
+# ---- contractions -------------------------------------------------------------------
+#
+# The same split for a tensor contraction whose contracted index is long (paper Sec. 4:
+# three-centre integrals T(P, mu, nu), P the auxiliary index, contracted with U(P, nu,
+# lam)): each process holds the blocks of T1 and T2 whose index along a contracted mode
+# pair lies in its range, contracts them with the library, and the partial results R~_i
+# are summed as above, R's blocks seen as the rows and columns of its fold (all modes
+# but the last as rows, the last as columns: R's canonical block order is then CSR
+# order, and a block's elements are the row-major fold of its own).
+
+
+def select_tensor_range(block_sizes, index, data, mode, lo, hi):
+    """The blocks of a host tensor (canonical order, blocks packed in that order) whose
+    index along `mode` lies in [lo, hi): (index, data)."""
+    index = np.asarray(index, np.int32)
+    lens = np.ones(len(index), np.int64)
+    for d, s in enumerate(block_sizes):
+        lens *= np.asarray(s, np.int64)[index[:, d]]
+    keep = (index[:, mode] >= lo) & (index[:, mode] < hi)
+    return index[keep], np.asarray(data, np.float64)[np.repeat(keep, lens)]
+
+
+def tensor_fold(index, block_sizes):
+    """A tensor's blocks as (rows, cols) of its fold -- rows = the modes but the last
+    (mixed radix, mode 0 slowest), cols = the last mode -- with the fold's row and column
+    block sizes."""
+    index = np.asarray(index, np.int64).reshape(len(index), -1)
+    rank = index.shape[1]
+    sizes = [np.asarray(s, np.int64) for s in block_sizes]
+    if rank == 1:
+        return (np.zeros(len(index), np.int32), index[:, 0].astype(np.int32),
+                np.ones(1, np.int64), sizes[0])
+    rows = np.zeros(len(index), np.int64)
+    row_sizes = np.ones(1, np.int64)
+    for d in range(rank - 1):
+        rows = rows * len(sizes[d]) + index[:, d]
+        row_sizes = np.outer(row_sizes, sizes[d]).reshape(-1)
+    return rows.astype(np.int32), index[:, -1].astype(np.int32), row_sizes, sizes[-1]
+
+
+def tensor_unfold(rows, cols, block_sizes):
+    """The block index tuples (nblocks x rank) of fold rows and columns."""
+    nblk = [len(s) for s in block_sizes]
+    rank = len(nblk)
+    out = np.zeros((len(rows), rank), np.int32)
+    out[:, -1] = cols
+    r = np.asarray(rows, np.int64).copy()
+    for d in range(rank - 2, -1, -1):
+        out[:, d] = r % nblk[d]
+        r //= nblk[d]
+    return out
+
+
+def result_block_sizes(sizes1, sizes2, f1, f2, result_order=None):
+    """Per-mode block sizes of a contraction's result: the free modes (f1..., f2...),
+    result mode r being free slot result_order[r]."""
+    free = [sizes1[d] for d in f1] + [sizes2[d] for d in f2]
+    order = range(len(free)) if result_order is None else result_order
+    return [np.asarray(free[r], np.int64) for r in order]
+
+
+def contract_ksplit(T1, T2, c1, c2, f1, f2, r_block_sizes, result_order=None, R_in=None,
+                    alpha=1.0, beta=0.0, eps=0.0, precision=None, group=None, device=0):
+    """R = alpha sum T1 T2 + beta R_in over the processes of `group`, a contracted mode
+    pair divided among them: T1 and T2 (library tensors on this process's GPU) hold this
+    process's blocks of it (select_tensor_range cuts them from whole host tensors), R_in
+    is used on process 0 only; r_block_sizes are R's per-mode block sizes
+    (result_block_sizes).  Returns this process's owned blocks of R as a KSplitResult
+    whose rows and columns are those of R's fold (tensor_unfold gives the index tuples).
+    Every process of the group must call it."""
+    import torch.distributed as dist
+
+    from . import bst
+    if precision is None:
+        precision = bst.BST_FP64
+    q = dist.get_rank(group)
+    plan = bst.contract(T1, T2, c1, c2, f1, f2, result_order, R_in if q == 0 else None,
+                        alpha, beta if q == 0 else 0.0, eps, precision, 1, device)
+    R = plan.result
+    idx, _ = R.index()
+    rows, cols, row_sizes, col_sizes = tensor_fold(idx, r_block_sizes)
+    nloc = R.info[2]
+    pdev = f"cuda:{device}" if dist.get_backend(group) == "nccl" else "cpu"
+    layout = exchange_layout(gather_patterns(rows, cols, group, pdev), row_sizes, col_sizes)
+    part = R.data[:nloc]
+    if pdev == "cpu":
+        part = part.cpu()
+    recv = exchange(part, layout, group).to(R.data.device)
     r, c, o, data, tables = sum_owned(layout, q, recv, device)
     return KSplitResult(r, c, o, data, layout, plan, tables)

@@ -211,3 +211,81 @@ def test_simulated_ksplit_with_cin_alpha_beta():
         out.append(data.cpu().numpy())
     got = np.concatenate(out)
     assert np.linalg.norm(got - full["data"]) / np.linalg.norm(full["data"]) <= 1e-12
+
+
+def _rank3_small():
+    from paper_1910_13555_gb300.workloads import rank3
+    return rank3(nP=300, sP=12, nao=60, window=8, p=0.3)
+
+
+def test_simulated_contraction_split_against_oracle():
+    """The rank-3 contraction split over P among 3 processes simulated on one GPU: the
+    library's partial contractions, the fold layout and bst_sum_parts, against the
+    oracle's undivided contraction."""
+    import torch
+    from paper_1910_13555_gb300.workloads import BSTensor
+    w = _rank3_small()
+    full = oracle.contract(w.T1, w.T2, w.c1, w.c2, w.f1, w.f2, w.result_order)
+    rsz = ksplit.result_block_sizes(w.T1.block_sizes, w.T2.block_sizes, w.f1, w.f2,
+                                    w.result_order)
+    nP = len(w.T1.block_sizes[0])
+    bounds = [0, nP // 3, 2 * nP // 3, nP]
+    parts, pats, keep = [], [], []
+    for i in range(3):
+        i1, d1 = ksplit.select_tensor_range(w.T1.block_sizes, w.T1.index, w.T1.data,
+                                            w.c1[0], bounds[i], bounds[i + 1])
+        i2, d2 = ksplit.select_tensor_range(w.T2.block_sizes, w.T2.index, w.T2.data,
+                                            w.c2[0], bounds[i], bounds[i + 1])
+        t1 = bst.Tensor.from_host(w.T1.block_sizes, i1, d1)
+        t2 = bst.Tensor.from_host(w.T2.block_sizes, i2, d2)
+        plan = bst.contract(t1, t2, w.c1, w.c2, w.f1, w.f2, w.result_order)
+        idx, _ = plan.result.index()
+        rows, cols, row_sizes, col_sizes = ksplit.tensor_fold(idx, rsz)
+        pats.append((rows, cols))
+        parts.append(plan.result.data[:plan.result.info[2]])
+        keep.append((plan, t1, t2))
+    lay = ksplit.exchange_layout(pats, row_sizes, col_sizes)
+    assert np.array_equal(ksplit.tensor_unfold(lay.rows, lay.cols, rsz), full["index"])
+    out = []
+    for q in range(3):
+        recv = torch.cat([parts[i][int(lay.send[i, :q].sum()):int(lay.send[i, :q + 1].sum())]
+                          for i in range(3)])
+        _, _, _, data, _ = ksplit.sum_owned(lay, q, recv)
+        torch.cuda.synchronize()
+        out.append(data.cpu().numpy())
+    got = np.concatenate(out)
+    assert np.linalg.norm(got - full["data"]) / np.linalg.norm(full["data"]) <= 1e-12
+
+
+_CWORKER = r"""
+import os, sys
+sys.path.insert(0, {root!r}); sys.path.insert(0, os.path.join({root!r}, "tests"))
+import numpy as np, torch, torch.distributed as dist
+import oracle
+import test_gpu_ksplit as T
+from paper_1910_13555_gb300 import bst, ksplit
+torch.cuda.set_device(0)
+dist.init_process_group("nccl", rank=0, world_size=1,
+                        init_method="tcp://127.0.0.1:" + os.environ["PORT"])
+w = T._rank3_small()
+t1 = bst.Tensor.from_host(w.T1.block_sizes, w.T1.index, w.T1.data)
+t2 = bst.Tensor.from_host(w.T2.block_sizes, w.T2.index, w.T2.data)
+rsz = ksplit.result_block_sizes(w.T1.block_sizes, w.T2.block_sizes, w.f1, w.f2, w.result_order)
+res = ksplit.contract_ksplit(t1, t2, w.c1, w.c2, w.f1, w.f2, rsz, w.result_order, alpha=2.0)
+torch.cuda.synchronize()
+full = oracle.contract(w.T1, w.T2, w.c1, w.c2, w.f1, w.f2, w.result_order, alpha=2.0)
+assert np.array_equal(ksplit.tensor_unfold(res.rows, res.cols, rsz), full["index"])
+got = res.data.cpu().numpy()
+rel = np.linalg.norm(got - full["data"]) / np.linalg.norm(full["data"])
+assert rel <= 1e-12, rel
+dist.destroy_process_group()
+print("ok", rel)
+"""
+
+
+def test_contract_ksplit_one_process_group():
+    env = dict(os.environ, PORT=str(_free_port()), NCCL_NVLS_ENABLE="0")
+    pr = subprocess.run([sys.executable, "-c", _CWORKER.format(root=ROOT)], env=env, cwd=ROOT,
+                        capture_output=True, text=True, timeout=300)
+    assert pr.returncode == 0, pr.stderr[-3000:]
+    assert any(line.startswith("ok ") for line in pr.stdout.splitlines()), pr.stdout

@@ -248,3 +248,40 @@ def test_gloo_processes_gather_exchange_and_sum(tmp_path, world):
     assert np.array_equal(np.concatenate(cols), full["cols"])
     assert _rel(np.concatenate(data), full["data"]) <= 1e-13
     assert all(len(x) > 0 for x in rows)  # every process owns a share
+
+
+def _rank3_small():
+    from paper_1910_13555_gb300.workloads import rank3
+    return rank3(nP=120, sP=6, nao=40, window=6, p=0.4)
+
+
+def test_contraction_split_over_the_auxiliary_index():
+    """A rank-3 contraction R(mu, lam) = sum_{P, nu} T(P, mu, nu) U(P, nu, lam) split over
+    P among 3 processes (paper Sec. 4's long contracted index): the oracle's partial
+    contractions, their folds, the layout and the owners' sums assemble the undivided
+    result (index bit-exact, values within rounding); fold and unfold are inverses."""
+    w = _rank3_small()
+    full = oracle.contract(w.T1, w.T2, w.c1, w.c2, w.f1, w.f2, w.result_order)
+    nP = len(w.T1.block_sizes[0])
+    bounds = [0, nP // 3, 2 * nP // 3, nP]
+    parts, pats = [], []
+    rsz = ksplit.result_block_sizes(w.T1.block_sizes, w.T2.block_sizes, w.f1, w.f2,
+                                    w.result_order)
+    from paper_1910_13555_gb300.workloads import BSTensor
+    for i in range(3):
+        i1, d1 = ksplit.select_tensor_range(w.T1.block_sizes, w.T1.index, w.T1.data,
+                                            w.c1[0], bounds[i], bounds[i + 1])
+        i2, d2 = ksplit.select_tensor_range(w.T2.block_sizes, w.T2.index, w.T2.data,
+                                            w.c2[0], bounds[i], bounds[i + 1])
+        r = oracle.contract(BSTensor(w.T1.block_sizes, i1, d1), BSTensor(w.T2.block_sizes, i2, d2),
+                            w.c1, w.c2, w.f1, w.f2, w.result_order)
+        rows, cols, row_sizes, col_sizes = ksplit.tensor_fold(r["index"], rsz)
+        assert np.array_equal(ksplit.tensor_unfold(rows, cols, rsz), r["index"])
+        parts.append(r)
+        pats.append((rows, cols))
+    lay = ksplit.exchange_layout(pats, row_sizes, col_sizes)
+    assert np.array_equal(ksplit.tensor_unfold(lay.rows, lay.cols, rsz), full["index"])
+    assert np.array_equal(lay.offsets[:-1], full["offsets"])
+    bufs = _simulate(lay, parts)
+    got = np.concatenate([_owner_sum(lay, q, bufs[q]) for q in range(3)])
+    assert _rel(got, full["data"]) <= 1e-13
