@@ -285,3 +285,29 @@ def test_contraction_split_over_the_auxiliary_index():
     bufs = _simulate(lay, parts)
     got = np.concatenate([_owner_sum(lay, q, bufs[q]) for q in range(3)])
     assert _rel(got, full["data"]) <= 1e-13
+
+
+@pytest.mark.parametrize("rank", [1, 2, 3, 4])
+def test_tensor_fold_roundtrip_and_order(rank):
+    """tensor_fold: rows in mixed radix over the modes but the last (mode 0 slowest), so
+    lexicographic tuple order is CSR order; row sizes are the products of the modes'
+    sizes; tensor_unfold inverts it."""
+    rng = np.random.default_rng(rank)
+    sizes = [rng.integers(1, 6, rng.integers(2, 6)) for _ in range(rank)]
+    grid = np.stack(np.meshgrid(*[np.arange(len(s)) for s in sizes], indexing="ij"), -1)
+    idx = grid.reshape(-1, rank)[rng.random(int(np.prod([len(s) for s in sizes]))) < 0.5]
+    rows, cols, row_sizes, col_sizes = ksplit.tensor_fold(idx, sizes)
+    assert np.array_equal(ksplit.tensor_unfold(rows, cols, sizes), idx)
+    key = rows.astype(np.int64) * len(col_sizes) + cols
+    assert (np.diff(key) > 0).all()  # lexicographic tuples -> increasing (row, col)
+    lens = np.ones(len(idx), np.int64)
+    for d, s in enumerate(sizes):
+        lens *= s[idx[:, d]]
+    assert np.array_equal(row_sizes[rows] * col_sizes[cols], lens)
+
+
+def test_result_block_sizes_follow_result_order():
+    s1 = [np.array([1, 2]), np.array([3]), np.array([4, 5, 6])]
+    s2 = [np.array([7]), np.array([8, 9])]
+    out = ksplit.result_block_sizes(s1, s2, f1=[1, 2], f2=[1], result_order=[2, 0, 1])
+    assert [list(x) for x in out] == [[8, 9], [3], [4, 5, 6]]
